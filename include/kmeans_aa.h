@@ -1,0 +1,183 @@
+/*
+ * kmeans_aa.h - C ABI of the GB300 (sm_103a) K-Means library with Anderson acceleration.
+ *
+ * Method: "Fast K-Means Clustering with Anderson Acceleration" (Zhang, Yao, Peng, Yu, Deng).
+ * The hot path is one fixed-point step G(C) (Eq. 6) = assignment (Eq. 3) + update (Eq. 4),
+ * with the energy E (Eq. 1) fused into the assignment, followed by the Anderson mix
+ * (Eq. 7, Eq. 8) under the energy safeguard and the dynamic-m rule of Algorithm 1.
+ *
+ * Conventions for every call:
+ *   - Matrices are row-major.  X is [N, d]; centroids are [K, d].
+ *   - Pointers are DEVICE pointers unless the parameter says "host".  The caller owns every
+ *     buffer it passes; the library owns only the workspace inside the context.
+ *   - Calls are asynchronous on the context's stream, except kmeans_solve and
+ *     kmeans_solve_host, which synchronise the stream to fill the host-side info struct.
+ *   - Every call returns a kmeans_status; nothing aborts.  kmeans_last_error() gives a
+ *     one-line description of the last failure on a context.
+ *   - Sizes: 1 <= K <= N (the problem statement of Eq. 1 requires K <= N), 1 <= d <= 4096.
+ *     Violations return KM_EINVAL before any work is queued.
+ *   - There is no CPU fallback: without a usable GPU every call returns KM_ECUDA.
+ */
+#ifndef KMEANS_AA_H
+#define KMEANS_AA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KM_OK = 0,
+    KM_EINVAL = 1,      /* bad argument (shape, NULL pointer, unsupported combination) */
+    KM_ENOMEM = 2,      /* workspace would exceed the context's HBM budget, or cudaMalloc failed */
+    KM_ECUDA = 3,       /* a CUDA runtime call failed (message in kmeans_last_error) */
+    KM_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    KM_ENONFINITE = 5,  /* X or the centroids contain NaN or Inf */
+    KM_EBUSY = 6        /* the context is in use by another call */
+} kmeans_status;
+
+/* Arithmetic of the distance computation.
+ *   KM_F64      X and centroids are double; distances in FP64, direct form sum (x-c)^2.
+ *   KM_F32      X and centroids are float; distances as ||c||^2 - 2 x.c in FP32 on CUDA cores
+ *               with a per-row error bound; rows whose top-2 gap is inside the bound are
+ *               rescored in the direct form in FP32.
+ *   KM_BF16_F32 X is float and a BF16 copy of X is supplied (kmeans_data.X_bf16); distances
+ *               on tcgen05 tensor cores in BF16 with FP32 accumulation, near-tie rows rescored
+ *               in FP32 from X.  Centroids are float.
+ * In every mode centroid-space arithmetic (update, residuals, Anderson least squares, energy
+ * comparison) is FP64. */
+typedef enum { KM_F64 = 0, KM_F32 = 1, KM_BF16_F32 = 2 } kmeans_prec;
+
+/* The samples.  X_bf16 must hold the BF16 rounding of X when prec == KM_BF16_F32 and is
+ * ignored otherwise.  The struct itself lives in host memory; X and X_bf16 are device
+ * pointers (host pointers for kmeans_solve_host). */
+typedef struct {
+    const void* X;       /* [N, d]: double for KM_F64, float otherwise */
+    const void* X_bf16;  /* [N, d] uint16 BF16 bit patterns, KM_BF16_F32 only */
+    int64_t N;
+    int32_t d;
+    int32_t prec;        /* kmeans_prec */
+} kmeans_data;
+
+/* Solver parameters (Algorithm 1; defaults from kmeans_default_params):
+ *   m_max     maximum history length m-bar (10)
+ *   m_init    initial m (2; clamped to m_max)
+ *   max_iter  iteration cap (1000)
+ *   lloyd_only 1 = plain Lloyd (the same loop with the Anderson step switched off)
+ *   eps1, eps2 thresholds of the dynamic-m rule (0.02, 0.5)
+ *   tol       0 = stop when the assignment no longer changes (the paper's criterion);
+ *             > 0 = stop when at most floor(tol*N) samples change cluster
+ *   rank_tol  least-squares columns from the first with R_kk <= rank_tol*R_00 on are dropped */
+typedef struct {
+    int32_t m_max;
+    int32_t m_init;
+    int32_t max_iter;
+    int32_t lloyd_only;
+    double eps1;
+    double eps2;
+    double tol;
+    double rank_tol;
+} kmeans_params;
+
+/* Result summary (host struct).
+ *   iters          loop passes t at termination (Algorithm 1's t; Lloyd counts the same way)
+ *   accepted       passes whose accelerated iterate passed the energy safeguard
+ *   rejected       passes that reverted to the Lloyd iterate (extra assignment pass each)
+ *   assign_passes  assignment passes over X in total (initial + one per t + rejections)
+ *   converged      1 = assignment stopped changing, 0 = hit max_iter
+ *   m_final        m after the last pass
+ *   E              final energy E(P, C) (Eq. 1)
+ *   rescored_rows  rows whose reduced-precision top-2 gap was inside the error bound and
+ *                  were rescored in FP32, summed over all passes
+ *   device_ms      device time of the solve measured with CUDA events */
+typedef struct {
+    int32_t iters;
+    int32_t accepted;
+    int32_t rejected;
+    int32_t assign_passes;
+    int32_t converged;
+    int32_t m_final;
+    double E;
+    int64_t rescored_rows;
+    double device_ms;
+} kmeans_info;
+
+typedef struct kmeans_ctx kmeans_ctx;
+
+/* Create a context on `device` bound to `cuda_stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  hbm_budget_bytes caps the workspace the context may allocate
+ * (0 = no cap); a call that would exceed it returns KM_ENOMEM.  *ctx is set on success. */
+kmeans_status kmeans_create(kmeans_ctx** ctx, int device, size_t hbm_budget_bytes,
+                            void* cuda_stream);
+
+/* Free the workspace and the context.  NULL is accepted. */
+kmeans_status kmeans_destroy(kmeans_ctx* ctx);
+
+/* Bind a different stream (a cudaStream_t) to the context. */
+kmeans_status kmeans_set_stream(kmeans_ctx* ctx, void* cuda_stream);
+
+/* Workspace bytes currently held by the context. */
+size_t kmeans_workspace_bytes(const kmeans_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* kmeans_status_string(kmeans_status s);
+
+/* Last error message on this context ("" if none).  Valid until the next call. */
+const char* kmeans_last_error(const kmeans_ctx* ctx);
+
+/* Fill *p with the defaults listed at kmeans_params. */
+void kmeans_default_params(kmeans_params* p);
+
+/* Assignment step, Eq. 3: rho[i] = argmin_j ||x_i - c_j||^2, lowest j on exact ties.
+ *   X         samples (see kmeans_data)
+ *   C         [K, d] centroids, double for KM_F64 else float
+ *   rho       [N] int32 output
+ *   rho_prev  [N] int32 previous assignment, or NULL
+ *   n_changed device int64 scalar: number of i with rho[i] != rho_prev[i]; requires rho_prev;
+ *             may be NULL
+ *   dmin      [N] output, X's element type (double or float): the squared distance to the
+ *             chosen centroid in the direct form; may be NULL */
+kmeans_status kmeans_assign(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K,
+                            int32_t* rho, const int32_t* rho_prev, int64_t* n_changed,
+                            void* dmin);
+
+/* Update step, Eq. 4: C_out[j] = mean of the x_i with rho[i] == j; an empty cluster keeps
+ * C_prev[j].  Deterministic: the same inputs give bitwise the same output on every run.
+ *   rho     [N] int32 in [0, K)
+ *   C_prev  [K, d] (element type of X): centroids for empty clusters
+ *   C_out   [K, d] output (element type of X); may alias C_prev
+ *   counts  [K] int64 output (cluster sizes N_j); may be NULL */
+kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t* rho,
+                            int32_t K, const void* C_prev, void* C_out, int64_t* counts);
+
+/* Energy, Eq. 1, with a given assignment: *E = sum_i ||x_i - c_{rho_i}||^2 (direct form per
+ * row in X's precision, accumulated in FP64 in a fixed order).  E is a device double. */
+kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K,
+                            const int32_t* rho, double* E);
+
+/* Full solve from C0: Lloyd (params->lloyd_only = 1) or Algorithm 1 (Anderson acceleration
+ * with the energy safeguard and dynamic m).  All iterations run on the device inside one CUDA
+ * graph with a conditional while node; the host only waits for the end.
+ *   C0     [K, d] initial centroids (element type of X)
+ *   params NULL = defaults
+ *   C_out  [K, d] final centroids (element type of X): the means of the final clusters
+ *   rho_out [N] int32 final assignment
+ *   info   host struct, filled before return (may be NULL) */
+kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const void* C0,
+                           const kmeans_params* params, void* C_out, int32_t* rho_out,
+                           kmeans_info* info);
+
+/* kmeans_solve with HOST buffers: X (and X_bf16), C0, C_out and rho_out are host pointers
+ * (pinned memory gives the fastest copies).  The inputs are copied to device workspace, the
+ * solve runs, and the results are copied back before return. */
+kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* X_host, int32_t K,
+                                const void* C0_host, const kmeans_params* params,
+                                void* C_out_host, int32_t* rho_out_host, kmeans_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMEANS_AA_H */

@@ -180,7 +180,7 @@ def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-10):
 
 
 DEFAULT_PARAMS = dict(m_max=10, m_init=2, max_iter=1000, lloyd_only=0, eps1=0.02, eps2=0.5,
-                      tol=0.0, rank_tol=1e-10)
+                      tol=0.0, rank_tol=1e-6)
 
 
 def solve(X, C0, lloyd: bool = False, trace: bool = False, **kw):

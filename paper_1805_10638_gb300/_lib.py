@@ -1,0 +1,229 @@
+"""ctypes binding of libkmeans_aa (include/kmeans_aa.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch tensors (device
+tensors, or host tensors / numpy arrays for ``kmeans_solve_host``).  Every step of the path runs
+in the CUDA library; there is no CPU fallback: if the library cannot be loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+KM_OK, KM_EINVAL, KM_ENOMEM, KM_ECUDA, KM_ETIMEOUT, KM_ENONFINITE, KM_EBUSY = range(7)
+KM_F64, KM_F32, KM_BF16_F32 = 0, 1, 2
+
+_STATUS = {0: "KM_OK", 1: "KM_EINVAL", 2: "KM_ENOMEM", 3: "KM_ECUDA", 4: "KM_ETIMEOUT",
+           5: "KM_ENONFINITE", 6: "KM_EBUSY"}
+
+
+class KmeansError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kmeans_data(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("X_bf16", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("d", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class kmeans_params(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int32), ("m_init", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("lloyd_only", ctypes.c_int32), ("eps1", ctypes.c_double), ("eps2", ctypes.c_double),
+                ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double)]
+
+
+class kmeans_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("assign_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("m_final", ctypes.c_int32), ("E", ctypes.c_double), ("rescored_rows", ctypes.c_int64),
+                ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libkmeans_aa.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libkmeans_aa.so not found at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    L.kmeans_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, vp]
+    L.kmeans_destroy.argtypes = [vp]
+    L.kmeans_set_stream.argtypes = [vp, vp]
+    L.kmeans_workspace_bytes.argtypes = [vp]
+    L.kmeans_workspace_bytes.restype = ctypes.c_size_t
+    L.kmeans_status_string.argtypes = [ctypes.c_int]
+    L.kmeans_status_string.restype = ctypes.c_char_p
+    L.kmeans_last_error.argtypes = [vp]
+    L.kmeans_last_error.restype = ctypes.c_char_p
+    L.kmeans_default_params.argtypes = [ctypes.POINTER(kmeans_params)]
+    L.kmeans_default_params.restype = None
+    pd = ctypes.POINTER(kmeans_data)
+    L.kmeans_assign.argtypes = [vp, pd, vp, i32, vp, vp, vp, vp]
+    L.kmeans_update.argtypes = [vp, pd, vp, i32, vp, vp, vp]
+    L.kmeans_energy.argtypes = [vp, pd, vp, i32, vp, dp]
+    L.kmeans_solve.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
+                               ctypes.POINTER(kmeans_info)]
+    L.kmeans_solve_host.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
+                                    ctypes.POINTER(kmeans_info)]
+    for name in ("kmeans_create", "kmeans_destroy", "kmeans_set_stream", "kmeans_assign",
+                 "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(ctx, status: int):
+    if status != KM_OK:
+        msg = load().kmeans_last_error(ctx.handle if ctx is not None else None)
+        raise KmeansError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _prec_of(X, X_bf16=None) -> int:
+    dt = X.dtype
+    if dt in (torch.float64, np.float64):
+        return KM_F64
+    if dt in (torch.float32, np.float32):
+        return KM_BF16_F32 if X_bf16 is not None else KM_F32
+    raise TypeError(f"X must be float64 or float32, got {dt}")
+
+
+def make_data(X, X_bf16=None) -> kmeans_data:
+    assert X.ndim == 2 and (X.is_contiguous() if torch.is_tensor(X) else X.flags.c_contiguous)
+    return kmeans_data(_ptr(X), _ptr(X_bf16), X.shape[0], X.shape[1], _prec_of(X, X_bf16))
+
+
+def default_params(**kw) -> kmeans_params:
+    p = kmeans_params()
+    load().kmeans_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """A kmeans_ctx bound to a device and a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, stream=None):
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        st = L.kmeans_create(ctypes.byref(h), device, hbm_budget, ctypes.c_void_p(stream))
+        if st != KM_OK:
+            raise KmeansError(st, "kmeans_create failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().kmeans_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        return int(load().kmeans_workspace_bytes(self.handle))
+
+
+def kmeans_assign(ctx: Context, X, C, rho=None, rho_prev=None, n_changed=None, dmin=None, X_bf16=None):
+    """Eq. 3 on the device; returns rho (int32 [N])."""
+    N = X.shape[0]
+    if rho is None:
+        rho = torch.empty(N, dtype=torch.int32, device=X.device)
+    data = make_data(X, X_bf16)
+    _check(ctx, load().kmeans_assign(ctx.handle, ctypes.byref(data), _ptr(C), C.shape[0], _ptr(rho),
+                                     _ptr(rho_prev), _ptr(n_changed), _ptr(dmin)))
+    return rho
+
+
+def kmeans_update(ctx: Context, X, rho, K: int, C_prev, C_out=None, counts=None):
+    """Eq. 4 on the device; returns (C_out, counts)."""
+    if C_out is None:
+        C_out = torch.empty_like(C_prev)
+    if counts is None:
+        counts = torch.empty(K, dtype=torch.int64, device=X.device)
+    data = make_data(X)
+    _check(ctx, load().kmeans_update(ctx.handle, ctypes.byref(data), _ptr(rho), K, _ptr(C_prev), _ptr(C_out),
+                                     _ptr(counts)))
+    return C_out, counts
+
+
+def kmeans_energy(ctx: Context, X, C, rho, E=None):
+    """Eq. 1 with a given assignment; returns a device float64 scalar tensor."""
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=X.device)
+    data = make_data(X)
+    _check(ctx, load().kmeans_energy(ctx.handle, ctypes.byref(data), _ptr(C), C.shape[0], _ptr(rho), _ptr(E)))
+    return E
+
+
+def kmeans_solve(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, **params):
+    """Lloyd (lloyd_only=1) or Algorithm 1 on the device; returns (C, rho, info dict)."""
+    if C_out is None:
+        C_out = torch.empty_like(C0)
+    if rho_out is None:
+        rho_out = torch.empty(X.shape[0], dtype=torch.int32, device=X.device)
+    data = make_data(X, X_bf16)
+    p = default_params(**params)
+    info = kmeans_info()
+    _check(ctx, load().kmeans_solve(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0), ctypes.byref(p),
+                                    _ptr(C_out), _ptr(rho_out), ctypes.byref(info)))
+    return C_out, rho_out, info.as_dict()
+
+
+def kmeans_solve_host(ctx: Context, X, C0, C_out=None, rho_out=None, **params):
+    """kmeans_solve with host buffers (torch CPU tensors, ideally pinned, or numpy arrays)."""
+    if C_out is None:
+        C_out = torch.empty(C0.shape, dtype=C0.dtype).pin_memory() if torch.is_tensor(C0) else np.empty_like(C0)
+    if rho_out is None:
+        rho_out = (torch.empty(X.shape[0], dtype=torch.int32).pin_memory() if torch.is_tensor(X)
+                   else np.empty(X.shape[0], np.int32))
+    data = make_data(X)
+    p = default_params(**params)
+    info = kmeans_info()
+    _check(ctx, load().kmeans_solve_host(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0),
+                                         ctypes.byref(p), _ptr(C_out), _ptr(rho_out), ctypes.byref(info)))
+    return C_out, rho_out, info.as_dict()
+
+
+def exported_symbols():
+    """Names of the C entry points declared in include/kmeans_aa.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(_build.PKG), "include", "kmeans_aa.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"\b(kmeans_[a-z_]+)\s*\(", txt)))

@@ -1,0 +1,686 @@
+// C ABI of libkmeans_aa (declared in include/kmeans_aa.h): context, workspace, the standalone
+// assignment / update / energy calls, and the solver, which runs every iteration of Lloyd or
+// Algorithm 1 inside one CUDA graph:
+//
+//   prologue : k_prep -> pass(INIT: P^0 = Assign(C^0)) -> k_fin(INIT: G^0, F^0) -> k_mix(INIT: C^1)
+//   while    : pass(TRIAL) -> pass(REVERT, exits at once unless the safeguard fired)
+//              -> k_fin(update, history, Gram, theta) -> k_mix(C^{t+1}; ends the loop when done)
+//   epilogue : pass(EPI: energy if stopped at max_iter) -> k_epi(results, info)
+//
+// All per-iteration decisions stay on the device; the host waits once per solve.
+#include "km_internal.cuh"
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+using namespace km;
+
+namespace {
+
+struct GraphKey {
+    const void* X;
+    const void* Xb;
+    int64_t N;
+    int d, K, prec;
+    const void* C0;
+    void* C_out;
+    int32_t* rho_out;
+    kmeans_params p;
+    void* arena;
+    size_t arena_bytes;
+};
+
+struct Plan {
+    // offsets into the arena
+    size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
+    size_t pS, pCnt, pE, pNch, pResc, pBad, pDots, counter, info;
+    size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
+    size_t total;
+    int nb, nfin, KB, Kpad, DP;
+    size_t smem;
+};
+
+}  // namespace
+
+struct kmeans_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    size_t budget = 0;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    int nsm = 0;
+    std::string err;
+    bool have_graph = false;
+    GraphKey key{};
+    cudaGraphExec_t exec = nullptr;
+    void* h_info = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::mutex mu;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+kmeans_status fail(kmeans_ctx* c, kmeans_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+kmeans_status cuda_fail(kmeans_ctx* c, cudaError_t e, const char* where)
+{
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, KM_ECUDA, buf);
+}
+
+#define KM_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+kmeans_status check_data(kmeans_ctx* ctx, const kmeans_data* X, int K, bool need_bf16)
+{
+    if (!X || !X->X) return fail(ctx, KM_EINVAL, "X is NULL");
+    if (X->N < 1 || X->d < 1 || X->d > 4096) return fail(ctx, KM_EINVAL, "need N >= 1 and 1 <= d <= 4096");
+    if (K < 1 || (int64_t)K > X->N) return fail(ctx, KM_EINVAL, "need 1 <= K <= N");
+    if (X->prec != KM_F64 && X->prec != KM_F32 && X->prec != KM_BF16_F32)
+        return fail(ctx, KM_EINVAL, "unknown precision");
+    if (X->prec == KM_BF16_F32 && need_bf16 && !X->X_bf16) return fail(ctx, KM_EINVAL, "X_bf16 is NULL");
+    return KM_OK;
+}
+
+int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem)
+{
+    int per_sm = (int)((200 * 1024) / (smem + 2048));
+    if (per_sm > 2) per_sm = 2;           // register-limited: 256 threads x ~128 registers
+    if (per_sm < 1) per_sm = 1;
+    int64_t nb = (int64_t)ctx->nsm * per_sm;
+    const int64_t need = (N + LOWD_THREADS - 1) / LOWD_THREADS;
+    if (nb > need) nb = need;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+// Workspace layout of one problem shape (bins = fused per-block update partials).
+kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
+                        Plan& P, bool bins = true)
+{
+    if (d > 16) return fail(ctx, KM_EINVAL, "this build supports d <= 16");
+    const bool f32 = prec != KM_F64;
+    const size_t esz = f32 ? 4 : 8;
+    P.DP = pass_lowd_dp(d);
+    P.Kpad = (K + CH - 1) / CH * CH;
+    P.smem = pass_lowd_smem(prec, d, K, P.Kpad, bins);
+    if (P.smem > 200 * 1024)
+        return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
+    P.nb = pass_blocks(ctx, N, P.smem);
+    P.nfin = fin_blocks(K, d, &P.KB);
+    const size_t n = (size_t)K * d;
+    const int mm = m_max > 0 ? m_max : 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
+    P.counter = take(256);          // fixed offset 0 for every plan; zeroed at the start of every call
+    P.st = take(sizeof(SolveState));
+    P.rhoA = take((size_t)N * 4);
+    P.rhoB = take((size_t)N * 4);
+    P.C64 = take(n * 8);
+    P.CAU = take(n * 8);
+    P.Fprev = take(n * 8);
+    P.dF = take((size_t)mm * n * 8);
+    P.dG = take((size_t)mm * n * 8);
+    P.cpk0 = take((size_t)P.Kpad * P.DP * 4);
+    P.cpk1 = take((size_t)P.Kpad * P.DP * 4);
+    P.c32_0 = take(n * 4);
+    P.c32_1 = take(n * 4);
+    P.origin = take(64 * 4);
+    P.pS = take((size_t)P.nb * n * esz);
+    P.pCnt = take((size_t)P.nb * K * 4);
+    P.pE = take((size_t)P.nb * 8);
+    P.pNch = take((size_t)P.nb * 8);
+    P.pResc = take((size_t)P.nb * 8);
+    P.pBad = take((size_t)P.nb * 4);
+    P.pDots = take((size_t)P.nfin * DOTS * 8);
+    P.info = take(256);
+    if (host_copies) {
+        P.hX = take((size_t)N * d * esz);
+        P.hXb = 0;
+        P.hC0 = take(n * esz);
+        P.hCout = take(n * esz);
+        P.hRho = take((size_t)N * 4);
+    } else {
+        P.hX = P.hXb = P.hC0 = P.hCout = P.hRho = 0;
+    }
+    P.total = o;
+    return KM_OK;
+}
+
+kmeans_status ensure_arena(kmeans_ctx* ctx, size_t bytes)
+{
+    if (ctx->arena && ctx->arena_bytes >= bytes) return KM_OK;
+    if (ctx->budget && bytes > ctx->budget) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "workspace of %zu bytes exceeds the HBM budget of %zu bytes", bytes, ctx->budget);
+        return fail(ctx, KM_ENOMEM, buf);
+    }
+    if (ctx->have_graph) {
+        cudaGraphExecDestroy(ctx->exec);
+        ctx->have_graph = false;
+    }
+    if (ctx->arena) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
+    ctx->arena = p;
+    ctx->arena_bytes = bytes;
+    return KM_OK;
+}
+
+template <typename T>
+T* at(kmeans_ctx* ctx, size_t off)
+{
+    return reinterpret_cast<T*>(static_cast<char*>(ctx->arena) + off);
+}
+
+PassArgs base_pass(kmeans_ctx* ctx, const Plan& P, const void* X, int64_t N, int K, int prec)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.N = N;
+    a.K = K;
+    a.Kpad = P.Kpad;
+    a.cpk[0] = at<float>(ctx, P.cpk0);
+    a.cpk[1] = at<float>(ctx, P.cpk1);
+    a.c32[0] = at<float>(ctx, P.c32_0);
+    a.c32[1] = at<float>(ctx, P.c32_1);
+    a.c64[0] = at<double>(ctx, P.C64);
+    a.c64[1] = at<double>(ctx, P.CAU);
+    a.origin = at<float>(ctx, P.origin);
+    a.rho[0] = at<int32_t>(ctx, P.rhoA);
+    a.rho[1] = at<int32_t>(ctx, P.rhoB);
+    a.pS = at<void>(ctx, P.pS);
+    a.pCnt = at<int32_t>(ctx, P.pCnt);
+    a.pE = at<double>(ctx, P.pE);
+    a.pNch = at<long long>(ctx, P.pNch);
+    a.pResc = at<long long>(ctx, P.pResc);
+    a.pBad = at<int>(ctx, P.pBad);
+    a.counter = at<unsigned int>(ctx, P.counter);
+    a.st = at<SolveState>(ctx, P.st);
+    (void)prec;
+    return a;
+}
+
+// First-order rounding-error bound of the FP32 score ||c'||^2 - 2 x'.c' (u = 2^-24), with a 1%
+// allowance for second-order terms:  D FMAs on partial sums <= ||c'||^2 + 2|x'||c'|, the rounding of
+// ||c'||^2, of c' = fl(c - o) and of x' = fl(x - o):
+//   |err| <= u * ((D + 3) max|c'|^2 + (2D + 4) |x'| max|c'|).
+void set_bound(PassArgs& a, int d)
+{
+    const double u = 5.9604644775390625e-8;
+    a.bound_coef = (float)(1.01 * (d + 3) * u);
+    a.bound_coef2 = (float)(1.01 * (2 * d + 4) * u);
+}
+
+kmeans_status pack_user_centroids(kmeans_ctx* ctx, const Plan& P, const void* C, int K, int d, int prec)
+{
+    KM_CUDA(launch_prep(C, prec == KM_F64, K, d, P.Kpad, P.DP, at<double>(ctx, P.C64), at<float>(ctx, P.origin),
+                        at<float>(ctx, P.cpk0), at<float>(ctx, P.cpk1), at<float>(ctx, P.c32_0),
+                        at<SolveState>(ctx, P.st), 0, 0, ctx->stream));
+    return KM_OK;
+}
+
+kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, const void* C0,
+                           const kmeans_params& p, void* C_out, int32_t* rho_out)
+{
+    const int d = X->d, prec = X->prec;
+    const int64_t N = X->N;
+    const bool f64 = prec == KM_F64;
+    const int m_max = p.lloyd_only ? 0 : p.m_max;
+    SolveState* st = at<SolveState>(ctx, P.st);
+    const int64_t thr = p.tol > 0 ? (int64_t)(p.tol * (double)N) : 0;
+
+    PassArgs pa = base_pass(ctx, P, X->X, N, K, prec);
+    set_bound(pa, d);
+    pa.m_max = m_max;
+    pa.max_iter = p.max_iter;
+    pa.lloyd_only = p.lloyd_only;
+    pa.eps1 = p.eps1;
+    pa.eps2 = p.eps2;
+    pa.thr = thr;
+
+    FinArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.K = K;
+    fa.d = d;
+    fa.nb = P.nb;
+    fa.part_f64 = f64;
+    fa.pS = at<void>(ctx, P.pS);
+    fa.pCnt = at<int32_t>(ctx, P.pCnt);
+    fa.KB = P.KB;
+    fa.C64 = at<double>(ctx, P.C64);
+    fa.CAU = at<double>(ctx, P.CAU);
+    fa.Fprev = at<double>(ctx, P.Fprev);
+    fa.dF = at<double>(ctx, P.dF);
+    fa.dG = at<double>(ctx, P.dG);
+    fa.pDots = at<double>(ctx, P.pDots);
+    fa.st = st;
+    fa.m_max = m_max;
+    fa.max_iter = p.max_iter;
+    fa.lloyd_only = p.lloyd_only;
+    fa.rank_tol = p.rank_tol;
+
+    MixArgs ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.K = K;
+    ma.d = d;
+    ma.Kpad = P.Kpad;
+    ma.DP = P.DP;
+    ma.fp32_path = !f64;
+    ma.C64 = at<double>(ctx, P.C64);
+    ma.CAU = at<double>(ctx, P.CAU);
+    ma.dG = at<double>(ctx, P.dG);
+    ma.m_max = m_max > 0 ? m_max : 1;
+    ma.origin = at<float>(ctx, P.origin);
+    ma.cpk[0] = at<float>(ctx, P.cpk0);
+    ma.cpk[1] = at<float>(ctx, P.cpk1);
+    ma.c32[0] = at<float>(ctx, P.c32_0);
+    ma.c32[1] = at<float>(ctx, P.c32_1);
+    ma.st = st;
+
+    cudaGraph_t g = nullptr, gp = nullptr, ge = nullptr;
+    cudaGraphConditionalHandle h;
+    KM_CUDA(cudaGraphCreate(&g, 0));
+    KM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+
+    // prologue
+    KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = cudaMemsetAsync(pa.counter, 0, 256, ctx->cap);
+        if (e == cudaSuccess)
+            e = launch_prep(C0, f64, K, d, P.Kpad, P.DP, ma.C64, at<float>(ctx, P.origin), ma.cpk[0],
+                                    ma.cpk[1], ma.c32[0], st, p.m_init, m_max, ctx->cap);
+        PassArgs a = pa;
+        a.mode = MODE_INIT;
+        a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
+        if (e == cudaSuccess) e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
+        FinArgs f = fa;
+        f.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_fin(f, P.nfin, ctx->cap);
+        MixArgs m = ma;
+        m.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_mix_full(m, 0, h, p.max_iter, ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &gp);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "prologue capture");
+    }
+    cudaGraphNode_t np, nc, ne;
+    KM_CUDA(cudaGraphAddChildGraphNode(&np, g, nullptr, 0, gp));
+
+    // while loop
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    KM_CUDA(cudaGraphAddNode(&nc, g, &np, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    KM_CUDA(cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        PassArgs a = pa;
+        a.mode = MODE_TRIAL;
+        a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
+        cudaError_t e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
+        a.mode = MODE_REVERT;
+        if (e == cudaSuccess) e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
+        FinArgs f = fa;
+        f.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_fin(f, P.nfin, ctx->cap);
+        MixArgs m = ma;
+        m.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_mix_full(m, 1, h, p.max_iter, ctx->cap);
+        cudaGraph_t bout = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &bout);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "loop body launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "loop body capture");
+    }
+
+    // epilogue
+    KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    {
+        PassArgs a = pa;
+        a.mode = MODE_EPI;
+        a.flags = F_ENERGY;
+        cudaError_t e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
+        if (e == cudaSuccess)
+            e = launch_epi(f64, st, ma.C64, ma.CAU, C_out, (size_t)K * d, at<int32_t>(ctx, P.rhoA),
+                           at<int32_t>(ctx, P.rhoB), rho_out, N, at<void>(ctx, P.info), ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &ge);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "epilogue launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "epilogue capture");
+    }
+    KM_CUDA(cudaGraphAddChildGraphNode(&ne, g, &nc, 1, ge));
+    cudaGraphExec_t exec;
+    KM_CUDA(cudaGraphInstantiate(&exec, g, 0));
+    cudaGraphDestroy(gp);
+    cudaGraphDestroy(ge);
+    cudaGraphDestroy(g);
+    if (ctx->have_graph) cudaGraphExecDestroy(ctx->exec);
+    ctx->exec = exec;
+    ctx->have_graph = true;
+    return KM_OK;
+}
+
+struct DevInfoH {
+    int iters, accepted, rejected, passes, converged, m_final, status, pad;
+    double E;
+    long long rescored;
+};
+
+kmeans_status validate_params(kmeans_ctx* ctx, const kmeans_params& p)
+{
+    if (p.m_max < 0 || p.m_max > MMAX) return fail(ctx, KM_EINVAL, "m_max must be in [0, 32]");
+    if (p.max_iter < 1) return fail(ctx, KM_EINVAL, "max_iter must be >= 1");
+    if (!(p.tol >= 0.0)) return fail(ctx, KM_EINVAL, "tol must be >= 0");
+    if (!(p.rank_tol >= 0.0)) return fail(ctx, KM_EINVAL, "rank_tol must be >= 0");
+    return KM_OK;
+}
+
+kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const void* C0,
+                           const kmeans_params& p, void* C_out, int32_t* rho_out, kmeans_info* info,
+                           const Plan& P)
+{
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.X = X->X;
+    key.Xb = X->X_bf16;
+    key.N = X->N;
+    key.d = X->d;
+    key.K = K;
+    key.prec = X->prec;
+    key.C0 = C0;
+    key.C_out = C_out;
+    key.rho_out = rho_out;
+    key.p = p;
+    key.arena = ctx->arena;
+    key.arena_bytes = ctx->arena_bytes;
+    if (!ctx->have_graph || memcmp(&key, &ctx->key, sizeof(key)) != 0) {
+        kmeans_status s = record_graph(ctx, P, X, K, C0, p, C_out, rho_out);
+        if (s != KM_OK) return s;
+        ctx->key = key;
+    }
+    KM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+    KM_CUDA(cudaGraphLaunch(ctx->exec, ctx->stream));
+    KM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+    KM_CUDA(cudaMemcpyAsync(ctx->h_info, at<void>(ctx, P.info), sizeof(DevInfoH), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    KM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const DevInfoH* di = reinterpret_cast<const DevInfoH*>(ctx->h_info);
+    if (info) {
+        info->iters = di->iters;
+        info->accepted = di->accepted;
+        info->rejected = di->rejected;
+        info->assign_passes = di->passes;
+        info->converged = di->converged;
+        info->m_final = di->m_final;
+        info->E = di->E;
+        info->rescored_rows = di->rescored;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        info->device_ms = ms;
+    }
+    if (di->status == KM_ENONFINITE) return fail(ctx, KM_ENONFINITE, "X contains NaN or Inf");
+    if (di->status == KM_ETIMEOUT) return fail(ctx, KM_ETIMEOUT, "iteration guard tripped");
+    return KM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void kmeans_default_params(kmeans_params* p)
+{
+    if (!p) return;
+    p->m_max = 10;
+    p->m_init = 2;
+    p->max_iter = 1000;
+    p->lloyd_only = 0;
+    p->eps1 = 0.02;
+    p->eps2 = 0.5;
+    p->tol = 0.0;
+    p->rank_tol = 1e-6;
+}
+
+const char* kmeans_status_string(kmeans_status s)
+{
+    switch (s) {
+        case KM_OK: return "KM_OK";
+        case KM_EINVAL: return "KM_EINVAL";
+        case KM_ENOMEM: return "KM_ENOMEM";
+        case KM_ECUDA: return "KM_ECUDA";
+        case KM_ETIMEOUT: return "KM_ETIMEOUT";
+        case KM_ENONFINITE: return "KM_ENONFINITE";
+        case KM_EBUSY: return "KM_EBUSY";
+    }
+    return "KM_UNKNOWN";
+}
+
+const char* kmeans_last_error(const kmeans_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "";
+}
+
+kmeans_status kmeans_create(kmeans_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
+{
+    if (!out) return KM_EINVAL;
+    *out = nullptr;
+    kmeans_ctx* ctx = new kmeans_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc(&ctx->h_info, 256, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return KM_ECUDA;
+    }
+    *out = ctx;
+    return KM_OK;
+}
+
+kmeans_status kmeans_destroy(kmeans_ctx* ctx)
+{
+    if (!ctx) return KM_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->have_graph) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->h_info) cudaFreeHost(ctx->h_info);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+    return KM_OK;
+}
+
+kmeans_status kmeans_set_stream(kmeans_ctx* ctx, void* cuda_stream)
+{
+    if (!ctx) return KM_EINVAL;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return KM_OK;
+}
+
+size_t kmeans_workspace_bytes(const kmeans_ctx* ctx)
+{
+    return ctx ? ctx->arena_bytes : 0;
+}
+
+kmeans_status kmeans_assign(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K, int32_t* rho,
+                            const int32_t* rho_prev, int64_t* n_changed, void* dmin)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, X, K, true);
+    if (s != KM_OK) return s;
+    if (!C || !rho) return fail(ctx, KM_EINVAL, "C and rho must not be NULL");
+    if (n_changed && !rho_prev) return fail(ctx, KM_EINVAL, "n_changed needs rho_prev");
+    if (X->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    Plan P;
+    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, 0, false, P, false)) != KM_OK) return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    if (X->prec != KM_F64 && (s = pack_user_centroids(ctx, P, C, K, X->d, X->prec)) != KM_OK) return s;
+    PassArgs a = base_pass(ctx, P, X->X, X->N, K, X->prec);
+    a.mode = MODE_STANDALONE;
+    a.flags = F_ASSIGN | (n_changed ? F_CHANGED : 0) | (dmin ? F_DMIN : 0);
+    set_bound(a, X->d);
+    if (X->prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C);
+    a.rho[0] = rho;
+    a.rho_prev = rho_prev;
+    a.out_nch = reinterpret_cast<long long*>(n_changed);
+    a.dmin = dmin;
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    KM_CUDA(launch_pass_lowd(a, X->prec, X->d, P.nb, ctx->stream));   // partials are sized for P.nb
+    return KM_OK;
+}
+
+kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K, const int32_t* rho,
+                            double* E)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, X, K, false);
+    if (s != KM_OK) return s;
+    if (!C || !rho || !E) return fail(ctx, KM_EINVAL, "C, rho and E must not be NULL");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    const int prec = X->prec == KM_F64 ? KM_F64 : KM_F32;
+    Plan P;
+    if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P, false)) != KM_OK) return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    if (prec != KM_F64 && (s = pack_user_centroids(ctx, P, C, K, X->d, prec)) != KM_OK) return s;
+    PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
+    a.mode = MODE_STANDALONE;
+    a.flags = F_ENERGY;
+    if (prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C);
+    a.rho_in = rho;
+    a.out_E = E;
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    KM_CUDA(launch_pass_lowd(a, prec, X->d, P.nb, ctx->stream));   // partials are sized for P.nb
+    return KM_OK;
+}
+
+kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t* rho, int32_t K,
+                            const void* C_prev, void* C_out, int64_t* counts)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, X, K, false);
+    if (s != KM_OK) return s;
+    if (!rho || !C_prev || !C_out) return fail(ctx, KM_EINVAL, "rho, C_prev and C_out must not be NULL");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    const int prec = X->prec == KM_F64 ? KM_F64 : KM_F32;
+    Plan P;
+    if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P)) != KM_OK) return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    if (prec != KM_F64 && (s = pack_user_centroids(ctx, P, C_prev, K, X->d, prec)) != KM_OK) return s;
+    PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
+    a.mode = MODE_STANDALONE;
+    a.flags = F_BINS;
+    if (prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C_prev);
+    a.rho_in = rho;
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    KM_CUDA(launch_pass_lowd(a, prec, X->d, P.nb, ctx->stream));
+    FinArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = MODE_STANDALONE;
+    f.K = K;
+    f.d = X->d;
+    f.nb = P.nb;
+    f.part_f64 = prec == KM_F64;
+    f.pS = a.pS;
+    f.pCnt = a.pCnt;
+    f.KB = P.KB;
+    f.C_ref = C_prev;
+    f.C_out = C_out;
+    f.out_f64 = prec == KM_F64;
+    f.counts = counts;
+    f.st = a.st;
+    KM_CUDA(launch_fin(f, P.nfin, ctx->stream));
+    return KM_OK;
+}
+
+kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const void* C0,
+                           const kmeans_params* params, void* C_out, int32_t* rho_out, kmeans_info* info)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, X, K, true);
+    if (s != KM_OK) return s;
+    if (!C0 || !C_out || !rho_out) return fail(ctx, KM_EINVAL, "C0, C_out and rho_out must not be NULL");
+    kmeans_params p;
+    if (params) p = *params; else kmeans_default_params(&p);
+    if ((s = validate_params(ctx, p)) != KM_OK) return s;
+    if (X->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    Plan P;
+    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P)) != KM_OK) return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    return solve_device(ctx, X, K, C0, p, C_out, rho_out, info, P);
+}
+
+kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t K, const void* C0_host,
+                                const kmeans_params* params, void* C_out_host, int32_t* rho_out_host,
+                                kmeans_info* info)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, Xh, K, true);
+    if (s != KM_OK) return s;
+    if (!C0_host || !C_out_host || !rho_out_host) return fail(ctx, KM_EINVAL, "NULL host buffer");
+    kmeans_params p;
+    if (params) p = *params; else kmeans_default_params(&p);
+    if ((s = validate_params(ctx, p)) != KM_OK) return s;
+    if (Xh->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    Plan P;
+    if ((s = make_plan(ctx, Xh->N, Xh->d, K, Xh->prec, p.lloyd_only ? 0 : p.m_max, true, P)) != KM_OK) return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    const size_t esz = Xh->prec == KM_F64 ? 8 : 4;
+    const size_t n = (size_t)K * Xh->d;
+    KM_CUDA(cudaMemcpyAsync(at<void>(ctx, P.hX), Xh->X, (size_t)Xh->N * Xh->d * esz, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    KM_CUDA(cudaMemcpyAsync(at<void>(ctx, P.hC0), C0_host, n * esz, cudaMemcpyHostToDevice, ctx->stream));
+    kmeans_data Xd = *Xh;
+    Xd.X = at<void>(ctx, P.hX);
+    Xd.X_bf16 = nullptr;
+    s = solve_device(ctx, &Xd, K, at<void>(ctx, P.hC0), p, at<void>(ctx, P.hCout), at<int32_t>(ctx, P.hRho),
+                     info, P);
+    if (s != KM_OK && s != KM_ENONFINITE) return s;
+    KM_CUDA(cudaMemcpyAsync(C_out_host, at<void>(ctx, P.hCout), n * esz, cudaMemcpyDeviceToHost, ctx->stream));
+    KM_CUDA(cudaMemcpyAsync(rho_out_host, at<void>(ctx, P.hRho), (size_t)Xh->N * 4, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    KM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return s;
+}
+
+}  // extern "C"

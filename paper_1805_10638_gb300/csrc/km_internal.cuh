@@ -1,0 +1,187 @@
+// Internal declarations shared by the CUDA translation units of libkmeans_aa.
+//
+// Data layout in HBM (one solve):
+//   X [N,d] (caller)            rho ping-pong [2][N] int32      C^t, C_AU, F^{t-1} [K*d] f64
+//   dF / dG rings [m_max][K*d] f64 (newest difference at ring_head)
+//   packed scoring centroids (FP32 path): [Kpad][DP] f32 = (-2 c'_0 .. -2 c'_{D-1}, ||c'||^2, 0..)
+//     with c' = fl32(c - o), o an origin near the data, pad rows (a = 0, ||c'||^2 = +inf)
+//   uncentred FP32 centroids [K][D] for the direct-form residual and rescoring
+//   per-block partials of one assignment pass: residual sums [nb][K][D], counts [nb][K],
+//     energy [nb] f64, changed [nb], rescored [nb]
+//   SolveState: controller scalars, the FP64 Gram matrix of the dF ring, theta.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/kmeans_aa.h"
+
+namespace km {
+
+constexpr int MMAX = 32;            // largest supported m_max (history ring length)
+constexpr int CH = 8;               // centroids per argmin chunk in the low-d FP32 kernel
+constexpr int LOWD_THREADS = 256;   // threads per block of the low-d pass kernel
+constexpr int FIN_THREADS = 256;    // threads per block of the update/finalize kernel
+constexpr int DOTS = 2 * MMAX;      // per-block dot partials: Gram row + right-hand side
+
+// Pass kinds of the assignment kernel.
+enum PassMode : int {
+    MODE_STANDALONE = 0,   // kmeans_assign / kmeans_energy / kmeans_update building blocks
+    MODE_INIT = 1,         // P^0 = Assign(C^0)
+    MODE_TRIAL = 2,        // P^t = Assign(C^t), then the controller (Algorithm 1 head)
+    MODE_REVERT = 3,       // only if the controller reverted: P^t = Assign(C_AU)
+    MODE_EPI = 4           // after the loop, if it stopped at max_iter: E(P^t, G^t)
+};
+
+enum PassFlags : int {
+    F_ASSIGN = 1,     // compute rho (else read rho from rho_in)
+    F_BINS = 2,       // accumulate per-cluster residual sums and counts
+    F_ENERGY = 4,     // accumulate the energy
+    F_CHANGED = 8,    // count rho != rho_prev
+    F_DMIN = 16,      // write the per-row squared distance
+    F_CHECK = 32      // flag non-finite samples
+};
+
+// Controller and Anderson state of one solve (device resident).
+struct SolveState {
+    int t;            // current loop pass (Algorithm 1's t), 1-based
+    int m;            // current m (dynamic)
+    int m_t;          // history length used in the last least-squares solve
+    int rank;         // columns kept by the last least-squares solve
+    int from_lloyd;   // 1 if C^t is a plain Lloyd iterate (no acceleration)
+    int revert;       // 1 if the current pass reverted to C_AU
+    int done;
+    int converged;
+    int accepted;
+    int rejected;
+    int passes;       // assignment passes so far
+    int status;       // kmeans_status of the solve
+    int ring_count;   // valid differences in the rings
+    int ring_head;    // slot of the newest difference
+    int cur;          // which rho buffer holds P^t
+    int final_src;    // 0: result is C^t (C64), 1: result is C_AU
+    long long n_changed;
+    long long rescored;
+    double E_prev;    // stored E^{t-1}
+    double E_prev2;   // stored E^{t-2}
+    double E_trial;   // E(P^t, C^t) of the proposed iterate
+    double E_cur;     // stored E^t (after any revert)
+    double E_final;
+    double gram[MMAX * MMAX];
+    double bvec[MMAX];
+    double theta[MMAX];
+    unsigned int ctr_pass;   // last-block counters (reset by the last block)
+    unsigned int ctr_fin;
+    unsigned int ctr_aux;
+    unsigned int pad;
+};
+
+// Arguments of the low-d assignment pass (by value).
+struct PassArgs {
+    const void* X;
+    int64_t N;
+    int K;
+    int Kpad;
+    int mode;
+    int flags;
+    // centroids: [0] = C^t (trial / standalone), [1] = C_AU (revert)
+    const float* cpk[2];     // FP32 path packed scoring centroids [Kpad][DP]
+    const float* c32[2];     // FP32 path uncentred [K][D]
+    const double* c64[2];    // FP64 path [K][D]
+    const float* origin;     // FP32 path origin o [D]
+    float bound_coef;        // FP32 path: score error bound = bound_coef*max|c'|^2 + bound_coef2*|x'|*max|c'|
+    float bound_coef2;
+    // assignment buffers: solver uses rho[st->cur] / rho[st->cur ^ 1]
+    int32_t* rho[2];
+    const int32_t* rho_in;   // standalone: rho to read (no F_ASSIGN) or NULL
+    const int32_t* rho_prev; // standalone: previous assignment or NULL
+    void* dmin;
+    // per-block partials
+    void* pS;
+    int32_t* pCnt;
+    double* pE;
+    long long* pNch;
+    long long* pResc;
+    int* pBad;
+    unsigned int* counter;
+    // finalize targets
+    SolveState* st;
+    long long* out_nch;
+    double* out_E;
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+    // controller parameters
+    int m_max;
+    int max_iter;
+    int lloyd_only;
+    double eps1;
+    double eps2;
+    long long thr;
+};
+
+// Arguments of the update / Anderson-finalize kernel.
+struct FinArgs {
+    int mode;             // MODE_STANDALONE (plain update) or MODE_INIT / MODE_TRIAL (solver)
+    int K;
+    int d;
+    int nb;               // number of partial blocks
+    int part_f64;         // partial sums are double (else float)
+    const void* pS;       // [nb][K][d]
+    const int32_t* pCnt;  // [nb][K]
+    int KB;               // centroids per block
+    // standalone update
+    const void* C_ref;    // reference centroids of the residuals (C_prev), element type T
+    void* C_out;          // [K][d] element type T
+    int out_f64;
+    int64_t* counts;
+    // solver
+    double* C64;          // C^t
+    double* CAU;          // C_AU (in: G^{t-1}, out: G^t)
+    double* Fprev;        // F^{t-1} -> F^t
+    double* dF;           // [m_max][K*d]
+    double* dG;
+    double* pDots;        // [gridDim][DOTS]
+    SolveState* st;
+    int m_max;
+    int max_iter;
+    int lloyd_only;
+    double rank_tol;
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+};
+
+// Arguments of the mix + pack kernel.
+struct MixArgs {
+    int mode;             // MODE_INIT or MODE_TRIAL
+    int K;
+    int d;
+    int Kpad;
+    int DP;
+    int fp32_path;
+    double* C64;
+    const double* CAU;
+    const double* dG;
+    int m_max;
+    const float* origin;
+    float* cpk[2];
+    float* c32[2];
+    SolveState* st;
+};
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s);
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins);
+int pass_lowd_dp(int d);
+cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s);
+int fin_blocks(int K, int d, int* KB);
+cudaError_t launch_mix_full(const MixArgs& a, int use_cond, cudaGraphConditionalHandle cond, int max_iter,
+                            cudaStream_t s);
+cudaError_t launch_prep(const void* C0, bool f64, int K, int d, int Kpad, int DP, double* C64,
+                        float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st, int m_init,
+                        int m_max, cudaStream_t s);
+cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const double* CAU, void* C_out,
+                       size_t n, const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N,
+                       void* info, cudaStream_t s);
+size_t devinfo_bytes();
+
+}  // namespace km

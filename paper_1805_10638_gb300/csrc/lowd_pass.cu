@@ -1,0 +1,688 @@
+// Low-dimensional assignment pass (d = 1..16) for sm_103a.
+//
+// One launch = one pass over X that computes, per sample, the assignment step (Eq. 3), and
+// fuses the O(N) work of the same pass:
+//   - the residual r_i = x_i - c_{rho_i} in the direct form, its squared norm (the energy term
+//     of Eq. 1) and per-cluster residual sums and counts (the update step, Eq. 4, written
+//     relative to the current centroids so that F = G(C) - C comes out without cancellation);
+//   - the number of samples whose assignment changed (the convergence test of Algorithm 1);
+//   - in the last block to finish, the fixed-order reduction of the per-block partials and the
+//     head of Algorithm 1 (convergence test, dynamic m, energy safeguard).
+//
+// FP32 path: distances as ||c'||^2 - 2 x'.c' with x' = x - o, c' = c - o (o = an origin near
+// the data), D FMAs per (sample, centroid) pair on CUDA cores, packed two samples per
+// fma.rn.f32x2.  The argmin over K runs in chunks of 8 centroids: a 3-input min tree gives the
+// chunk minimum, and only the best chunk index, the best value and the second-best chunk
+// minimum are tracked.  After the scan the best chunk is re-scored (bit-identical arithmetic)
+// to find the lowest index attaining the minimum and the second-best value.  If the top-2 gap
+// is within twice the rounding-error bound of the expansion the row is re-scored over all K in
+// the direct form sum (x - c)^2 (lowest index wins exact ties).
+//
+// FP64 path: direct form sum (x - c)^2 with explicitly rounded operations (no contraction),
+// ascending j with strict '<', i.e. the same arithmetic as the FP64 oracle.
+//
+// Determinism: per-cluster sums go to per-warp shared-memory bins; within a warp, lanes with the
+// same label are combined by the lowest such lane in lane order (__match_any_sync); warps are
+// combined in warp order and blocks in block order.  No floating-point atomics.
+#include "km_internal.cuh"
+
+#include <type_traits>
+
+namespace km {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int W = LOWD_THREADS / 32;
+
+__device__ __forceinline__ float fmin3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <int D>
+struct Shape {
+    static constexpr int DP = ((D + 1) + 3) / 4 * 4;      // packed stride (floats)
+    static constexpr int R = (D <= 8) ? 4 : 2;             // samples per thread in the scan
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct Layout {
+    size_t red, cpk, c, stage, bS, bC, total;
+};
+
+__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins)
+{
+    const size_t esz = f32 ? 4 : 8;
+    Layout L;
+    size_t o = 0;
+    L.red = o;   o += 64 * sizeof(double);
+    if (f32) {
+        L.cpk = o; o += al16((size_t)Kpad * DP * 4);
+        L.c = o;   o += al16((size_t)K * D * 4);
+    } else {
+        L.cpk = 0;
+        L.c = o;   o += al16((size_t)K * D * 8);
+    }
+    L.stage = o; o += al16((size_t)W * 32 * D * esz);
+    if (bins) {
+        L.bS = o; o += al16((size_t)W * K * D * esz);
+        L.bC = o; o += al16((size_t)W * K * 4);
+    } else {
+        L.bS = L.bC = 0;
+    }
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Block-wide fixed-order sums (result valid in thread 0).
+__device__ double block_sum_d(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+__device__ long long block_sum_ll(long long v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long* r = reinterpret_cast<long long*>(red);
+    v = warp_sum_ll(v);
+    __syncthreads();
+    if (lane == 0) r[warp] = v;
+    __syncthreads();
+    long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += r[w];
+    __syncthreads();
+    return s;
+}
+
+// Head of Algorithm 1 after P^t = Assign(C^t): convergence, dynamic m, safeguard.
+__device__ void controller_trial(const PassArgs& a, SolveState* st, double E, long long nch)
+{
+    st->passes += 1;
+    st->n_changed = nch;
+    st->E_trial = E;
+    const bool conv = nch <= a.thr;
+    if (conv && st->from_lloyd) {                  // converged at a Lloyd iterate: return
+        st->done = 1;
+        st->converged = 1;
+        st->E_cur = E;
+        st->E_final = E;
+        st->final_src = 0;
+        return;
+    }
+    if (!a.lloyd_only && st->t >= 3) {             // dynamic m (only once E^{t-2} is finite)
+        const double num = st->E_prev - E, den = st->E_prev2 - st->E_prev;
+        if (num < a.eps1 * den)
+            st->m = st->m - 1 > 0 ? st->m - 1 : 0;
+        else if (num > a.eps2 * den)
+            st->m = st->m + 1 < a.m_max ? st->m + 1 : a.m_max;
+    }
+    const bool reject = !st->from_lloyd && (conv || E >= st->E_prev);
+    if (reject) {
+        st->revert = 1;                            // the revert pass runs next
+    } else {
+        st->revert = 0;
+        if (!st->from_lloyd) st->accepted += 1;
+        st->E_cur = E;
+    }
+}
+
+// After the revert pass P^t = Assign(C_AU): bookkeeping and the convergence test again.
+__device__ void controller_revert(const PassArgs& a, SolveState* st, double E, long long nch)
+{
+    st->passes += 1;
+    st->rejected += 1;
+    st->n_changed = nch;
+    st->E_cur = E;
+    if (nch <= a.thr) {
+        st->done = 1;
+        st->converged = 1;
+        st->E_final = E;
+        st->final_src = 1;
+    }
+}
+
+template <int D, int R, bool PAIR>
+__device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int Kpad,
+                                            const float (&x)[R][D], float (&best)[R],
+                                            float (&sec)[R], int (&bc)[R])
+{
+    constexpr int DP = Shape<D>::DP;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        best[r] = __int_as_float(0x7f800000);
+        sec[r] = __int_as_float(0x7f800000);
+        bc[r] = 0;
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < Kpad; c0 += CH) {
+        float s[R][CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            float cv[DP];
+            const float4* p4 = reinterpret_cast<const float4*>(s_cpk + (size_t)(c0 + q) * DP);
+#pragma unroll
+            for (int v = 0; v < DP / 4; ++v) {
+                const float4 t = p4[v];
+                cv[4 * v] = t.x;
+                cv[4 * v + 1] = t.y;
+                cv[4 * v + 2] = t.z;
+                cv[4 * v + 3] = t.w;
+            }
+            if constexpr (PAIR) {
+#pragma unroll
+                for (int r = 0; r < R; r += 2) {
+                    float2 acc = make_float2(cv[D], cv[D]);
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        acc = __ffma2_rn(make_float2(cv[k], cv[k]), make_float2(x[r][k], x[r + 1][k]), acc);
+                    s[r][q] = acc.x;
+                    s[r + 1][q] = acc.y;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float acc = cv[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc = fmaf(cv[k], x[r][k], acc);
+                    s[r][q] = acc;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float m = fmin3f(fmin3f(s[r][0], s[r][1], s[r][2]), fmin3f(s[r][3], s[r][4], s[r][5]),
+                                   fminf(s[r][6], s[r][7]));
+            sec[r] = fminf(sec[r], fmaxf(best[r], m));
+            const bool p = m < best[r];
+            best[r] = p ? m : best[r];
+            bc[r] = p ? c0 : bc[r];
+        }
+    }
+}
+
+// Re-score the best chunk with the same arithmetic; lowest index attaining `best` and the
+// smallest other value in the chunk.
+template <int D>
+__device__ __forceinline__ int recover(const float* __restrict__ s_cpk, const float (&x)[D], float best,
+                                       int bc, float& second_in)
+{
+    constexpr int DP = Shape<D>::DP;
+    int jj = -1;
+    float sv = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+        const float* cp = s_cpk + (size_t)(bc + q) * DP;
+        float acc = cp[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc = fmaf(cp[k], x[k], acc);
+        if (acc == best && jj < 0)
+            jj = q;
+        else
+            sv = fminf(sv, acc);
+    }
+    second_in = sv;
+    if (jj < 0) {                 // cannot happen with identical arithmetic; force a rescore
+        second_in = -__int_as_float(0x7f800000);
+        return bc;
+    }
+    return bc + jj;
+}
+
+// Warp-cooperative FP32 direct-form rescoring of the rows some lanes flagged: for each flagged
+// row in turn, the 32 lanes split the K centroids (ascending j per lane, strict '<'), then a
+// lexicographic (distance, index) butterfly gives the lowest index attaining the minimum.
+template <int D>
+__device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int K, const float* __restrict__ X,
+                                            int64_t my_row, bool need, int idx, int lane, long long& resc)
+{
+    unsigned bal = __ballot_sync(FULL, need);
+    while (bal) {
+        const int l = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const int64_t row = __shfl_sync(FULL, my_row, l);
+        float xo[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xo[k] = X[row * D + k];
+        float bd = __int_as_float(0x7f800000);
+        int bj = K;
+        for (int j = lane; j < K; j += 32) {
+            const float* c = s_c32 + (size_t)j * D;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = xo[k] - c[k];
+                acc = fmaf(t, t, acc);
+            }
+            if (acc < bd) {
+                bd = acc;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, bd, o);
+            const int oj = __shfl_xor_sync(FULL, bj, o);
+            if (ob < bd || (ob == bd && oj < bj)) {
+                bd = ob;
+                bj = oj;
+            }
+        }
+        if (lane == l) {
+            idx = bj;
+            resc += 1;
+        }
+    }
+    return idx;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int DP = Shape<D>::DP;
+    constexpr int R = F32 ? Shape<D>::R : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    SolveState* st = a.st;
+    int which = 0;
+    int32_t* rho_out = a.rho[0];
+    const int32_t* rho_prev = a.rho_prev;
+    const int32_t* rho_in = a.rho_in;
+    if (a.mode == MODE_EPI) {
+        // energy of (P^t, G^t) when the loop stopped at max_iter
+        if (st->converged || st->status != KM_OK) return;
+        which = 1;
+        rho_in = a.rho[st->cur];
+    } else if (a.mode != MODE_STANDALONE) {
+        if (st->done) return;
+        if (a.mode == MODE_REVERT) {
+            if (!st->revert) return;
+            which = 1;
+        }
+        const int cur = st->cur;
+        rho_out = a.rho[cur];
+        rho_prev = (a.mode == MODE_INIT) ? nullptr : a.rho[cur ^ 1];
+    }
+    const int flags = a.flags;
+    const bool do_assign = flags & F_ASSIGN;
+    const bool do_bins = flags & F_BINS;
+    const int K = a.K;
+    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins);
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    T* s_stage = reinterpret_cast<T*>(smem + L.stage);
+    T* s_bS = reinterpret_cast<T*>(smem + L.bS);
+    int* s_bC = reinterpret_cast<int*>(smem + L.bC);
+    const float* s_cpk = reinterpret_cast<const float*>(smem + L.cpk);
+    const T* s_c = reinterpret_cast<const T*>(smem + L.c);
+
+    // ---- stage centroids and clear bins
+    if constexpr (F32) {
+        const float4* src = reinterpret_cast<const float4*>(a.cpk[which]);
+        float4* dst = reinterpret_cast<float4*>(smem + L.cpk);
+        for (int i = tid; i < a.Kpad * DP / 4; i += blockDim.x) dst[i] = src[i];
+        float* dc = reinterpret_cast<float*>(smem + L.c);
+        if (a.mode == MODE_EPI) {          // G^t was not packed: round it here
+            const double* g64 = a.c64[1];
+            for (int i = tid; i < K * D; i += blockDim.x) dc[i] = (float)g64[i];
+        } else {
+            const float* c32 = a.c32[which];
+            for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c32[i];
+        }
+    } else {
+        const double* c64 = a.c64[which];
+        double* dc = reinterpret_cast<double*>(smem + L.c);
+        for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c64[i];
+    }
+    if (do_bins) {
+        for (int i = tid; i < W * K * D; i += blockDim.x) s_bS[i] = T(0);
+        for (int i = tid; i < W * K; i += blockDim.x) s_bC[i] = 0;
+    }
+    __syncthreads();
+
+    // ---- the rounding-error bound of the FP32 expansion needs max|c'| over the centroids
+    float cmax = 0.f;
+    float o[D];
+    if constexpr (F32) {
+        float mx = 0.f;
+        for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, s_cpk[(size_t)j * DP + D]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+        float* fr = reinterpret_cast<float*>(s_red);
+        if (lane == 0) fr[warp] = mx;
+        __syncthreads();
+        mx = 0.f;
+        for (int w = 0; w < W; ++w) mx = fmaxf(mx, fr[w]);
+        cmax = sqrtf(mx);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < D; ++k) o[k] = a.origin[k];
+    }
+
+    const T* X = reinterpret_cast<const T*>(a.X);
+    const int64_t N = a.N;
+    const int64_t TT = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + tid;
+    const int64_t n_g = g < N ? (N - 1 - g) / TT + 1 : 0;
+    const int64_t n_min = __shfl_sync(FULL, n_g, 31);
+    const int64_t n_max = __shfl_sync(FULL, n_g, 0);
+
+    T eacc = T(0);
+    long long nch = 0, resc = 0;
+    int bad = 0;
+
+    // Everything after the label is known, for one sample (warp-uniform call).
+    auto finish = [&](int64_t row, bool valid, int idx) {
+        idx = idx < K ? idx : K - 1;           // only reachable with non-finite data
+        T res[D];
+        T e = T(0);
+        if (valid) {
+            const T* xr = X + row * D;
+            const T* c = s_c + (size_t)idx * D;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if constexpr (F32) {
+                    res[k] = xr[k] - c[k];
+                    e = fmaf(res[k], res[k], e);
+                } else {
+                    res[k] = __dsub_rn(xr[k], c[k]);
+                    e = __dadd_rn(e, __dmul_rn(res[k], res[k]));
+                }
+            }
+            if (do_assign) rho_out[row] = idx;
+            if ((flags & F_CHANGED) && rho_prev) nch += (rho_prev[row] != idx);
+            if (flags & F_DMIN) reinterpret_cast<T*>(a.dmin)[row] = e;
+            eacc += e;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) res[k] = T(0);
+        }
+        if (do_bins) {
+            const int lab = valid ? idx : -1;
+            const unsigned mm = __match_any_sync(FULL, lab);
+            T* stg = s_stage + (size_t)warp * 32 * D;
+#pragma unroll
+            for (int k = 0; k < D; ++k) stg[lane * D + k] = res[k];
+            __syncwarp();
+            if (valid && lane == __ffs(mm) - 1) {
+                T acc[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc[k] = T(0);
+                unsigned m2 = mm;
+                while (m2) {
+                    const int l = __ffs(m2) - 1;
+                    m2 &= m2 - 1;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc[k] += stg[l * D + k];
+                }
+                T* bin = s_bS + ((size_t)warp * K + lab) * D;
+#pragma unroll
+                for (int k = 0; k < D; ++k) bin[k] += acc[k];
+                s_bC[warp * K + lab] += __popc(mm);
+            }
+            __syncwarp();
+        }
+    };
+
+    auto check = [&](const T* xr) {
+        if (flags & F_CHECK) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) bad |= !isfinite(xr[k]);
+        }
+    };
+
+    int64_t kk = 0;
+    if (do_assign) {
+        if constexpr (F32) {
+            const float cA = a.bound_coef, cB = a.bound_coef2;
+            const int64_t main_iters = n_min / R;
+            for (int64_t it = 0; it < main_iters; ++it, kk += R) {
+                float x[R][D];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float* xr = X + (g + (kk + r) * TT) * D;
+                    check(xr);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) x[r][k] = xr[k] - o[k];
+                }
+                float best[R], sec[R];
+                int bc[R];
+                scan_chunks<D, R, (R % 2 == 0)>(s_cpk, a.Kpad, x, best, sec, bc);
+                int idxr[R];
+                bool need[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float xn = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xn = fmaf(x[r][k], x[r][k], xn);
+                    float sin_;
+                    idxr[r] = recover<D>(s_cpk, x[r], best[r], bc[r], sin_);
+                    const float second = fminf(sec[r], sin_);
+                    const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                    need[r] = second - best[r] <= 2.f * bnd;
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    idxr[r] = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, g + (kk + r) * TT, need[r],
+                                              idxr[r], lane, resc);
+#pragma unroll
+                for (int r = 0; r < R; ++r) finish(g + (kk + r) * TT, true, idxr[r]);
+            }
+            for (; kk < n_max; ++kk) {
+                const bool valid = kk < n_g;
+                const int64_t row = valid ? g + kk * TT : 0;
+                float x[1][D];
+                const float* xr = X + row * D;
+                if (valid) check(xr);
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[0][k] = xr[k] - o[k];
+                float best[1], sec[1];
+                int bc[1];
+                scan_chunks<D, 1, false>(s_cpk, a.Kpad, x, best, sec, bc);
+                float xn = 0.f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) xn = fmaf(x[0][k], x[0][k], xn);
+                float sin_;
+                int idx = recover<D>(s_cpk, x[0], best[0], bc[0], sin_);
+                const float second = fminf(sec[0], sin_);
+                const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                const bool need = valid && second - best[0] <= 2.f * bnd;
+                idx = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, row, need, idx, lane, resc);
+                finish(row, valid, idx);
+            }
+        } else {
+            for (; kk < n_max; ++kk) {
+                const bool valid = kk < n_g;
+                const int64_t row = valid ? g + kk * TT : 0;
+                const double* xr = X + row * D;
+                if (valid) check(xr);
+                double x[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[k] = xr[k];
+                double bd = __longlong_as_double(0x7ff0000000000000LL);
+                int bj = 0;
+                for (int j = 0; j < K; ++j) {
+                    const double* c = s_c + (size_t)j * D;
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const double t = __dsub_rn(x[k], c[k]);
+                        s = __dadd_rn(s, __dmul_rn(t, t));
+                    }
+                    if (s < bd) {
+                        bd = s;
+                        bj = j;
+                    }
+                }
+                finish(row, valid, bj);
+            }
+        }
+    } else {
+        // labels given: energy / update from rho_in
+        for (; kk < n_max; ++kk) {
+            const bool valid = kk < n_g;
+            const int64_t row = valid ? g + kk * TT : 0;
+            int idx = valid ? rho_in[row] : 0;
+            idx = (idx >= 0 && idx < K) ? idx : 0;
+            finish(row, valid, idx);
+        }
+    }
+
+    // ---- block partials
+    const double eb = block_sum_d((double)eacc, s_red);
+    const long long nb_ch = block_sum_ll(nch, s_red);
+    const long long nb_rs = block_sum_ll(resc, s_red);
+    const long long nb_bad = block_sum_ll(bad, s_red);
+    if (tid == 0) {
+        a.pE[blockIdx.x] = eb;
+        a.pNch[blockIdx.x] = nb_ch;
+        a.pResc[blockIdx.x] = nb_rs;
+        a.pBad[blockIdx.x] = (int)(nb_bad != 0);
+    }
+    if (do_bins) {
+        __syncthreads();
+        T* pS = reinterpret_cast<T*>(a.pS) + (size_t)blockIdx.x * K * D;
+        for (int e = tid; e < K * D; e += blockDim.x) {
+            T s = T(0);
+            for (int w = 0; w < W; ++w) s += s_bS[(size_t)w * K * D + e];
+            pS[e] = s;
+        }
+        int32_t* pC = a.pCnt + (size_t)blockIdx.x * K;
+        for (int j = tid; j < K; j += blockDim.x) {
+            int s = 0;
+            for (int w = 0; w < W; ++w) s += s_bC[w * K + j];
+            pC[j] = s;
+        }
+    }
+
+    // ---- last block: fixed-order reduction over blocks and the controller
+    __threadfence();
+    __syncthreads();
+    unsigned int* sflag = reinterpret_cast<unsigned int*>(s_red + 40);
+    if (tid == 0) {
+        const unsigned int prev = atomicAdd(a.counter, 1u);
+        *sflag = (prev == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (*sflag == 0u) return;
+    __threadfence();
+    double E = 0.0;
+    long long ch = 0, rs = 0, bd = 0;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+        E += __ldcg(a.pE + b);
+        ch += __ldcg(a.pNch + b);
+        rs += __ldcg(a.pResc + b);
+        bd += __ldcg(a.pBad + b);
+    }
+    E = block_sum_d(E, s_red);
+    ch = block_sum_ll(ch, s_red);
+    rs = block_sum_ll(rs, s_red);
+    bd = block_sum_ll(bd, s_red);
+    if (tid == 0) {
+        *a.counter = 0u;
+        if (a.mode == MODE_STANDALONE) {
+            if (a.out_nch) *a.out_nch = ch;
+            if (a.out_E) *a.out_E = E;
+        } else {
+            st->rescored += rs;
+            if (a.mode == MODE_EPI) {
+                st->E_final = E;
+            } else if (a.mode == MODE_INIT) {
+                st->passes += 1;
+                st->E_trial = E;
+                if (bd) {
+                    st->status = KM_ENONFINITE;
+                    st->done = 1;
+                }
+            } else if (a.mode == MODE_TRIAL) {
+                controller_trial(a, st, E, ch);
+            } else {
+                controller_revert(a, st, E, ch);
+            }
+        }
+    }
+}
+
+template <typename T, int D>
+cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
+{
+    auto kern = k_pass_lowd<T, D>;
+    static bool attr_set = false;
+    if (!attr_set || smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<nb, LOWD_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int pass_lowd_dp(int d)
+{
+    return ((d + 1) + 3) / 4 * 4;
+}
+
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins)
+{
+    return layout(prec != KM_F64, d, pass_lowd_dp(d), K, Kpad, bins).total;
+}
+
+#define KM_LOWD_CASE(DD)                                                              \
+    case DD:                                                                          \
+        return prec == KM_F64 ? launch_one<double, DD>(a, nb, smem, s)                \
+                              : launch_one<float, DD>(a, nb, smem, s);
+
+cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s)
+{
+    const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0);
+    switch (d) {
+        KM_LOWD_CASE(1)
+        KM_LOWD_CASE(2)
+        KM_LOWD_CASE(3)
+        KM_LOWD_CASE(4)
+        KM_LOWD_CASE(5)
+        KM_LOWD_CASE(6)
+        KM_LOWD_CASE(7)
+        KM_LOWD_CASE(8)
+        KM_LOWD_CASE(9)
+        KM_LOWD_CASE(10)
+        KM_LOWD_CASE(11)
+        KM_LOWD_CASE(12)
+        KM_LOWD_CASE(13)
+        KM_LOWD_CASE(14)
+        KM_LOWD_CASE(15)
+        KM_LOWD_CASE(16)
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace km

@@ -1,0 +1,257 @@
+"""GPU parity of the low-d path (d <= 16) against the FP64 oracle, through the C ABI.
+
+FP64 path: assignments, counts and iteration counts bit-exact; distances bit-exact.
+FP32 path: assignments identical wherever the oracle's top-2 gap exceeds 1e-6 * max(norms);
+centroids and energy within 1e-6 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+import paper_1805_10638_gb300 as km
+from gpu_util import check_assignment, need_gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = km.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _mixture(N, d, K, seed, dtype):
+    X = datagen.isotropic_mixture(N, d, max(K, 2), seed, dtype=dtype)
+    return X, datagen.init_centroids(X, K, seed + 1000)
+
+
+# ------------------------------------------------------------------------------ assignment
+@pytest.mark.parametrize("N,K,d", [(10_000, 10, 2), (12_345, 37, 5), (1000, 1, 3), (64, 64, 2),
+                                   (9_999, 250, 16), (1, 1, 1)])
+def test_assign_f64_bitexact(ctx, N, K, d):
+    X, C = _mixture(N, d, K, seed=N + K + d, dtype=np.float64)
+    Xd, Cd = dev(X), dev(C)
+    dmin = torch.empty(N, dtype=torch.float64, device="cuda")
+    rho = km.kmeans_assign(ctx, Xd, Cd, dmin=dmin).cpu().numpy()
+    rho_o, dmin_o, _ = oracle.assign(X, C)
+    np.testing.assert_array_equal(rho, rho_o)
+    np.testing.assert_array_equal(dmin.cpu().numpy(), dmin_o)     # same direct-form arithmetic
+
+
+@pytest.mark.parametrize("N,K,d", [(200_003, 250, 3), (50_001, 256, 16), (100_000, 13, 1),
+                                   (70_000, 64, 8), (33_333, 7, 2), (4097, 1, 3)])
+def test_assign_f32_masked_parity(ctx, N, K, d):
+    X, C = _mixture(N, d, K, seed=3 * N + K, dtype=np.float32)
+    rho = km.kmeans_assign(ctx, dev(X), dev(C)).cpu().numpy()
+    check_assignment(X, C, rho, f"N={N} K={K} d={d}")
+
+
+def test_assign_f32_lowd_2m_shape(ctx):
+    X, C0 = datagen.lowd_2m(seed=1, N=300_000)
+    rho = km.kmeans_assign(ctx, dev(X), dev(C0)).cpu().numpy()
+    check_assignment(X, C0, rho, "lowd")
+
+
+def test_assign_exact_ties_lowest_index(ctx):
+    # duplicated centroids and points exactly between integer centroids
+    X = np.array([[0.5], [1.5], [2.5], [1.0], [3.0]], np.float64)
+    C = np.array([[0.0], [1.0], [2.0], [3.0], [1.0]], np.float64)
+    rho = km.kmeans_assign(ctx, dev(X), dev(C)).cpu().numpy()
+    np.testing.assert_array_equal(rho, [0, 1, 2, 1, 3])
+    rho32 = km.kmeans_assign(ctx, dev(X, torch.float32), dev(C, torch.float32)).cpu().numpy()
+    np.testing.assert_array_equal(rho32, [0, 1, 2, 1, 3])
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_assign_n_changed_and_dmin(ctx, dtype):
+    X, C = _mixture(40_000, 3, 20, seed=5, dtype=dtype)
+    Xd = dev(X)
+    rho0 = km.kmeans_assign(ctx, Xd, dev(C))
+    C2 = C + np.asarray(0.3, dtype)
+    nch = torch.zeros((), dtype=torch.int64, device="cuda")
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    dmin = torch.empty(40_000, dtype=tdt, device="cuda")
+    rho1 = km.kmeans_assign(ctx, Xd, dev(C2), rho_prev=rho0, n_changed=nch, dmin=dmin)
+    r0, r1 = rho0.cpu().numpy(), rho1.cpu().numpy()
+    assert int(nch.item()) == int((r0 != r1).sum())
+    ref = ((X.astype(np.float64) - C2.astype(np.float64)[r1]) ** 2).sum(1)
+    np.testing.assert_allclose(dmin.cpu().numpy(), ref, rtol=1e-5 if dtype == np.float32 else 1e-15,
+                               atol=1e-6 if dtype == np.float32 else 0)
+
+
+# ---------------------------------------------------------------------------------- update
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("N,K,d", [(100_001, 50, 3), (5000, 7, 16), (2049, 300, 2)])
+def test_update_parity_deterministic(ctx, dtype, N, K, d):
+    r = np.random.default_rng(N + K)
+    X = (r.normal(size=(N, d)) * 10 + 50).astype(dtype)
+    rho = r.integers(0, max(1, K - 3), size=N).astype(np.int32)      # last clusters empty
+    Cp = r.normal(size=(K, d)).astype(dtype)
+    Xd, rd, Cd = dev(X), dev(rho), dev(Cp)
+    C1, n1 = km.kmeans_update(ctx, Xd, rd, K, Cd)
+    C2, n2 = km.kmeans_update(ctx, Xd, rd, K, Cd)
+    C1h, C2h = C1.cpu().numpy(), C2.cpu().numpy()
+    np.testing.assert_array_equal(C1h.view(np.uint8), C2h.view(np.uint8))     # run-to-run identical
+    Co, no = oracle.update(X, rho, K, Cp)
+    np.testing.assert_array_equal(n1.cpu().numpy(), no)
+    tol = 1e-13 if dtype == np.float64 else 1e-6
+    assert rel_err(C1h, Co) < tol
+    np.testing.assert_array_equal(C1h[no == 0], Cp[no == 0])
+
+
+# ---------------------------------------------------------------------------------- energy
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_energy_parity(ctx, dtype):
+    X, C = _mixture(123_457, 4, 33, seed=9, dtype=dtype)
+    rho, _, _ = oracle.assign(X, C)
+    E = km.kmeans_energy(ctx, dev(X), dev(C), dev(rho)).item()
+    Eo = oracle.energy(X, C, rho)
+    assert abs(E - Eo) / Eo < (1e-13 if dtype == np.float64 else 1e-6)
+
+
+# ----------------------------------------------------------------------------------- solve
+GOLD = json.load(open(os.path.join(HERE, "golden", "small_2d.json")))
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("method", ["lloyd", "aa"])
+def test_solve_small_2d_fp64_matches_oracle(ctx, seed, method):
+    X, C0 = datagen.small_2d(seed)
+    g = GOLD["seeds"][str(seed)][method]
+    kw = dict(lloyd_only=1) if method == "lloyd" else dict(m_max=10)
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(C0), **kw)
+    for f in ("iters", "accepted", "rejected", "assign_passes", "converged"):
+        assert info[f] == g[f], (f, info, g)
+    assert rel_err(C.cpu().numpy(), np.array(g["C"])) < 1e-12
+    assert abs(info["E"] - g["E"]) / g["E"] < 1e-12
+    # fixed point of the result (Reading R8): C = means(P), Assign(C) = P
+    Cm, _ = oracle.update(X, rho.cpu().numpy(), C.shape[0], C.cpu().numpy())
+    assert rel_err(C.cpu().numpy(), Cm) < 1e-13
+    np.testing.assert_array_equal(oracle.assign(X, C.cpu().numpy())[0], rho.cpu().numpy())
+
+
+def test_solve_m0_is_lloyd_on_gpu(ctx):
+    X, C0 = datagen.small_2d(2)
+    Xd, Cd = dev(X), dev(C0)
+    C1, r1, i1 = km.kmeans_solve(ctx, Xd, Cd, lloyd_only=1)
+    C2, r2, i2 = km.kmeans_solve(ctx, Xd, Cd, m_max=0)
+    assert torch.equal(C1, C2) and torch.equal(r1, r2)
+    assert i1["iters"] == i2["iters"] and i1["E"] == i2["E"]
+
+
+def test_solve_repeatable_bitwise(ctx):
+    X, C0 = datagen.lowd_2m(seed=2, N=150_000)
+    Xd, Cd = dev(X), dev(C0)
+    C1, r1, i1 = km.kmeans_solve(ctx, Xd, Cd)
+    C1 = C1.clone()
+    r1 = r1.clone()
+    C2, r2, i2 = km.kmeans_solve(ctx, Xd, Cd)
+    assert torch.equal(C1, C2) and torch.equal(r1, r2) and i1["iters"] == i2["iters"]
+
+
+@pytest.mark.parametrize("method", ["lloyd", "aa"])
+def test_solve_fp32_lowd_matches_oracle(ctx, method):
+    X, C0 = datagen.lowd_2m(seed=3, N=100_000, K=64)
+    kw = dict(lloyd_only=1) if method == "lloyd" else {}
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(C0), **kw)
+    Ch, rh = C.cpu().numpy(), rho.cpu().numpy()
+    assert info["converged"] == 1
+    # energy reported = energy of the returned pair
+    Eo_at = oracle.energy(X, Ch, rh)
+    assert abs(info["E"] - Eo_at) / Eo_at < 1e-6
+    # fixed point: centroids are the cluster means, and the assignment is stable
+    Cm, _ = oracle.update(X, rh, C.shape[0], Ch)
+    assert rel_err(Ch, Cm) < 1e-6
+    check_assignment(X, Ch, rh, "fixed point")
+    # Same minimum as the FP64 oracle (centroids and energy within 1e-6).  Lloyd follows the
+    # oracle's trajectory step for step; Algorithm 1 may take a different number of passes in
+    # FP32, because its accept/reject and m decisions compare energies that differ from the FP64
+    # ones in the 8th digit, but it must reach the same fixed point.
+    Co, ro, io = oracle.solve(X, C0, lloyd=(method == "lloyd"))
+    assert abs(info["E"] - io["E"]) / io["E"] < 1e-6, (info, io)
+    differ = int((rh != ro).sum())
+    if method == "lloyd":
+        assert info["iters"] == io["iters"], (info, io)
+    if differ == 0:
+        assert rel_err(Ch, Co) < 1e-6, (info, io)
+    else:
+        # a neighbouring fixed point: a handful of rows on the other side of a bisector
+        assert method == "aa" and differ < 1e-3 * X.shape[0], (differ, info, io)
+
+
+def test_solve_edge_cases(ctx):
+    X = np.random.default_rng(0).normal(size=(64, 2))
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(X))           # K = N
+    np.testing.assert_array_equal(rho.cpu().numpy(), np.arange(64))
+    assert info["E"] == 0.0 and info["iters"] == 1
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(X[:1]))       # K = 1
+    assert (rho.cpu().numpy() == 0).all()
+    np.testing.assert_allclose(C.cpu().numpy()[0], X.mean(0), rtol=1e-13)
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(X[:5]), max_iter=1)
+    assert info["iters"] == 1 and info["converged"] == 0
+    Co, ro, io = oracle.solve(X, X[:5], max_iter=1)
+    np.testing.assert_allclose(C.cpu().numpy(), Co, rtol=1e-13)
+    assert abs(info["E"] - io["E"]) <= 1e-12 * io["E"]
+
+
+def test_solve_host_matches_device(ctx):
+    X, C0 = datagen.lowd_2m(seed=4, N=50_000, K=32)
+    Cd, rd, idv = km.kmeans_solve(ctx, dev(X), dev(C0))
+    Ch, rh, ih = km.kmeans_solve_host(ctx, torch.from_numpy(X).pin_memory(), torch.from_numpy(C0).pin_memory())
+    assert torch.equal(Cd.cpu(), Ch) and torch.equal(rd.cpu(), rh)
+    assert idv["iters"] == ih["iters"]
+
+
+def test_errors(ctx):
+    X = dev(np.zeros((10, 2)))
+    with pytest.raises(km.KmeansError) as e:
+        km.kmeans_assign(ctx, X, dev(np.zeros((11, 2))))
+    assert e.value.status == 1
+    Xn = np.random.default_rng(1).normal(size=(100, 2))
+    Xn[17, 1] = np.nan
+    with pytest.raises(km.KmeansError) as e:
+        km.kmeans_solve(ctx, dev(Xn), dev(Xn[:3] * 0))
+    assert e.value.status == 5
+    small = km.Context(0, hbm_budget=1024)
+    with pytest.raises(km.KmeansError) as e:
+        km.kmeans_solve(small, dev(np.zeros((1000, 2))), dev(np.zeros((4, 2))))
+    assert e.value.status == 2
+    small.close()
+
+
+@pytest.mark.slow
+def test_solve_lowd_2m_full_size_sampled(ctx):
+    """Full-size low-d workload (N=2M, d=3, K=256) in the bench's launch configuration:
+    properties that hold at any size plus sampled rows against the oracle."""
+    X, C0 = datagen.lowd_2m(seed=0)
+    Xd = dev(X)
+    C, rho, info = km.kmeans_solve(ctx, Xd, dev(C0))
+    Ch, rh = C.cpu().numpy(), rho.cpu().numpy()
+    assert info["converged"] == 1
+    r = np.random.default_rng(0)
+    idx = np.sort(r.choice(X.shape[0], 20_000, replace=False))
+    check_assignment(X[idx], Ch, rh[idx], "sampled rows at the solution")
+    Cm, cnt = oracle.update(X, rh, Ch.shape[0], Ch)
+    assert cnt.sum() == X.shape[0]
+    assert rel_err(Ch, Cm) < 1e-6
+    Eo = oracle.energy(X, Ch, rh)
+    assert abs(info["E"] - Eo) / Eo < 1e-6
+    Cl, rl, il = km.kmeans_solve(ctx, Xd, dev(C0), lloyd_only=1)
+    assert il["converged"] == 1

@@ -1,0 +1,39 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point of the header."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_1805_10638_gb300 as km
+from paper_1805_10638_gb300 import _lib
+
+
+def test_library_exports_every_declared_symbol():
+    L = km.load()
+    names = _lib.exported_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.lib_path()], capture_output=True, text=True)
+    if out.returncode == 0:
+        defined = {ln.split()[-1] for ln in out.stdout.splitlines() if ln.strip()}
+        for n in names:
+            assert n in defined, n
+
+
+def test_defaults_and_status_strings_without_gpu():
+    p = km.default_params()
+    assert (p.m_max, p.m_init, p.max_iter, p.lloyd_only) == (10, 2, 1000, 0)
+    assert (p.eps1, p.eps2, p.tol, p.rank_tol) == (0.02, 0.5, 0.0, 1e-6)
+    L = km.load()
+    assert L.kmeans_status_string(1) == b"KM_EINVAL"
+    assert L.kmeans_status_string(5) == b"KM_ENONFINITE"
+    assert L.kmeans_last_error(None) == b""
+
+
+def test_null_arguments_rejected_before_any_cuda_call():
+    L = km.load()
+    assert L.kmeans_create(None, 0, 0, None) == _lib.KM_EINVAL
+    assert L.kmeans_destroy(None) == _lib.KM_OK
+    data = _lib.kmeans_data(None, None, 10, 2, 0)
+    assert L.kmeans_assign(None, ctypes.byref(data), None, 1, None, None, None, None) == _lib.KM_EINVAL

@@ -227,10 +227,10 @@ def run_ours(args, rank, world, local_rank):
     a1.record(stream)
     torch.cuda.synchronize()
     assign_ms = a0.elapsed_time(a1) / reps
-    ops = float(N) * K * (d + 1)              # d FMAs + 1 compare per (sample, centroid) pair
+    flops = 2.0 * N * K * d                   # the distance contraction: d FMAs per (sample, centroid)
     clock_mhz = 2070.0
-    peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
-    achieved = ops / (assign_ms * 1e-3) / 1e12
+    peak = 2.0 * SM_COUNT_NOMINAL * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    achieved = flops / (assign_ms * 1e-3) / 1e12
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -294,10 +294,11 @@ def run_ours(args, rank, world, local_rank):
             "aa_over_lloyd_speed": tot_ll / tot_aa,
             "aa_lloyd_same_energy_frac": same_E,
             "roofline": {"bound": "alu", "kernel": "k_pass_lowd<float,3> (assignment pass)",
-                         "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "assign_ms": assign_ms,
-                         "note": "ops = N*K*(d+1) FP32 lane-ops per pass; peak = 152 SMs x 128 FP32 lanes x 2070 MHz"},
+                         "note": "2*N*K*d FP32 FMA flops per pass over the launch's CUDA-event time; peak = FP32 "
+                                 "FMA pipe 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived, not measured)"},
             "e2e": {"value": world * args.steps / e2e_tot, "unit": "solves/s",
                     "h2d_bytes_per_step": int(X.nbytes + C0s[0].nbytes),
                     "d2h_bytes_per_step": int(K * d * 4 + N * 4)},

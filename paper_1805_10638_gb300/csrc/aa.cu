@@ -3,16 +3,15 @@
 // k_fin  : fixed-order reduction of the per-block residual sums and counts of a pass into the
 //          update step (Eq. 4) written as G(C) = C + F, F_j = (1/N_j) sum_{rho_i=j}(x_i - c_j)
 //          (F_j = 0 for an empty cluster, which keeps its centroid).  In the solver it also
-//          forms dF = F^t - F^{t-1} and dG = G^t - G^{t-1} (Eq. 7 / Eq. 8 differences) into the
-//          history rings and the new row of the FP64 Gram matrix of the dF columns plus the
-//          right-hand side <dF_j, F^t> (the "m inner products between (Kd)-dimensional
-//          vectors" of Section 2.1).  The last block solves the m_t x m_t least-squares system
+//          forms dF = F^t - F^{t-1} and dG = G^t - G^{t-1} (the differences of Eq. 7 / Eq. 8)
+//          into the history rings, and the new row of the FP64 Gram matrix of the dF columns
+//          plus the right-hand side <dF_j, F^t> (the "m inner products between (Kd)-dimensional
+//          vectors" of Section 2.1).  The last block solves the m_t x m_t least-squares problem
 //          through the Cholesky factor of the Gram matrix (= the R factor of the QR of dF),
-//          dropping columns from the first with R_kk <= rank_tol * R_00 on, and closes the
-//          iteration of Algorithm 1.
+//          dropping columns from the first with R_kk <= rank_tol * R_00 on, closes the iteration
+//          of Algorithm 1 and, when K*d is small, also forms the accelerated iterate.
 // k_mix  : C^{t+1} = G^t - sum_j theta_j dG_j (Eq. 8 with Algorithm 1's sign) in FP64 and the
-//          FP32 packing of C^{t+1} and G^t for the next assignment passes; the only place that
-//          ends the graph's while loop.
+//          FP32 packing of C^{t+1} and G^t for the next assignment passes (large K*d).
 // k_prep : once per solve: origin, C^0, packing, controller state.
 // k_epi  : once per solve: result centroids, assignment and info.
 #include "km_internal.cuh"
@@ -30,41 +29,103 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Solve the LS problem of Eq. 7 from the Gram matrix: columns a = 0..mt-1 are ring slots
-// slot[a] (a = 0 newest).  Cholesky M = L L^T with column truncation; returns the rank.
-__device__ int ls_from_gram(const SolveState* st, const int* slot, int mt, double rank_tol,
-                            double* theta)
+// Least squares of Eq. 7 from the Gram matrix, by one warp: columns a = 0..mt-1 are ring slots
+// (hnew - a) mod m_max (a = 0 newest).  Right-looking Cholesky M = L L^T in shared memory, lane r
+// owning row r, with 1/L_kk from rsqrt (no divisions); columns from the first with
+// L_kk <= rank_tol * L_00 on are dropped.  Forward and back substitution give theta.
+// Returns the rank (in every lane); theta[0..MMAX) in shared memory.
+__device__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
+                       double* sInv, double* sV)
 {
-    double Lm[MMAX][MMAX];
-    double y[MMAX];
+    const int lane = threadIdx.x & 31;
+    const int sr = lane < mt ? (hnew - lane + m_max) % m_max : 0;
+    for (int c = 0; c < mt; ++c) {
+        const int sc = (hnew - c + m_max) % m_max;
+        if (lane < mt) sM[lane * MMAX + c] = st->gram[sr * MMAX + sc];
+    }
+    sV[lane] = lane < mt ? st->bvec[sr] : 0.0;
+    __syncwarp();
     int rank = 0;
     double l00 = 0.0;
     for (int k = 0; k < mt; ++k) {
-        double piv = st->gram[slot[k] * MMAX + slot[k]];
-        for (int i = 0; i < k; ++i) piv -= Lm[k][i] * Lm[k][i];
-        const double lkk = piv > 0.0 ? sqrt(piv) : 0.0;
+        const double piv = sM[k * MMAX + k];
+        const double r = piv > 0.0 ? rsqrt(piv) : 0.0;
+        const double lkk = piv * r;
         if (k == 0) l00 = lkk;
-        if (l00 == 0.0 || lkk <= rank_tol * l00) break;
-        Lm[k][k] = lkk;
-        for (int r = k + 1; r < mt; ++r) {
-            double v = st->gram[slot[r] * MMAX + slot[k]];
-            for (int i = 0; i < k; ++i) v -= Lm[r][i] * Lm[k][i];
-            Lm[r][k] = v / lkk;
+        if (l00 == 0.0 || !(lkk > rank_tol * l00)) break;
+        __syncwarp();
+        if (lane > k && lane < mt) sM[lane * MMAX + k] *= r;
+        if (lane == k) {
+            sM[k * MMAX + k] = lkk;
+            sInv[k] = r;
         }
+        __syncwarp();
+        if (lane > k && lane < mt) {
+            const double lrk = sM[lane * MMAX + k];
+            for (int j = k + 1; j <= lane; ++j) sM[lane * MMAX + j] -= lrk * sM[j * MMAX + k];
+        }
+        __syncwarp();
         rank = k + 1;
     }
-    for (int k = 0; k < rank; ++k) {            // L y = b
-        double v = st->bvec[slot[k]];
-        for (int i = 0; i < k; ++i) v -= Lm[k][i] * y[i];
-        y[k] = v / Lm[k][k];
+    for (int k = 0; k < rank; ++k) {               // L y = b
+        const double yk = sV[k] * sInv[k];
+        __syncwarp();
+        if (lane == k) sV[k] = yk;
+        if (lane > k && lane < rank) sV[lane] -= sM[lane * MMAX + k] * yk;
+        __syncwarp();
     }
-    for (int k = rank - 1; k >= 0; --k) {       // L^T theta = y
-        double v = y[k];
-        for (int i = k + 1; i < rank; ++i) v -= Lm[i][k] * theta[i];
-        theta[k] = v / Lm[k][k];
+    for (int k = rank - 1; k >= 0; --k) {          // L^T theta = y
+        const double tk = sV[k] * sInv[k];
+        __syncwarp();
+        if (lane == k) sV[k] = tk;
+        if (lane < k) sV[lane] -= sM[k * MMAX + lane] * tk;
+        __syncwarp();
     }
-    for (int k = rank; k < MMAX; ++k) theta[k] = 0.0;
+    if (lane >= rank) sV[lane] = 0.0;
+    __syncwarp();
     return rank;
+}
+
+// C^{t+1}_j = G^t_j - sum_q theta_q dG_q,j for one centroid (one warp, lanes over d), written to
+// C64, and the FP32 packing of C^{t+1} (set 0) and G^t (set 1).  Reads go through L2 (__ldcg):
+// G^t and dG were written by other blocks of the same kernel when called from k_fin.
+__device__ void mix_pack_centroid(int j, int K, int d, int DP, int fp32_path, double* C64, const double* CAU,
+                                  const double* dG, const double* th, const int* sl, int rank, const float* origin,
+                                  float* const* cpk, float* const* c32)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t n = (size_t)K * d;
+    double nrm0 = 0.0, nrm1 = 0.0;
+    for (int k = lane; k < d; k += 32) {
+        const size_t i = (size_t)j * d + k;
+        const double g = __ldcg(CAU + i);
+        double dg[MMAX];
+#pragma unroll
+        for (int q = 0; q < MMAX; ++q) dg[q] = q < rank ? __ldcg(dG + (size_t)sl[q] * n + i) : 0.0;
+        double c = g;
+#pragma unroll
+        for (int q = 0; q < MMAX; ++q)
+            if (q < rank) c -= th[q] * dg[q];
+        C64[i] = c;
+        if (fp32_path) {
+            const double o = (double)origin[k];
+            const float c0 = (float)(c - o), c1 = (float)(g - o);
+            c32[0][i] = (float)c;
+            c32[1][i] = (float)g;
+            cpk[0][pk_index(j, k, DP)] = -2.f * c0;
+            cpk[1][pk_index(j, k, DP)] = -2.f * c1;
+            nrm0 += (double)c0 * (double)c0;
+            nrm1 += (double)c1 * (double)c1;
+        }
+    }
+    if (fp32_path) {
+        nrm0 = warp_sum(nrm0);
+        nrm1 = warp_sum(nrm1);
+        if (lane == 0) {
+            cpk[0][pk_index(j, d, DP)] = (float)nrm0;
+            cpk[1][pk_index(j, d, DP)] = (float)nrm1;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
@@ -72,69 +133,62 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     SolveState* st = a.st;
     const bool solver = a.mode != MODE_STANDALONE;
     if (solver && st->done) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K, d = a.d, nb = a.nb;
     const int j0 = blockIdx.x * a.KB;
     const int kb = min(a.KB, K - j0);
     const int E = kb * (d + 1);
     int split = FIN_THREADS / max(E, 1);
-    split = split < 1 ? 1 : (split > 8 ? 8 : split);
+    split = split < 1 ? 1 : (split > 32 ? 32 : split);
 
     extern __shared__ __align__(16) unsigned char smem[];
     double* s_tot = reinterpret_cast<double*>(smem);             // [E]
     double* s_dfn = s_tot + E;                                    // [kb*d]
     double* s_F = s_dfn + (size_t)kb * d;                         // [kb*d]
-    double* s_part = s_F + (size_t)kb * d;                        // [FIN_THREADS] (split > 1)
+    double* s_part = s_F + (size_t)kb * d;                        // [FIN_THREADS]
     double* s_red = s_part + FIN_THREADS;                         // [2*MMAX*8]
+    __shared__ double s_M[MMAX * MMAX];
+    __shared__ double s_inv[MMAX];
+    __shared__ double s_th[MMAX];
+    __shared__ int s_sl[MMAX];
+    __shared__ int s_rank;
+    __shared__ unsigned int s_last;
 
-    // ---- phase 1/2: sums over partial blocks in a fixed order
-    if (split > 1) {
-        for (int p = tid; p < E * split; p += blockDim.x) {
-            const int e = p / split, s = p % split;
-            double acc = 0.0;
-            if (e < kb * d) {
-                const size_t off = (size_t)j0 * d + e;
-                if (a.part_f64) {
-                    const double* pS = reinterpret_cast<const double*>(a.pS);
-                    for (int b = s; b < nb; b += split) acc += pS[(size_t)b * K * d + off];
-                } else {
-                    const float* pS = reinterpret_cast<const float*>(a.pS);
-                    for (int b = s; b < nb; b += split) acc += (double)pS[(size_t)b * K * d + off];
-                }
+    // ---- phase 1/2: sums over the partial blocks in a fixed order
+    for (int p = tid; p < E * split; p += blockDim.x) {
+        const int e = p / split, sp = p % split;
+        double acc = 0.0;
+        if (e < kb * d) {
+            const size_t off = (size_t)j0 * d + e;
+            if (a.part_f64) {
+                const double* pS = reinterpret_cast<const double*>(a.pS);
+#pragma unroll 8
+                for (int b = sp; b < nb; b += split) acc += pS[(size_t)b * K * d + off];
             } else {
-                const int j = j0 + (e - kb * d);
-                long long c = 0;
-                for (int b = s; b < nb; b += split) c += a.pCnt[(size_t)b * K + j];
-                acc = (double)c;
+                const float* pS = reinterpret_cast<const float*>(a.pS);
+#pragma unroll 8
+                for (int b = sp; b < nb; b += split) acc += (double)pS[(size_t)b * K * d + off];
             }
-            s_part[p] = acc;
+        } else {
+            const int j = j0 + (e - kb * d);
+            long long c = 0;
+#pragma unroll 8
+            for (int b = sp; b < nb; b += split) c += a.pCnt[(size_t)b * K + j];
+            acc = (double)c;
         }
-        __syncthreads();
-        for (int e = tid; e < E; e += blockDim.x) {
-            double v = 0.0;
-            for (int s = 0; s < split; ++s) v += s_part[e * split + s];
-            s_tot[e] = v;
-        }
-    } else {
-        for (int e = tid; e < E; e += blockDim.x) {
-            double acc = 0.0;
-            if (e < kb * d) {
-                const size_t off = (size_t)j0 * d + e;
-                if (a.part_f64) {
-                    const double* pS = reinterpret_cast<const double*>(a.pS);
-                    for (int b = 0; b < nb; ++b) acc += pS[(size_t)b * K * d + off];
-                } else {
-                    const float* pS = reinterpret_cast<const float*>(a.pS);
-                    for (int b = 0; b < nb; ++b) acc += (double)pS[(size_t)b * K * d + off];
-                }
-            } else {
-                const int j = j0 + (e - kb * d);
-                long long c = 0;
-                for (int b = 0; b < nb; ++b) c += a.pCnt[(size_t)b * K + j];
-                acc = (double)c;
-            }
-            s_tot[e] = acc;
-        }
+        s_part[p] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < E; e += blockDim.x) {
+        double v = 0.0;
+        for (int sp = 0; sp < split; ++sp) v += s_part[e * split + sp];
+        s_tot[e] = v;
+    }
+    __syncthreads();
+    // 1/N_j once per centroid
+    for (int e = tid; e < kb; e += blockDim.x) {
+        const double Nj = s_tot[kb * d + e];
+        s_part[e] = Nj > 0.0 ? 1.0 / Nj : 0.0;
     }
     __syncthreads();
 
@@ -142,13 +196,13 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     if (!solver) {
         for (int e = tid; e < kb * d; e += blockDim.x) {
             const size_t i = (size_t)j0 * d + e;
-            const double Nj = s_tot[kb * d + e / d];
+            const double inv = s_part[e / d];
             if (a.out_f64) {
                 const double cr = reinterpret_cast<const double*>(a.C_ref)[i];
-                reinterpret_cast<double*>(a.C_out)[i] = Nj > 0.0 ? cr + s_tot[e] / Nj : cr;
+                reinterpret_cast<double*>(a.C_out)[i] = inv > 0.0 ? cr + s_tot[e] * inv : cr;
             } else {
                 const double cr = (double)reinterpret_cast<const float*>(a.C_ref)[i];
-                reinterpret_cast<float*>(a.C_out)[i] = (float)(Nj > 0.0 ? cr + s_tot[e] / Nj : cr);
+                reinterpret_cast<float*>(a.C_out)[i] = (float)(inv > 0.0 ? cr + s_tot[e] * inv : cr);
             }
         }
         if (a.counts)
@@ -163,14 +217,13 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     const int hnew = ring ? (head + 1) % m_max : 0;
     const int nold = ring ? min(count, m_max - 1) : 0;
     const double* Ct = st->revert ? a.CAU : a.C64;
+    const size_t n = (size_t)K * d;
     for (int e = tid; e < kb * d; e += blockDim.x) {
         const size_t i = (size_t)j0 * d + e;
-        const double Nj = s_tot[kb * d + e / d];
-        const double F = Nj > 0.0 ? s_tot[e] / Nj : 0.0;
+        const double F = s_tot[e] * s_part[e / d];
         const double c = Ct[i];
         const double G = c + F;
         if (ring) {
-            const size_t n = (size_t)K * d;
             const double dfn = F - a.Fprev[i];
             const double dgn = G - a.CAU[i];
             a.dF[(size_t)hnew * n + i] = dfn;
@@ -181,30 +234,41 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
         a.Fprev[i] = F;
         a.CAU[i] = G;
     }
-    if (!ring) {
-        // no least squares: a plain Lloyd step; still close the iteration in the last block
-    }
     __syncthreads();
 
     // ---- dot partials: age 0 = the new column, age s >= 1 = slot (head - s + 1)
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nw = blockDim.x >> 5;
     const int nage = ring ? nold + 1 : 0;
     if (ring) {
-        const size_t n = (size_t)K * d;
-        for (int s = 0; s < nage; ++s) {
-            const int q = s == 0 ? hnew : (head - (s - 1) + m_max) % m_max;
-            double gv = 0.0, bv = 0.0;
-            for (int e = tid; e < kb * d; e += blockDim.x) {
-                const size_t i = (size_t)j0 * d + e;
-                const double col = s == 0 ? s_dfn[e] : a.dF[(size_t)q * n + i];
-                gv += s_dfn[e] * col;
-                bv += col * s_F[e];
+        double gv[MMAX], bv[MMAX];
+#pragma unroll
+        for (int s = 0; s < MMAX; ++s) gv[s] = bv[s] = 0.0;
+        for (int e = tid; e < kb * d; e += blockDim.x) {
+            const size_t i = (size_t)j0 * d + e;
+            const double dfn = s_dfn[e], Fe = s_F[e];
+            double col[MMAX];
+#pragma unroll
+            for (int s = 1; s < MMAX; ++s) {
+                const int q = (head - (s - 1) + m_max) % m_max;
+                col[s] = s < nage ? a.dF[(size_t)q * n + i] : 0.0;
             }
-            gv = warp_sum(gv);
-            bv = warp_sum(bv);
-            if (lane == 0) {
-                s_red[(2 * s) * 8 + warp] = gv;
-                s_red[(2 * s + 1) * 8 + warp] = bv;
+            gv[0] += dfn * dfn;
+            bv[0] += dfn * Fe;
+#pragma unroll
+            for (int s = 1; s < MMAX; ++s) {
+                gv[s] += dfn * col[s];
+                bv[s] += col[s] * Fe;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < MMAX; ++s) {
+            if (s < nage) {
+                const double g = warp_sum(gv[s]);
+                const double b = warp_sum(bv[s]);
+                if (lane == 0) {
+                    s_red[(2 * s) * 8 + warp] = g;
+                    s_red[(2 * s + 1) * 8 + warp] = b;
+                }
             }
         }
         __syncthreads();
@@ -215,10 +279,9 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
         }
     }
 
-    // ---- last block: Gram update, least squares, end of iteration
+    // ---- last block: Gram update, least squares, end of the iteration
     __threadfence();
     __syncthreads();
-    __shared__ unsigned int s_last;
     if (tid == 0) s_last = (atomicAdd(&st->ctr_fin, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
     if (!s_last) return;
@@ -226,132 +289,163 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     if (ring) {
         for (int v = tid; v < 2 * nage; v += blockDim.x) {
             double acc = 0.0;
+#pragma unroll 8
             for (int b = 0; b < (int)gridDim.x; ++b) acc += __ldcg(a.pDots + (size_t)b * DOTS + v);
             s_red[v] = acc;
         }
         __syncthreads();
-    }
-    if (tid != 0) return;
-    st->ctr_fin = 0u;
-    if (init) {
-        st->t = 1;
-        st->cur = 1;
-        st->revert = 0;
-        return;
-    }
-    int rank = 0, mt = 0;
-    if (ring) {
-        st->gram[hnew * MMAX + hnew] = s_red[0];
-        st->bvec[hnew] = s_red[1];
-        for (int s = 1; s < nage; ++s) {
-            const int q = (head - (s - 1) + m_max) % m_max;
-            st->gram[hnew * MMAX + q] = s_red[2 * s];
-            st->gram[q * MMAX + hnew] = s_red[2 * s];
-            st->bvec[q] = s_red[2 * s + 1];
+        if (tid == 0) {
+            st->gram[hnew * MMAX + hnew] = s_red[0];
+            st->bvec[hnew] = s_red[1];
+            for (int s = 1; s < nage; ++s) {
+                const int q = (head - (s - 1) + m_max) % m_max;
+                st->gram[hnew * MMAX + q] = s_red[2 * s];
+                st->gram[q * MMAX + hnew] = s_red[2 * s];
+                st->bvec[q] = s_red[2 * s + 1];
+            }
+            st->ring_head = hnew;
+            st->ring_count = min(count + 1, m_max);
         }
-        st->ring_head = hnew;
-        st->ring_count = min(count + 1, m_max);
-        mt = min(min(st->m, st->t), st->ring_count);
-        int slot[MMAX];
-        for (int k = 0; k < mt; ++k) slot[k] = (hnew - k + m_max) % m_max;
-        double th[MMAX];
-        rank = mt > 0 ? ls_from_gram(st, slot, mt, a.rank_tol, th) : 0;
-        for (int k = 0; k < MMAX; ++k) st->theta[k] = k < rank ? th[k] : 0.0;
+        __syncthreads();
+        if (warp == 0) {
+            const int mt = min(min(st->m, st->t), st->ring_count);
+            const int rank = mt > 0 ? ls_warp(st, hnew, m_max, mt, a.rank_tol, s_M, s_inv, s_th) : 0;
+            if (mt == 0) s_th[lane] = 0.0;
+            st->theta[lane] = s_th[lane];
+            s_sl[lane] = (hnew - lane + m_max) % m_max;
+            if (lane == 0) {
+                s_rank = rank;
+                st->m_t = mt;
+            }
+        }
+    } else if (tid == 0) {
+        s_rank = 0;
+        st->m_t = 0;
     }
-    st->m_t = mt;
-    st->rank = rank;
-    st->from_lloyd = rank == 0;
-    st->E_prev2 = st->E_prev;
-    st->E_prev = st->E_cur;
-    if (st->t >= a.max_iter) {
-        st->done = 1;
-        st->converged = 0;
-        st->final_src = 1;          // (P^t, G^t)
+    __syncthreads();
+    const int rank = s_rank;
+    bool stop = false;
+    if (init) {
+        if (tid == 0) {
+            st->t = 1;
+            st->cur = 1;
+            st->revert = 0;
+        }
     } else {
-        st->t += 1;
-        st->cur ^= 1;
-        st->revert = 0;
+        stop = st->t >= a.max_iter;
+        __syncthreads();
+        if (tid == 0) {
+            st->ctr_fin = 0u;
+            st->rank = rank;
+            st->from_lloyd = rank == 0;
+            st->E_prev2 = st->E_prev;
+            st->E_prev = st->E_cur;
+            if (stop) {
+                st->done = 1;                // (P^t, G^t)
+                st->converged = 0;
+                st->final_src = 1;
+                if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+            } else {
+                st->t += 1;
+                st->cur ^= 1;
+                st->revert = 0;
+            }
+        }
+    }
+    if (init && tid == 0) st->ctr_fin = 0u;
+    // ---- small K*d: the accelerated iterate here, saving a launch.  Element-parallel (one
+    // element per thread, FP64), then ||c'||^2 per centroid from the packed FP32 values.
+    if (a.fuse_mix && !stop) {
+        const int rk = init ? 0 : rank;
+        for (size_t i = tid; i < n; i += blockDim.x) {
+            const int j = (int)(i / d), k = (int)(i % d);
+            const double g = __ldcg(a.CAU + i);
+            double dg[MMAX];
+#pragma unroll
+            for (int q = 0; q < MMAX; ++q) dg[q] = q < rk ? __ldcg(a.dG + (size_t)s_sl[q] * n + i) : 0.0;
+            double c = g;
+#pragma unroll
+            for (int q = 0; q < MMAX; ++q)
+                if (q < rk) c -= s_th[q] * dg[q];
+            a.C64[i] = c;
+            if (a.fp32_path) {
+                const double o = (double)a.origin[k];
+                a.c32[0][i] = (float)c;
+                a.c32[1][i] = (float)g;
+                a.cpk[0][pk_index(j, k, a.DP)] = -2.f * (float)(c - o);
+                a.cpk[1][pk_index(j, k, a.DP)] = -2.f * (float)(g - o);
+            }
+        }
+        if (a.fp32_path) {
+            __syncthreads();
+            for (int j = tid; j < K; j += blockDim.x) {
+                double n0 = 0.0, n1 = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    const double c0 = -0.5 * (double)a.cpk[0][pk_index(j, k, a.DP)];
+                    const double c1 = -0.5 * (double)a.cpk[1][pk_index(j, k, a.DP)];
+                    n0 += c0 * c0;
+                    n1 += c1 * c1;
+                }
+                a.cpk[0][pk_index(j, d, a.DP)] = (float)n0;
+                a.cpk[1][pk_index(j, d, a.DP)] = (float)n1;
+            }
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) k_mix(MixArgs a, int use_cond, cudaGraphConditionalHandle cond,
-                                             int max_iter)
+__global__ void __launch_bounds__(256) k_mix(MixArgs a)
 {
     SolveState* st = a.st;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // the single place that ends the graph's loop: done, or a hard iteration guard
-        int stop = st->done;
-        st->pad += 1;                                   // body executions (guard)
-        if (!stop && (int)st->pad > max_iter + 2) {
-            st->status = KM_ETIMEOUT;
-            st->done = 1;
-            stop = 1;
-        }
-        if (stop && use_cond) cudaGraphSetConditional(cond, 0);
-    }
     if (st->done) return;
-    const int K = a.K, d = a.d;
-    const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= K) return;
-    const size_t n = (size_t)K * d;
+    if (j >= a.K) return;
+    __shared__ double s_th[MMAX];
+    __shared__ int s_sl[MMAX];
     const int rank = a.mode == MODE_INIT ? 0 : st->rank;
     const int head = st->ring_head, m_max = a.m_max;
-    double th[MMAX];
-    int sl[MMAX];
-    for (int k = 0; k < rank; ++k) {
-        th[k] = st->theta[k];
-        sl[k] = (head - k + m_max) % m_max;
+    if (threadIdx.x < MMAX) {
+        s_th[threadIdx.x] = threadIdx.x < rank ? st->theta[threadIdx.x] : 0.0;
+        s_sl[threadIdx.x] = (head - (int)threadIdx.x + m_max) % m_max;
     }
-    double nrm0 = 0.0, nrm1 = 0.0;
-    for (int k = lane; k < d; k += 32) {
-        const size_t i = (size_t)j * d + k;
-        const double g = a.CAU[i];
-        double c = g;
-        for (int q = 0; q < rank; ++q) c -= th[q] * a.dG[(size_t)sl[q] * n + i];
-        a.C64[i] = c;
-        if (a.fp32_path) {
-            const double o = (double)a.origin[k];
-            const float c0 = (float)(c - o), c1 = (float)(g - o);
-            a.c32[0][i] = (float)c;
-            a.c32[1][i] = (float)g;
-            a.cpk[0][(size_t)j * a.DP + k] = -2.f * c0;
-            a.cpk[1][(size_t)j * a.DP + k] = -2.f * c1;
-            nrm0 += (double)c0 * (double)c0;
-            nrm1 += (double)c1 * (double)c1;
-        }
-    }
-    if (a.fp32_path) {
-        nrm0 = warp_sum(nrm0);
-        nrm1 = warp_sum(nrm1);
-        if (lane == 0) {
-            a.cpk[0][(size_t)j * a.DP + d] = (float)nrm0;
-            a.cpk[1][(size_t)j * a.DP + d] = (float)nrm1;
-        }
-    }
+    __syncthreads();
+    mix_pack_centroid(j, a.K, a.d, a.DP, a.fp32_path, a.C64, a.CAU, a.dG, s_th, s_sl, rank, a.origin, a.cpk,
+                      a.c32);
 }
 
 template <typename T>
-__global__ void k_prep(const T* C0, int K, int d, int Kpad, int DP, int fp32_path, double* C64,
-                       float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st,
-                       int m_init, int m_max)
+__global__ void __launch_bounds__(1024) k_prep(const T* C0, int K, int d, int Kpad, int DP, int fp32_path,
+                                               double* C64, float* origin, float* cpk0, float* cpk1, float* c32_0,
+                                               SolveState* st, int m_init, int m_max)
 {
-    const int tid = threadIdx.x;
-    __shared__ double s_o[64];
-    // origin o = mean of the initial centroids (FP64, ascending j), rounded to FP32
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double s_red[32];
+    __shared__ float s_o[64];
+    // zero the controller state
+    unsigned int* sw = reinterpret_cast<unsigned int*>(st);
+    for (size_t i = tid; i < sizeof(SolveState) / 4; i += blockDim.x) sw[i] = 0u;
+    // origin o = mean of the initial centroids (FP64, fixed-order block reduction), rounded to FP32
     if (fp32_path) {
-        for (int k = tid; k < d; k += blockDim.x) {
-            double s = 0.0;
-            for (int j = 0; j < K; ++j) s += (double)C0[(size_t)j * d + k];
-            origin[k] = (float)(s / K);
+        for (int k = 0; k < d; ++k) {
+            double v = 0.0;
+            for (int j = tid; j < K; j += blockDim.x) v += (double)C0[(size_t)j * d + k];
+            v = warp_sum(v);
+            if (lane == 0) s_red[warp] = v;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+                s_o[k] = (float)(t / K);
+                origin[k] = s_o[k];
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
     const size_t n = (size_t)K * d;
     for (size_t i = tid; i < n; i += blockDim.x) C64[i] = (double)C0[i];
     if (fp32_path) {
         for (size_t i = tid; i < (size_t)Kpad * DP; i += blockDim.x) {
-            const int j = (int)(i / DP), k = (int)(i % DP);
+            const int w = (int)(i % (2 * DP));
+            const int j = (int)(i / (2 * DP)) * 2 + (w & 1), k = w >> 1;
             const float v = (j >= K && k == d) ? __int_as_float(0x7f800000) : 0.f;
             cpk0[i] = v;
             cpk1[i] = v;
@@ -361,27 +455,23 @@ __global__ void k_prep(const T* C0, int K, int d, int Kpad, int DP, int fp32_pat
             double nrm = 0.0;
             for (int k = 0; k < d; ++k) {
                 const double c = (double)C0[(size_t)j * d + k];
-                const float cc = (float)(c - (double)origin[k]);
+                const float cc = (float)(c - (double)s_o[k]);
                 c32_0[(size_t)j * d + k] = (float)c;
-                cpk0[(size_t)j * DP + k] = -2.f * cc;
+                cpk0[pk_index(j, k, DP)] = -2.f * cc;
                 nrm += (double)cc * (double)cc;
             }
-            cpk0[(size_t)j * DP + d] = (float)nrm;
+            cpk0[pk_index(j, d, DP)] = (float)nrm;
         }
     }
+    __syncthreads();
     if (tid == 0) {
-        SolveState s;
-        memset(&s, 0, sizeof(s));
-        s.m = m_init < m_max ? m_init : m_max;
-        if (s.m < 0) s.m = 0;
-        s.from_lloyd = 1;
-        s.E_prev = s.E_prev2 = __longlong_as_double(0x7ff0000000000000LL);
-        s.ring_head = -1 + (m_max > 0 ? m_max : 1);      // first insert goes to slot 0
-        s.ring_count = 0;
-        s.status = KM_OK;
-        *st = s;
+        st->m = m_init < m_max ? m_init : m_max;
+        if (st->m < 0) st->m = 0;
+        st->from_lloyd = 1;
+        st->E_prev = st->E_prev2 = __longlong_as_double(0x7ff0000000000000LL);
+        st->ring_head = m_max > 0 ? m_max - 1 : 0;      // first insert goes to slot 0
+        st->status = KM_OK;
     }
-    (void)s_o;
 }
 
 struct DevInfo {
@@ -419,7 +509,7 @@ __global__ void k_epi(const SolveState* st, const double* C64, const double* CAU
 
 int fin_blocks(int K, int d, int* KB)
 {
-    int kb = 32 / (d + 1);
+    int kb = 16 / (d + 1);
     if (kb < 1) kb = 1;
     *KB = kb;
     return (K + kb - 1) / kb;
@@ -437,12 +527,10 @@ cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_mix_full(const MixArgs& a, int use_cond, cudaGraphConditionalHandle cond, int max_iter,
-                            cudaStream_t s)
+cudaError_t launch_mix(const MixArgs& a, cudaStream_t s)
 {
-    const int warps = a.K;
-    const int blocks = (warps * 32 + 255) / 256;
-    k_mix<<<blocks, 256, 0, s>>>(a, use_cond, cond, max_iter);
+    const int blocks = (a.K * 32 + 255) / 256;
+    k_mix<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

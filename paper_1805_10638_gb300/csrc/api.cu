@@ -238,39 +238,64 @@ void set_bound(PassArgs& a, int d)
     a.bound_coef2 = (float)(1.01 * (2 * d + 4) * u);
 }
 
-kmeans_status pack_user_centroids(kmeans_ctx* ctx, const Plan& P, const void* C, int K, int d, int prec)
-{
-    KM_CUDA(launch_prep(C, prec == KM_F64, K, d, P.Kpad, P.DP, at<double>(ctx, P.C64), at<float>(ctx, P.origin),
-                        at<float>(ctx, P.cpk0), at<float>(ctx, P.cpk1), at<float>(ctx, P.c32_0),
-                        at<SolveState>(ctx, P.st), 0, 0, ctx->stream));
-    return KM_OK;
-}
 
-kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, const void* C0,
-                           const kmeans_params& p, void* C_out, int32_t* rho_out)
-{
-    const int d = X->d, prec = X->prec;
-    const int64_t N = X->N;
-    const bool f64 = prec == KM_F64;
-    const int m_max = p.lloyd_only ? 0 : p.m_max;
-    SolveState* st = at<SolveState>(ctx, P.st);
-    const int64_t thr = p.tol > 0 ? (int64_t)(p.tol * (double)N) : 0;
+// Everything one solve launches, resolved to device pointers once.
+struct Launch {
+    PassArgs pa;
+    FinArgs fa;
+    MixArgs ma;
+    Plan P;
+    kmeans_params p;
+    const void* C0;
+    void* C_out;
+    int32_t* rho_out;
+    SolveState* st;
+    void* info;
+    int32_t* rhoA;
+    int32_t* rhoB;
+    int64_t N;
+    int d, K, prec, m_max;
+    bool f64;
+};
 
-    PassArgs pa = base_pass(ctx, P, X->X, N, K, prec);
+Launch make_launch(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, const void* C0,
+                   const kmeans_params& p, void* C_out, int32_t* rho_out)
+{
+    Launch L;
+    L.P = P;
+    L.p = p;
+    L.C0 = C0;
+    L.C_out = C_out;
+    L.rho_out = rho_out;
+    L.N = X->N;
+    L.d = X->d;
+    L.K = K;
+    L.prec = X->prec;
+    L.f64 = X->prec == KM_F64;
+    L.m_max = p.lloyd_only ? 0 : p.m_max;
+    L.st = at<SolveState>(ctx, P.st);
+    L.info = at<void>(ctx, P.info);
+    L.rhoA = at<int32_t>(ctx, P.rhoA);
+    L.rhoB = at<int32_t>(ctx, P.rhoB);
+    const int d = X->d;
+    const int64_t thr = p.tol > 0 ? (int64_t)(p.tol * (double)X->N) : 0;
+
+    PassArgs& pa = L.pa;
+    pa = base_pass(ctx, P, X->X, X->N, K, X->prec);
     set_bound(pa, d);
-    pa.m_max = m_max;
+    pa.m_max = L.m_max;
     pa.max_iter = p.max_iter;
     pa.lloyd_only = p.lloyd_only;
     pa.eps1 = p.eps1;
     pa.eps2 = p.eps2;
     pa.thr = thr;
 
-    FinArgs fa;
+    FinArgs& fa = L.fa;
     memset(&fa, 0, sizeof(fa));
     fa.K = K;
     fa.d = d;
     fa.nb = P.nb;
-    fa.part_f64 = f64;
+    fa.part_f64 = L.f64;
     fa.pS = at<void>(ctx, P.pS);
     fa.pCnt = at<int32_t>(ctx, P.pCnt);
     fa.KB = P.KB;
@@ -280,52 +305,111 @@ kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X,
     fa.dF = at<double>(ctx, P.dF);
     fa.dG = at<double>(ctx, P.dG);
     fa.pDots = at<double>(ctx, P.pDots);
-    fa.st = st;
-    fa.m_max = m_max;
+    fa.st = L.st;
+    fa.m_max = L.m_max;
     fa.max_iter = p.max_iter;
     fa.lloyd_only = p.lloyd_only;
     fa.rank_tol = p.rank_tol;
+    fa.fuse_mix = (K <= 1024 && (size_t)K * d <= 16384) ? 1 : 0;
+    fa.DP = P.DP;
+    fa.fp32_path = !L.f64;
+    fa.origin = at<float>(ctx, P.origin);
+    fa.cpk[0] = at<float>(ctx, P.cpk0);
+    fa.cpk[1] = at<float>(ctx, P.cpk1);
+    fa.c32[0] = at<float>(ctx, P.c32_0);
+    fa.c32[1] = at<float>(ctx, P.c32_1);
 
-    MixArgs ma;
+    MixArgs& ma = L.ma;
     memset(&ma, 0, sizeof(ma));
     ma.K = K;
     ma.d = d;
     ma.Kpad = P.Kpad;
     ma.DP = P.DP;
-    ma.fp32_path = !f64;
+    ma.fp32_path = !L.f64;
     ma.C64 = at<double>(ctx, P.C64);
     ma.CAU = at<double>(ctx, P.CAU);
     ma.dG = at<double>(ctx, P.dG);
-    ma.m_max = m_max > 0 ? m_max : 1;
+    ma.m_max = L.m_max > 0 ? L.m_max : 1;
     ma.origin = at<float>(ctx, P.origin);
     ma.cpk[0] = at<float>(ctx, P.cpk0);
     ma.cpk[1] = at<float>(ctx, P.cpk1);
     ma.c32[0] = at<float>(ctx, P.c32_0);
     ma.c32[1] = at<float>(ctx, P.c32_1);
-    ma.st = st;
+    ma.st = L.st;
+    return L;
+}
 
+// Prologue: C^0 -> P^0 -> G^0 = C^1 (Algorithm 1's first line).
+cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditionalHandle h)
+{
+    cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
+    if (e == cudaSuccess)
+        e = launch_prep(L.C0, L.f64, L.K, L.d, L.P.Kpad, L.P.DP, L.ma.C64, const_cast<float*>(L.ma.origin),
+                        L.ma.cpk[0], L.ma.cpk[1], L.ma.c32[0], L.st, L.p.m_init, L.m_max, s);
+    PassArgs a = L.pa;
+    a.mode = MODE_INIT;
+    a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
+    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    FinArgs f = L.fa;
+    f.mode = MODE_INIT;
+    if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+    if (!L.fa.fuse_mix) {
+        MixArgs m = L.ma;
+        m.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+    }
+    (void)h;
+    return e;
+}
+
+// One loop pass t of Algorithm 1 (or Lloyd): trial assignment + controller, conditional revert,
+// update + history + least squares, accelerated iterate (which also ends the graph loop).
+cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h)
+{
+    PassArgs a = L.pa;
+    a.mode = MODE_TRIAL;
+    a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
+    a.use_cond = use_cond;
+    a.cond = h;
+    cudaError_t e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    a.mode = MODE_REVERT;
+    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    FinArgs f = L.fa;
+    f.mode = MODE_TRIAL;
+    f.use_cond = use_cond;
+    f.cond = h;
+    if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+    if (!L.fa.fuse_mix) {
+        MixArgs m = L.ma;
+        m.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+    }
+    return e;
+}
+
+// Epilogue: the energy of (P^t, G^t) if the loop stopped at max_iter, results and info.
+cudaError_t launch_epilogue(const Launch& L, cudaStream_t s)
+{
+    PassArgs a = L.pa;
+    a.mode = MODE_EPI;
+    a.flags = F_ENERGY;
+    cudaError_t e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    if (e == cudaSuccess)
+        e = launch_epi(L.f64, L.st, L.ma.C64, L.ma.CAU, L.C_out, (size_t)L.K * L.d, L.rhoA, L.rhoB, L.rho_out, L.N,
+                       L.info, s);
+    return e;
+}
+
+kmeans_status record_graph(kmeans_ctx* ctx, const Launch& L)
+{
     cudaGraph_t g = nullptr, gp = nullptr, ge = nullptr;
     cudaGraphConditionalHandle h;
     KM_CUDA(cudaGraphCreate(&g, 0));
     KM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
 
-    // prologue
     KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
     {
-        cudaError_t e = cudaMemsetAsync(pa.counter, 0, 256, ctx->cap);
-        if (e == cudaSuccess)
-            e = launch_prep(C0, f64, K, d, P.Kpad, P.DP, ma.C64, at<float>(ctx, P.origin), ma.cpk[0],
-                                    ma.cpk[1], ma.c32[0], st, p.m_init, m_max, ctx->cap);
-        PassArgs a = pa;
-        a.mode = MODE_INIT;
-        a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
-        if (e == cudaSuccess) e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
-        FinArgs f = fa;
-        f.mode = MODE_INIT;
-        if (e == cudaSuccess) e = launch_fin(f, P.nfin, ctx->cap);
-        MixArgs m = ma;
-        m.mode = MODE_INIT;
-        if (e == cudaSuccess) e = launch_mix_full(m, 0, h, p.max_iter, ctx->cap);
+        cudaError_t e = launch_prologue(L, ctx->cap, h);
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &gp);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue launch");
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "prologue capture");
@@ -333,7 +417,6 @@ kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X,
     cudaGraphNode_t np, nc, ne;
     KM_CUDA(cudaGraphAddChildGraphNode(&np, g, nullptr, 0, gp));
 
-    // while loop
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
@@ -342,34 +425,16 @@ kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X,
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     KM_CUDA(cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     {
-        PassArgs a = pa;
-        a.mode = MODE_TRIAL;
-        a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
-        cudaError_t e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
-        a.mode = MODE_REVERT;
-        if (e == cudaSuccess) e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
-        FinArgs f = fa;
-        f.mode = MODE_TRIAL;
-        if (e == cudaSuccess) e = launch_fin(f, P.nfin, ctx->cap);
-        MixArgs m = ma;
-        m.mode = MODE_TRIAL;
-        if (e == cudaSuccess) e = launch_mix_full(m, 1, h, p.max_iter, ctx->cap);
+        cudaError_t e = launch_body(L, ctx->cap, 1, h);
         cudaGraph_t bout = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &bout);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "loop body launch");
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "loop body capture");
     }
 
-    // epilogue
     KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
     {
-        PassArgs a = pa;
-        a.mode = MODE_EPI;
-        a.flags = F_ENERGY;
-        cudaError_t e = launch_pass_lowd(a, prec, d, P.nb, ctx->cap);
-        if (e == cudaSuccess)
-            e = launch_epi(f64, st, ma.C64, ma.CAU, C_out, (size_t)K * d, at<int32_t>(ctx, P.rhoA),
-                           at<int32_t>(ctx, P.rhoB), rho_out, N, at<void>(ctx, P.info), ctx->cap);
+        cudaError_t e = launch_epilogue(L, ctx->cap);
         cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &ge);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "epilogue launch");
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "epilogue capture");
@@ -383,6 +448,29 @@ kmeans_status record_graph(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X,
     if (ctx->have_graph) cudaGraphExecDestroy(ctx->exec);
     ctx->exec = exec;
     ctx->have_graph = true;
+    return KM_OK;
+}
+
+// KM_GRAPH=0 in the environment launches the same kernels from a host loop (one wait per
+// iteration) instead of the graph; profilers cannot see kernels inside conditional graphs.
+bool graph_mode()
+{
+    const char* v = getenv("KM_GRAPH");
+    return !(v && v[0] == '0');
+}
+
+kmeans_status run_host_loop(kmeans_ctx* ctx, const Launch& L)
+{
+    cudaGraphConditionalHandle h = 0;
+    KM_CUDA(launch_prologue(L, ctx->stream, h));
+    int* done = reinterpret_cast<int*>(static_cast<char*>(ctx->h_info) + 128);
+    for (int it = 0; it < L.p.max_iter + 2; ++it) {
+        KM_CUDA(launch_body(L, ctx->stream, 0, h));
+        KM_CUDA(cudaMemcpyAsync(done, &L.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        KM_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (*done) break;
+    }
+    KM_CUDA(launch_epilogue(L, ctx->stream));
     return KM_OK;
 }
 
@@ -419,13 +507,20 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     key.p = p;
     key.arena = ctx->arena;
     key.arena_bytes = ctx->arena_bytes;
-    if (!ctx->have_graph || memcmp(&key, &ctx->key, sizeof(key)) != 0) {
-        kmeans_status s = record_graph(ctx, P, X, K, C0, p, C_out, rho_out);
+    const Launch L = make_launch(ctx, P, X, K, C0, p, C_out, rho_out);
+    const bool use_graph = graph_mode();
+    if (use_graph && (!ctx->have_graph || memcmp(&key, &ctx->key, sizeof(key)) != 0)) {
+        kmeans_status s = record_graph(ctx, L);
         if (s != KM_OK) return s;
         ctx->key = key;
     }
     KM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-    KM_CUDA(cudaGraphLaunch(ctx->exec, ctx->stream));
+    if (use_graph) {
+        KM_CUDA(cudaGraphLaunch(ctx->exec, ctx->stream));
+    } else {
+        kmeans_status s = run_host_loop(ctx, L);
+        if (s != KM_OK) return s;
+    }
     KM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
     KM_CUDA(cudaMemcpyAsync(ctx->h_info, at<void>(ctx, P.info), sizeof(DevInfoH), cudaMemcpyDeviceToHost,
                             ctx->stream));
@@ -549,12 +644,12 @@ kmeans_status kmeans_assign(kmeans_ctx* ctx, const kmeans_data* X, const void* C
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, X->prec, 0, false, P, false)) != KM_OK) return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
-    if (X->prec != KM_F64 && (s = pack_user_centroids(ctx, P, C, K, X->d, X->prec)) != KM_OK) return s;
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, X->prec);
     a.mode = MODE_STANDALONE;
-    a.flags = F_ASSIGN | (n_changed ? F_CHANGED : 0) | (dmin ? F_DMIN : 0);
+    a.flags = F_ASSIGN | (n_changed ? F_CHANGED : 0) | (dmin ? F_DMIN : 0) | (X->prec != KM_F64 ? F_PACK : 0);
     set_bound(a, X->d);
     if (X->prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C);
+    else a.rawC = reinterpret_cast<const float*>(C);
     a.rho[0] = rho;
     a.rho_prev = rho_prev;
     a.out_nch = reinterpret_cast<long long*>(n_changed);
@@ -577,11 +672,11 @@ kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P, false)) != KM_OK) return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
-    if (prec != KM_F64 && (s = pack_user_centroids(ctx, P, C, K, X->d, prec)) != KM_OK) return s;
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
     a.mode = MODE_STANDALONE;
-    a.flags = F_ENERGY;
+    a.flags = F_ENERGY | (prec != KM_F64 ? F_PACK : 0);
     if (prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C);
+    else a.rawC = reinterpret_cast<const float*>(C);
     a.rho_in = rho;
     a.out_E = E;
     KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
@@ -602,11 +697,11 @@ kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P)) != KM_OK) return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
-    if (prec != KM_F64 && (s = pack_user_centroids(ctx, P, C_prev, K, X->d, prec)) != KM_OK) return s;
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
     a.mode = MODE_STANDALONE;
-    a.flags = F_BINS;
+    a.flags = F_BINS | (prec != KM_F64 ? F_PACK : 0);
     if (prec == KM_F64) a.c64[0] = reinterpret_cast<const double*>(C_prev);
+    else a.rawC = reinterpret_cast<const float*>(C_prev);
     a.rho_in = rho;
     KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
     KM_CUDA(launch_pass_lowd(a, prec, X->d, P.nb, ctx->stream));

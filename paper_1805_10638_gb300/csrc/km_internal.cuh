@@ -39,7 +39,8 @@ enum PassFlags : int {
     F_ENERGY = 4,     // accumulate the energy
     F_CHANGED = 8,    // count rho != rho_prev
     F_DMIN = 16,      // write the per-row squared distance
-    F_CHECK = 32      // flag non-finite samples
+    F_CHECK = 32,     // flag non-finite samples
+    F_PACK = 64       // FP32 standalone: pack the raw centroids rawC in every block
 };
 
 // Controller and Anderson state of one solve (device resident).
@@ -73,7 +74,7 @@ struct SolveState {
     unsigned int ctr_pass;   // last-block counters (reset by the last block)
     unsigned int ctr_fin;
     unsigned int ctr_aux;
-    unsigned int pad;
+    unsigned int body_runs;  // loop body executions (hard iteration guard)
 };
 
 // Arguments of the low-d assignment pass (by value).
@@ -89,6 +90,7 @@ struct PassArgs {
     const float* c32[2];     // FP32 path uncentred [K][D]
     const double* c64[2];    // FP64 path [K][D]
     const float* origin;     // FP32 path origin o [D]
+    const float* rawC;       // F_PACK: the caller's FP32 centroids [K][D]
     float bound_coef;        // FP32 path: score error bound = bound_coef*max|c'|^2 + bound_coef2*|x'|*max|c'|
     float bound_coef2;
     // assignment buffers: solver uses rho[st->cur] / rho[st->cur ^ 1]
@@ -148,6 +150,13 @@ struct FinArgs {
     double rank_tol;
     int use_cond;
     cudaGraphConditionalHandle cond;
+    // accelerated iterate in the last block (small K*d)
+    int fuse_mix;
+    int DP;
+    int fp32_path;
+    const float* origin;
+    float* cpk[2];
+    float* c32[2];
 };
 
 // Arguments of the mix + pack kernel.
@@ -168,14 +177,22 @@ struct MixArgs {
     SolveState* st;
 };
 
+// Packed scoring centroids of the FP32 path, pair-interleaved so that one fma.rn.f32x2 scores a
+// sample against two centroids: centroids 2p and 2p+1 share a row of 2*DP floats
+//   (a_{2p,0}, a_{2p+1,0}, ..., a_{2p,D-1}, a_{2p+1,D-1}, ||c'_{2p}||^2, ||c'_{2p+1}||^2, 0...)
+// with a = -2 c'.  Element k of centroid j (k = D is ||c'||^2):
+__host__ __device__ inline size_t pk_index(int j, int k, int DP)
+{
+    return (size_t)(j >> 1) * (2 * DP) + 2 * k + (j & 1);
+}
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s);
 size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins);
 int pass_lowd_dp(int d);
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s);
 int fin_blocks(int K, int d, int* KB);
-cudaError_t launch_mix_full(const MixArgs& a, int use_cond, cudaGraphConditionalHandle cond, int max_iter,
-                            cudaStream_t s);
+cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const void* C0, bool f64, int K, int d, int Kpad, int DP, double* C64,
                         float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st, int m_init,
                         int m_max, cudaStream_t s);

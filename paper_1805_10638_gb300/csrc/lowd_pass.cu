@@ -44,15 +44,21 @@ __device__ __forceinline__ float fmin3f(float a, float b, float c)
 
 template <int D>
 struct Shape {
-    static constexpr int DP = ((D + 1) + 3) / 4 * 4;      // packed stride (floats)
+    static constexpr int DP = ((2 * (D + 1) + 3) / 4 * 4) / 2;   // packed floats per centroid
     static constexpr int R = (D <= 8) ? 4 : 2;             // samples per thread in the scan
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Layout {
-    size_t red, cpk, c, stage, bS, bC, total;
+    size_t red, org, cpk, rec, c, stage, bS, bC, total;
 };
+
+// Skewed copy of the packed centroids for the per-row recovery reads: chunk b (8 centroids of
+// D+1 floats) starts at b * RS floats, RS = 8(D+1)+1 is odd, so lanes recovering different chunks
+// read different banks (the unskewed layout puts every chunk's element (q,k) in the same bank).
+template <int D>
+__host__ __device__ constexpr int rec_stride() { return 8 * (D + 1) + 1; }
 
 __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins)
 {
@@ -60,11 +66,14 @@ __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpa
     Layout L;
     size_t o = 0;
     L.red = o;   o += 64 * sizeof(double);
+    L.org = o;   o += 64 * sizeof(float);
     if (f32) {
         L.cpk = o; o += al16((size_t)Kpad * DP * 4);
+        L.rec = o; o += al16((size_t)(Kpad / 8) * (8 * (D + 1) + 1) * 4);
         L.c = o;   o += al16((size_t)K * D * 4);
     } else {
         L.cpk = 0;
+        L.rec = 0;
         L.c = o;   o += al16((size_t)K * D * 8);
     }
     L.stage = o; o += al16((size_t)W * 32 * D * esz);
@@ -123,6 +132,13 @@ __device__ long long block_sum_ll(long long v, double* red)
 // Head of Algorithm 1 after P^t = Assign(C^t): convergence, dynamic m, safeguard.
 __device__ void controller_trial(const PassArgs& a, SolveState* st, double E, long long nch)
 {
+    st->body_runs += 1;
+    if (st->status != KM_OK || st->body_runs > (unsigned)a.max_iter + 2u) {
+        // non-finite input found by the first pass, or the hard iteration guard
+        if (st->status == KM_OK) st->status = KM_ETIMEOUT;
+        st->done = 1;
+        return;
+    }
     st->passes += 1;
     st->n_changed = nch;
     st->E_trial = E;
@@ -167,12 +183,14 @@ __device__ void controller_revert(const PassArgs& a, SolveState* st, double E, l
     }
 }
 
-template <int D, int R, bool PAIR>
+// Scan all centroids for R samples: per chunk of 8 centroids (4 interleaved pairs), each
+// fma.rn.f32x2 scores one sample against two centroids; xd holds each sample coordinate twice.
+template <int D, int R>
 __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int Kpad,
-                                            const float (&x)[R][D], float (&best)[R],
+                                            const float2 (&xd)[R][D], float (&best)[R],
                                             float (&sec)[R], int (&bc)[R])
 {
-    constexpr int DP = Shape<D>::DP;
+    constexpr int PP = 2 * Shape<D>::DP;        // floats per centroid pair
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         best[r] = __int_as_float(0x7f800000);
@@ -181,43 +199,31 @@ __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int
     }
 #pragma unroll 1
     for (int c0 = 0; c0 < Kpad; c0 += CH) {
-        float s[R][CH];
+        float2 s[R][CH / 2];
 #pragma unroll
-        for (int q = 0; q < CH; ++q) {
-            float cv[DP];
-            const float4* p4 = reinterpret_cast<const float4*>(s_cpk + (size_t)(c0 + q) * DP);
+        for (int p = 0; p < CH / 2; ++p) {
+            float cv[PP];
+            const float4* p4 = reinterpret_cast<const float4*>(s_cpk + (size_t)((c0 >> 1) + p) * PP);
 #pragma unroll
-            for (int v = 0; v < DP / 4; ++v) {
+            for (int v = 0; v < PP / 4; ++v) {
                 const float4 t = p4[v];
                 cv[4 * v] = t.x;
                 cv[4 * v + 1] = t.y;
                 cv[4 * v + 2] = t.z;
                 cv[4 * v + 3] = t.w;
             }
-            if constexpr (PAIR) {
 #pragma unroll
-                for (int r = 0; r < R; r += 2) {
-                    float2 acc = make_float2(cv[D], cv[D]);
+            for (int r = 0; r < R; ++r) {
+                float2 acc = make_float2(cv[2 * D], cv[2 * D + 1]);
 #pragma unroll
-                    for (int k = 0; k < D; ++k)
-                        acc = __ffma2_rn(make_float2(cv[k], cv[k]), make_float2(x[r][k], x[r + 1][k]), acc);
-                    s[r][q] = acc.x;
-                    s[r + 1][q] = acc.y;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float acc = cv[D];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) acc = fmaf(cv[k], x[r][k], acc);
-                    s[r][q] = acc;
-                }
+                for (int k = 0; k < D; ++k) acc = __ffma2_rn(make_float2(cv[2 * k], cv[2 * k + 1]), xd[r][k], acc);
+                s[r][p] = acc;
             }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float m = fmin3f(fmin3f(s[r][0], s[r][1], s[r][2]), fmin3f(s[r][3], s[r][4], s[r][5]),
-                                   fminf(s[r][6], s[r][7]));
+            const float m = fmin3f(fmin3f(s[r][0].x, s[r][0].y, s[r][1].x), fmin3f(s[r][1].y, s[r][2].x, s[r][2].y),
+                                   fminf(s[r][3].x, s[r][3].y));
             sec[r] = fminf(sec[r], fmaxf(best[r], m));
             const bool p = m < best[r];
             best[r] = p ? m : best[r];
@@ -229,15 +235,16 @@ __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int
 // Re-score the best chunk with the same arithmetic; lowest index attaining `best` and the
 // smallest other value in the chunk.
 template <int D>
-__device__ __forceinline__ int recover(const float* __restrict__ s_cpk, const float (&x)[D], float best,
+__device__ __forceinline__ int recover(const float* __restrict__ s_rec, const float (&x)[D], float best,
                                        int bc, float& second_in)
 {
-    constexpr int DP = Shape<D>::DP;
+    constexpr int RS = rec_stride<D>();
+    const float* base = s_rec + (size_t)(bc >> 3) * RS;
     int jj = -1;
     float sv = __int_as_float(0x7f800000);
 #pragma unroll
     for (int q = 0; q < CH; ++q) {
-        const float* cp = s_cpk + (size_t)(bc + q) * DP;
+        const float* cp = base + q * (D + 1);
         float acc = cp[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) acc = fmaf(cp[k], x[k], acc);
@@ -343,17 +350,51 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
     const T* s_c = reinterpret_cast<const T*>(smem + L.c);
 
     // ---- stage centroids and clear bins
+    const float* s_rec = reinterpret_cast<const float*>(smem + L.rec);
+    float* s_org = reinterpret_cast<float*>(smem + L.org);
     if constexpr (F32) {
-        const float4* src = reinterpret_cast<const float4*>(a.cpk[which]);
-        float4* dst = reinterpret_cast<float4*>(smem + L.cpk);
-        for (int i = tid; i < a.Kpad * DP / 4; i += blockDim.x) dst[i] = src[i];
+        float* dst = reinterpret_cast<float*>(smem + L.cpk);
         float* dc = reinterpret_cast<float*>(smem + L.c);
-        if (a.mode == MODE_EPI) {          // G^t was not packed: round it here
-            const double* g64 = a.c64[1];
-            for (int i = tid; i < K * D; i += blockDim.x) dc[i] = (float)g64[i];
+        if (flags & F_PACK) {
+            // standalone call: o = mean of the given centroids (FP64, fixed order), then pack
+            const float* Cr = a.rawC;
+            for (int k = 0; k < D; ++k) {
+                double v = 0.0;
+                for (int j = tid; j < K; j += blockDim.x) v += (double)Cr[(size_t)j * D + k];
+                v = block_sum_d(v, s_red);
+                if (tid == 0) s_org[k] = (float)(v / K);
+            }
+            __syncthreads();
+            for (int j = tid; j < a.Kpad; j += blockDim.x) {
+#pragma unroll
+                for (int k = 0; k < DP; ++k) dst[pk_index(j, k, DP)] = 0.f;
+                if (j < K) {
+                    double nrm = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float c = Cr[(size_t)j * D + k];
+                        dc[(size_t)j * D + k] = c;
+                        const float cc = (float)((double)c - (double)s_org[k]);
+                        dst[pk_index(j, k, DP)] = -2.f * cc;
+                        nrm += (double)cc * (double)cc;
+                    }
+                    dst[pk_index(j, D, DP)] = (float)nrm;
+                } else {
+                    dst[pk_index(j, D, DP)] = __int_as_float(0x7f800000);
+                }
+            }
         } else {
-            const float* c32 = a.c32[which];
-            for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c32[i];
+            const float4* src = reinterpret_cast<const float4*>(a.cpk[which]);
+            float4* dst4 = reinterpret_cast<float4*>(dst);
+            for (int i = tid; i < a.Kpad * DP / 4; i += blockDim.x) dst4[i] = src[i];
+            if (a.mode == MODE_EPI) {          // G^t was not packed: round it here
+                const double* g64 = a.c64[1];
+                for (int i = tid; i < K * D; i += blockDim.x) dc[i] = (float)g64[i];
+            } else {
+                const float* c32 = a.c32[which];
+                for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c32[i];
+            }
+            if (tid < D) s_org[tid] = a.origin[tid];
         }
     } else {
         const double* c64 = a.c64[which];
@@ -366,12 +407,18 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
     }
     __syncthreads();
 
-    // ---- the rounding-error bound of the FP32 expansion needs max|c'| over the centroids
+    // ---- skewed recovery copy and the rounding-error bound's max|c'| (FP32 path)
     float cmax = 0.f;
     float o[D];
     if constexpr (F32) {
+        constexpr int RS = rec_stride<D>();
+        float* sr = reinterpret_cast<float*>(smem + L.rec);
+        for (int i = tid; i < a.Kpad * (D + 1); i += blockDim.x) {
+            const int j = i / (D + 1), k = i % (D + 1);
+            sr[(size_t)(j >> 3) * RS + (j & 7) * (D + 1) + k] = s_cpk[pk_index(j, k, DP)];
+        }
         float mx = 0.f;
-        for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, s_cpk[(size_t)j * DP + D]);
+        for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, s_cpk[pk_index(j, D, DP)]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
         float* fr = reinterpret_cast<float*>(s_red);
@@ -380,9 +427,9 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
         mx = 0.f;
         for (int w = 0; w < W; ++w) mx = fmaxf(mx, fr[w]);
         cmax = sqrtf(mx);
-        __syncthreads();
 #pragma unroll
-        for (int k = 0; k < D; ++k) o[k] = a.origin[k];
+        for (int k = 0; k < D; ++k) o[k] = s_org[k];
+        __syncthreads();
     }
 
     const T* X = reinterpret_cast<const T*>(a.X);
@@ -471,9 +518,14 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
 #pragma unroll
                     for (int k = 0; k < D; ++k) x[r][k] = xr[k] - o[k];
                 }
+                float2 xd[R][D];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xd[r][k] = make_float2(x[r][k], x[r][k]);
                 float best[R], sec[R];
                 int bc[R];
-                scan_chunks<D, R, (R % 2 == 0)>(s_cpk, a.Kpad, x, best, sec, bc);
+                scan_chunks<D, R>(s_cpk, a.Kpad, xd, best, sec, bc);
                 int idxr[R];
                 bool need[R];
 #pragma unroll
@@ -482,7 +534,7 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
 #pragma unroll
                     for (int k = 0; k < D; ++k) xn = fmaf(x[r][k], x[r][k], xn);
                     float sin_;
-                    idxr[r] = recover<D>(s_cpk, x[r], best[r], bc[r], sin_);
+                    idxr[r] = recover<D>(s_rec, x[r], best[r], bc[r], sin_);
                     const float second = fminf(sec[r], sin_);
                     const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
                     need[r] = second - best[r] <= 2.f * bnd;
@@ -502,14 +554,17 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
                 if (valid) check(xr);
 #pragma unroll
                 for (int k = 0; k < D; ++k) x[0][k] = xr[k] - o[k];
+                float2 xd[1][D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) xd[0][k] = make_float2(x[0][k], x[0][k]);
                 float best[1], sec[1];
                 int bc[1];
-                scan_chunks<D, 1, false>(s_cpk, a.Kpad, x, best, sec, bc);
+                scan_chunks<D, 1>(s_cpk, a.Kpad, xd, best, sec, bc);
                 float xn = 0.f;
 #pragma unroll
                 for (int k = 0; k < D; ++k) xn = fmaf(x[0][k], x[0][k], xn);
                 float sin_;
-                int idx = recover<D>(s_cpk, x[0], best[0], bc[0], sin_);
+                int idx = recover<D>(s_rec, x[0], best[0], bc[0], sin_);
                 const float second = fminf(sec[0], sin_);
                 const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
                 const bool need = valid && second - best[0] <= 2.f * bnd;
@@ -616,14 +671,14 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
             } else if (a.mode == MODE_INIT) {
                 st->passes += 1;
                 st->E_trial = E;
-                if (bd) {
-                    st->status = KM_ENONFINITE;
-                    st->done = 1;
-                }
-            } else if (a.mode == MODE_TRIAL) {
-                controller_trial(a, st, E, ch);
+                if (bd) st->status = KM_ENONFINITE;       // the first loop pass stops the solve
             } else {
-                controller_revert(a, st, E, ch);
+                if (a.mode == MODE_TRIAL)
+                    controller_trial(a, st, E, ch);
+                else
+                    controller_revert(a, st, E, ch);
+                // the kernel that ends the solve also ends the graph's while loop
+                if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
             }
         }
     }
@@ -647,7 +702,7 @@ cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
 
 int pass_lowd_dp(int d)
 {
-    return ((d + 1) + 3) / 4 * 4;
+    return ((2 * (d + 1) + 3) / 4 * 4) / 2;
 }
 
 size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins)

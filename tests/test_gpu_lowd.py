@@ -255,3 +255,18 @@ def test_solve_lowd_2m_full_size_sampled(ctx):
     assert abs(info["E"] - Eo) / Eo < 1e-6
     Cl, rl, il = km.kmeans_solve(ctx, Xd, dev(C0), lloyd_only=1)
     assert il["converged"] == 1
+
+
+def test_host_loop_mode_matches_graph(ctx):
+    """KM_GRAPH=0 launches the same kernels from a host loop: results must be bitwise equal."""
+    X, C0 = datagen.lowd_2m(seed=5, N=60_000, K=48)
+    Xd, Cd = dev(X), dev(C0)
+    C1, r1, i1 = km.kmeans_solve(ctx, Xd, Cd)
+    C1, r1 = C1.clone(), r1.clone()
+    os.environ["KM_GRAPH"] = "0"
+    try:
+        C2, r2, i2 = km.kmeans_solve(ctx, Xd, Cd)
+    finally:
+        del os.environ["KM_GRAPH"]
+    assert torch.equal(C1, C2) and torch.equal(r1, r2)
+    assert {k: v for k, v in i1.items() if k != "device_ms"} == {k: v for k, v in i2.items() if k != "device_ms"}

@@ -206,14 +206,14 @@ def kmeans_solve(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, **p
     return C_out, rho_out, info.as_dict()
 
 
-def kmeans_solve_host(ctx: Context, X, C0, C_out=None, rho_out=None, **params):
+def kmeans_solve_host(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, **params):
     """kmeans_solve with host buffers (torch CPU tensors, ideally pinned, or numpy arrays)."""
     if C_out is None:
         C_out = torch.empty(C0.shape, dtype=C0.dtype).pin_memory() if torch.is_tensor(C0) else np.empty_like(C0)
     if rho_out is None:
         rho_out = (torch.empty(X.shape[0], dtype=torch.int32).pin_memory() if torch.is_tensor(X)
                    else np.empty(X.shape[0], np.int32))
-    data = make_data(X)
+    data = make_data(X, X_bf16)
     p = default_params(**params)
     info = kmeans_info()
     _check(ctx, load().kmeans_solve_host(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0),

@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     double* s_tot = reinterpret_cast<double*>(smem);             // [E]
     double* s_dfn = s_tot + E;                                    // [kb*d]
     double* s_F = s_dfn + (size_t)kb * d;                         // [kb*d]
-    double* s_part = s_F + (size_t)kb * d;                        // [FIN_THREADS]
-    double* s_red = s_part + FIN_THREADS;                         // [2*MMAX*8]
+    double* s_part = s_F + (size_t)kb * d;                        // [2*FIN_THREADS] (>= 2*MMAX*8)
+    double* s_red = s_part + 2 * FIN_THREADS;                     // [2*MMAX*8]
     __shared__ double s_M[MMAX * MMAX];
     __shared__ double s_inv[MMAX];
     __shared__ double s_th[MMAX];
@@ -154,8 +154,33 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     __shared__ int s_rank;
     __shared__ unsigned int s_last;
 
-    // ---- phase 1/2: sums over the partial blocks in a fixed order
-    for (int p = tid; p < E * split; p += blockDim.x) {
+    // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
+    // block size) each element goes straight to s_tot; s_part holds only 2*FIN_THREADS entries.
+    if (split == 1) {
+        for (int e = tid; e < E; e += blockDim.x) {
+            double acc = 0.0;
+            if (e < kb * d) {
+                const size_t off = (size_t)j0 * d + e;
+                if (a.part_f64) {
+                    const double* pS = reinterpret_cast<const double*>(a.pS);
+#pragma unroll 8
+                    for (int b = 0; b < nb; ++b) acc += pS[(size_t)b * K * d + off];
+                } else {
+                    const float* pS = reinterpret_cast<const float*>(a.pS);
+#pragma unroll 8
+                    for (int b = 0; b < nb; ++b) acc += (double)pS[(size_t)b * K * d + off];
+                }
+            } else {
+                const int j = j0 + (e - kb * d);
+                long long c = 0;
+#pragma unroll 8
+                for (int b = 0; b < nb; ++b) c += a.pCnt[(size_t)b * K + j];
+                acc = (double)c;
+            }
+            s_tot[e] = acc;
+        }
+    }
+    for (int p = tid; split > 1 && p < E * split; p += blockDim.x) {
         const int e = p / split, sp = p % split;
         double acc = 0.0;
         if (e < kb * d) {
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
         s_part[p] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < E; e += blockDim.x) {
+    for (int e = tid; split > 1 && e < E; e += blockDim.x) {
         double v = 0.0;
         for (int sp = 0; sp < split; ++sp) v += s_part[e * split + sp];
         s_tot[e] = v;
@@ -287,10 +312,18 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     if (!s_last) return;
     __threadfence();
     if (ring) {
-        for (int v = tid; v < 2 * nage; v += blockDim.x) {
+        // fixed-order two-level sum over the blocks: 8 interleaved sub-sums, then in order
+        for (int t = tid; t < 2 * nage * 8; t += blockDim.x) {
+            const int v = t >> 3, sp = t & 7;
             double acc = 0.0;
 #pragma unroll 8
-            for (int b = 0; b < (int)gridDim.x; ++b) acc += __ldcg(a.pDots + (size_t)b * DOTS + v);
+            for (int b = sp; b < (int)gridDim.x; b += 8) acc += __ldcg(a.pDots + (size_t)b * DOTS + v);
+            s_part[t] = acc;
+        }
+        __syncthreads();
+        for (int v = tid; v < 2 * nage; v += blockDim.x) {
+            double acc = 0.0;
+            for (int sp = 0; sp < 8; ++sp) acc += s_part[v * 8 + sp];
             s_red[v] = acc;
         }
         __syncthreads();
@@ -509,7 +542,7 @@ __global__ void k_epi(const SolveState* st, const double* C64, const double* CAU
 
 int fin_blocks(int K, int d, int* KB)
 {
-    int kb = 16 / (d + 1);
+    int kb = d > 16 ? 8 : 16 / (d + 1);
     if (kb < 1) kb = 1;
     *KB = kb;
     return (K + kb - 1) / kb;
@@ -518,7 +551,7 @@ int fin_blocks(int K, int d, int* KB)
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s)
 {
     const int E = a.KB * (a.d + 1);
-    const size_t smem = sizeof(double) * ((size_t)E + 2 * (size_t)a.KB * a.d + FIN_THREADS + 2 * MMAX * 8);
+    const size_t smem = sizeof(double) * ((size_t)E + 2 * (size_t)a.KB * a.d + 2 * FIN_THREADS + 2 * MMAX * 8);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -536,13 +569,13 @@ cudaError_t launch_mix(const MixArgs& a, cudaStream_t s)
 
 cudaError_t launch_prep(const void* C0, bool f64, int K, int d, int Kpad, int DP, double* C64,
                         float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st, int m_init,
-                        int m_max, cudaStream_t s)
+                        int m_max, cudaStream_t s, int pack)
 {
     if (f64)
         k_prep<double><<<1, 1024, 0, s>>>(reinterpret_cast<const double*>(C0), K, d, Kpad, DP, 0, C64, origin,
                                           cpk0, cpk1, c32_0, st, m_init, m_max);
     else
-        k_prep<float><<<1, 1024, 0, s>>>(reinterpret_cast<const float*>(C0), K, d, Kpad, DP, 1, C64, origin,
+        k_prep<float><<<1, 1024, 0, s>>>(reinterpret_cast<const float*>(C0), K, d, Kpad, DP, pack, C64, origin,
                                          cpk0, cpk1, c32_0, st, m_init, m_max);
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 //   epilogue : pass(EPI: energy if stopped at max_iter) -> k_epi(results, info)
 //
 // All per-iteration decisions stay on the device; the host waits once per solve.
+#include "dense.cuh"
 #include "km_internal.cuh"
 
 #include <cstdio>
@@ -38,10 +39,18 @@ struct Plan {
     size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
     size_t pS, pCnt, pE, pNch, pResc, pBad, pDots, counter, info;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
+    // dense path (tensor-core assignment, sort-based update)
+    size_t cb0, cb1, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
+        part, pe, pnch, S, rowe, rown;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
+    bool dense;
+    int dpad, nbk, rpb, max_chunks;
     size_t smem;
 };
+
+constexpr int DENSE_RPB = 4096;   // rows per block of the dense update's histogram and scatter
+constexpr int DENSE_SEG = 64;     // rows per segment-sum chunk
 
 }  // namespace
 
@@ -109,10 +118,85 @@ int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem)
 }
 
 // Workspace layout of one problem shape (bins = fused per-block update partials).
+// Dense path: BF16 tensor-core assignment, sort-based update (d in 17..128, d % 8 == 0).
+kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_max, bool host_copies, Plan& P)
+{
+    if (d > 128 || d % 8 != 0)
+        return fail(ctx, KM_EINVAL, "the tensor-core path needs d <= 128 and d % 8 == 0");
+    if (K > 4096) return fail(ctx, KM_EINVAL, "the tensor-core path supports K <= 4096");
+    P.dense = true;
+    P.dpad = (d + 63) / 64 * 64;
+    P.Kpad = (K + 255) / 256 * 256;
+    P.DP = 0;
+    P.nb = 1;
+    P.nfin = fin_blocks(K, d, &P.KB);
+    P.rpb = DENSE_RPB;
+    P.nbk = (int)((N + DENSE_RPB - 1) / DENSE_RPB);
+    P.max_chunks = (int)((N + DENSE_SEG - 1) / DENSE_SEG) + K;
+    P.smem = 0;
+    const size_t n = (size_t)K * d;
+    const int mm = m_max > 0 ? m_max : 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
+    P.counter = take(256);
+    P.st = take(sizeof(SolveState));
+    P.rhoA = take((size_t)N * 4);
+    P.rhoB = take((size_t)N * 4);
+    P.C64 = take(n * 8);
+    P.CAU = take(n * 8);
+    P.Fprev = take(n * 8);
+    P.dF = take((size_t)mm * n * 8);
+    P.dG = take((size_t)mm * n * 8);
+    P.cpk0 = P.cpk1 = 0;
+    P.c32_0 = take(n * 4);
+    P.c32_1 = take(n * 4);
+    P.origin = take(256);
+    P.cb0 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cb1 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cn0 = take((size_t)P.Kpad * 4);
+    P.cn1 = take((size_t)P.Kpad * 4);
+    P.xnorm = take((size_t)N * 4);
+    P.queue = take((size_t)N * 4);
+    P.qcount = take(256);
+    P.err = take(256);
+    P.hist = take((size_t)K * P.nbk * 4);
+    P.counts = take((size_t)K * 4);
+    P.off = take((size_t)(K + 1) * 4);
+    P.choff = take((size_t)K * 4);
+    P.chunk_cluster = take((size_t)P.max_chunks * 4);
+    P.nchunks = take(256);
+    P.perm = take((size_t)N * 4);
+    P.part = take((size_t)P.max_chunks * d * 4);
+    P.pe = take((size_t)P.max_chunks * 8);
+    P.pnch = take((size_t)P.nbk * 8);
+    P.S = take(n * 8);
+    P.rowe = take(4096 * 8);
+    P.rown = take(4096 * 8);
+    P.pS = P.S;
+    P.pCnt = P.counts;
+    P.pE = P.pNch = P.pResc = P.pBad = 0;
+    P.pDots = take((size_t)P.nfin * DOTS * 8);
+    P.info = take(256);
+    if (host_copies) {
+        P.hX = take((size_t)N * d * 4);
+        P.hXb = take((size_t)N * d * 2);
+        P.hC0 = take(n * 4);
+        P.hCout = take(n * 4);
+        P.hRho = take((size_t)N * 4);
+    } else {
+        P.hX = P.hXb = P.hC0 = P.hCout = P.hRho = 0;
+    }
+    P.total = o;
+    return KM_OK;
+}
+
 kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
                         Plan& P, bool bins = true)
 {
-    if (d > 16) return fail(ctx, KM_EINVAL, "this build supports d <= 16");
+    P.dense = false;
+    P.dpad = P.nbk = P.rpb = P.max_chunks = 0;
+    if (prec == KM_BF16_F32 && d > 16) return make_plan_dense(ctx, N, d, K, m_max, host_copies, P);
+    if (d > 16) return fail(ctx, KM_EINVAL, "d > 16 needs KM_BF16_F32 (the tensor-core path)");
     const bool f32 = prec != KM_F64;
     const size_t esz = f32 ? 4 : 8;
     P.DP = pass_lowd_dp(d);
@@ -256,7 +340,89 @@ struct Launch {
     int64_t N;
     int d, K, prec, m_max;
     bool f64;
+    // dense path
+    DenseArgs da;
+    PackArgs pk;
+    const float* X32;
+    int nsm;
+    alignas(64) unsigned char tmX[128];
+    alignas(64) unsigned char tmC0[128];
+    alignas(64) unsigned char tmC1[128];
+    bool maps_ok = true;
 };
+
+// Dense-path arguments over the plan's buffers (centroid sets 0 = C^t, 1 = C_AU).
+DenseArgs dense_args(kmeans_ctx* ctx, const Plan& P, const float* X32, int64_t N, int d, int K)
+{
+    DenseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N;
+    a.d = d;
+    a.dpad = P.dpad;
+    a.K = K;
+    a.Kpad = P.Kpad;
+    a.X = X32;
+    a.xnorm = at<float>(ctx, P.xnorm);
+    a.cn[0] = at<float>(ctx, P.cn0);
+    a.cn[1] = at<float>(ctx, P.cn1);
+    a.c32[0] = at<float>(ctx, P.c32_0);
+    a.c32[1] = at<float>(ctx, P.c32_1);
+    a.c64[0] = at<double>(ctx, P.C64);
+    a.c64[1] = at<double>(ctx, P.CAU);
+    // BF16 score error bound: 2 (2 u_b + d u) |x| max|c| for 2 x.c, u max|c|^2 for ||c||^2, with a
+    // factor 2 of allowance for the accumulation order inside the MMA
+    const double ub = 1.0 / 512.0, u = 5.9604644775390625e-8;
+    a.bcoef_a = (float)(2.0 * (2.0 * (2.0 * ub + d * u)));
+    a.bcoef_b = (float)(2.0 * 2.0 * u);
+    a.rho_pair[0] = at<int32_t>(ctx, P.rhoA);
+    a.rho_pair[1] = at<int32_t>(ctx, P.rhoB);
+    a.queue = at<int>(ctx, P.queue);
+    a.qcount = at<unsigned int>(ctx, P.qcount);
+    a.err = at<int>(ctx, P.err);
+    a.rows_per_block = P.rpb;
+    a.hist = at<int>(ctx, P.hist);
+    a.counts = at<int32_t>(ctx, P.counts);
+    a.off = at<int>(ctx, P.off);
+    a.choff = at<int>(ctx, P.choff);
+    a.chunk_cluster = at<int>(ctx, P.chunk_cluster);
+    a.nchunks = at<int>(ctx, P.nchunks);
+    a.perm = at<int>(ctx, P.perm);
+    a.part = at<float>(ctx, P.part);
+    a.pe = at<double>(ctx, P.pe);
+    a.pnch = at<long long>(ctx, P.pnch);
+    a.S = at<double>(ctx, P.S);
+    a.counter = at<unsigned int>(ctx, P.counter);
+    a.st = at<SolveState>(ctx, P.st);
+    return a;
+}
+
+PackArgs pack_args(kmeans_ctx* ctx, const Plan& P, int d, int K)
+{
+    PackArgs p;
+    memset(&p, 0, sizeof(p));
+    p.K = K;
+    p.Kpad = P.Kpad;
+    p.d = d;
+    p.dpad = P.dpad;
+    p.nsets = 2;
+    p.src64[0] = at<double>(ctx, P.C64);
+    p.src64[1] = at<double>(ctx, P.CAU);
+    p.cb[0] = at<__nv_bfloat16>(ctx, P.cb0);
+    p.cb[1] = at<__nv_bfloat16>(ctx, P.cb1);
+    p.cn[0] = at<float>(ctx, P.cn0);
+    p.cn[1] = at<float>(ctx, P.cn1);
+    p.c32[0] = at<float>(ctx, P.c32_0);
+    p.c32[1] = at<float>(ctx, P.c32_1);
+    p.st = at<SolveState>(ctx, P.st);
+    return p;
+}
+
+bool dense_maps(kmeans_ctx* ctx, const Plan& P, const void* Xb, int64_t N, int d, void* tmX, void* tmC0, void* tmC1)
+{
+    return make_tmap_bf16(tmX, Xb, N, d, 128) &&
+           make_tmap_bf16(tmC0, at<void>(ctx, P.cb0), P.Kpad, P.dpad, 256) &&
+           make_tmap_bf16(tmC1, at<void>(ctx, P.cb1), P.Kpad, P.dpad, 256);
+}
 
 Launch make_launch(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, const void* C0,
                    const kmeans_params& p, void* C_out, int32_t* rho_out)
@@ -336,12 +502,68 @@ Launch make_launch(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, 
     ma.c32[0] = at<float>(ctx, P.c32_0);
     ma.c32[1] = at<float>(ctx, P.c32_1);
     ma.st = L.st;
+
+    L.nsm = ctx->nsm;
+    L.X32 = reinterpret_cast<const float*>(X->X);
+    if (P.dense) {
+        fa.part_f64 = 1;                 // S: FP64 residual sums per cluster, one "partial block"
+        fa.fuse_mix = 0;
+        fa.fp32_path = 0;
+        ma.fp32_path = 0;                // the mix only writes C; the BF16 packing is separate
+        DenseArgs& da = L.da;
+        da = dense_args(ctx, P, L.X32, X->N, d, K);
+        da.thr = thr;
+        da.lloyd_only = p.lloyd_only;
+        da.eps1 = p.eps1;
+        da.eps2 = p.eps2;
+        da.m_max = L.m_max;
+        da.max_iter = p.max_iter;
+        L.pk = pack_args(ctx, P, d, K);
+        L.pk.check_done = 1;
+        L.maps_ok = dense_maps(ctx, P, X->X_bf16, X->N, d, L.tmX, L.tmC0, L.tmC1);
+    }
     return L;
+}
+
+// One dense pass (assignment, rescoring, update chain with the controller) in the given mode.
+cudaError_t dense_pass(const Launch& L, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s,
+                       bool assign = true)
+{
+    DenseArgs a = L.da;
+    a.mode = mode;
+    a.use_cond = use_cond;
+    a.cond = h;
+    cudaError_t e = cudaSuccess;
+    if (assign) e = launch_dense_pass(a, L.tmX, L.tmC0, L.tmC1, L.nsm, s);
+    if (e == cudaSuccess) e = launch_dense_update(a, L.P.nbk, L.P.max_chunks, s);
+    return e;
 }
 
 // Prologue: C^0 -> P^0 -> G^0 = C^1 (Algorithm 1's first line).
 cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditionalHandle h)
 {
+    if (L.P.dense) {
+        cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
+        if (e == cudaSuccess)
+            e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
+                            nullptr, L.st, L.p.m_init, L.m_max, s, 0);
+        if (e == cudaSuccess) e = launch_xnorm(L.X32, L.N, L.d, const_cast<float*>(L.da.xnorm), L.st, L.nsm, s);
+        PackArgs pk = L.pk;
+        pk.nsets = 1;
+        pk.check_done = 0;
+        if (e == cudaSuccess) e = launch_pack_dense(pk, s);
+        if (e == cudaSuccess) e = dense_pass(L, MODE_INIT, 0, h, s);
+        FinArgs f = L.fa;
+        f.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+        MixArgs m = L.ma;
+        m.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+        pk = L.pk;
+        pk.check_done = 0;
+        if (e == cudaSuccess) e = launch_pack_dense(pk, s);
+        return e;
+    }
     cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
     if (e == cudaSuccess)
         e = launch_prep(L.C0, L.f64, L.K, L.d, L.P.Kpad, L.P.DP, L.ma.C64, const_cast<float*>(L.ma.origin),
@@ -366,6 +588,20 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
 // update + history + least squares, accelerated iterate (which also ends the graph loop).
 cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h)
 {
+    if (L.P.dense) {
+        cudaError_t e = dense_pass(L, MODE_TRIAL, use_cond, h, s);
+        if (e == cudaSuccess) e = dense_pass(L, MODE_REVERT, use_cond, h, s);
+        FinArgs f = L.fa;
+        f.mode = MODE_TRIAL;
+        f.use_cond = use_cond;
+        f.cond = h;
+        if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+        MixArgs m = L.ma;
+        m.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+        if (e == cudaSuccess) e = launch_pack_dense(L.pk, s);
+        return e;
+    }
     PassArgs a = L.pa;
     a.mode = MODE_TRIAL;
     a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
@@ -390,10 +626,15 @@ cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraph
 // Epilogue: the energy of (P^t, G^t) if the loop stopped at max_iter, results and info.
 cudaError_t launch_epilogue(const Launch& L, cudaStream_t s)
 {
-    PassArgs a = L.pa;
-    a.mode = MODE_EPI;
-    a.flags = F_ENERGY;
-    cudaError_t e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    cudaError_t e;
+    if (L.P.dense) {
+        e = dense_pass(L, MODE_EPI, 0, 0, s, false);
+    } else {
+        PassArgs a = L.pa;
+        a.mode = MODE_EPI;
+        a.flags = F_ENERGY;
+        e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    }
     if (e == cudaSuccess)
         e = launch_epi(L.f64, L.st, L.ma.C64, L.ma.CAU, L.C_out, (size_t)L.K * L.d, L.rhoA, L.rhoB, L.rho_out, L.N,
                        L.info, s);
@@ -508,6 +749,7 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     key.arena = ctx->arena;
     key.arena_bytes = ctx->arena_bytes;
     const Launch L = make_launch(ctx, P, X, K, C0, p, C_out, rho_out);
+    if (!L.maps_ok) return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
     const bool use_graph = graph_mode();
     if (use_graph && (!ctx->have_graph || memcmp(&key, &ctx->key, sizeof(key)) != 0)) {
         kmeans_status s = record_graph(ctx, L);
@@ -541,6 +783,88 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     }
     if (di->status == KM_ENONFINITE) return fail(ctx, KM_ENONFINITE, "X contains NaN or Inf");
     if (di->status == KM_ETIMEOUT) return fail(ctx, KM_ETIMEOUT, "iteration guard tripped");
+    return KM_OK;
+}
+
+// ---- standalone calls on the dense path
+kmeans_status dense_pack_user(kmeans_ctx* ctx, const Plan& P, const void* C, int d, int K)
+{
+    PackArgs pk = pack_args(ctx, P, d, K);
+    pk.nsets = 1;
+    pk.src64[0] = nullptr;
+    pk.src32 = reinterpret_cast<const float*>(C);
+    pk.st = nullptr;
+    pk.check_done = 0;
+    KM_CUDA(launch_pack_dense(pk, ctx->stream));
+    return KM_OK;
+}
+
+int rowred_blocks(kmeans_ctx* ctx) { return ctx->nsm * 4 < 4096 ? ctx->nsm * 4 : 4096; }
+
+kmeans_status dense_assign_call(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, const void* C, int K,
+                                int32_t* rho, const int32_t* rho_prev, int64_t* n_changed, void* dmin)
+{
+    kmeans_status s = ensure_arena(ctx, P.total);
+    if (s != KM_OK) return s;
+    const float* X32 = reinterpret_cast<const float*>(X->X);
+    DenseArgs a = dense_args(ctx, P, X32, X->N, X->d, K);
+    a.mode = MODE_STANDALONE;
+    a.rho_out = rho;
+    a.rho_prev = rho_prev;
+    a.out_nch = reinterpret_cast<long long*>(n_changed);
+    alignas(64) unsigned char tmX[128], tmC[128], tmC1[128];
+    if (!dense_maps(ctx, P, X->X_bf16, X->N, X->d, tmX, tmC, tmC1))
+        return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    KM_CUDA(launch_xnorm(X32, X->N, X->d, const_cast<float*>(a.xnorm), nullptr, ctx->nsm, ctx->stream));
+    if ((s = dense_pack_user(ctx, P, C, X->d, K)) != KM_OK) return s;
+    KM_CUDA(launch_dense_pass(a, tmX, tmC, tmC, ctx->nsm, ctx->stream));
+    if (n_changed || dmin)
+        KM_CUDA(launch_drow(a, rho, reinterpret_cast<float*>(dmin), at<double>(ctx, P.rowe), at<long long>(ctx, P.rown),
+                            rowred_blocks(ctx), ctx->stream));
+    return KM_OK;
+}
+
+kmeans_status dense_energy_call(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, const void* C, int K,
+                                const int32_t* rho, double* E)
+{
+    kmeans_status s;
+    DenseArgs a = dense_args(ctx, P, reinterpret_cast<const float*>(X->X), X->N, X->d, K);
+    a.mode = MODE_STANDALONE;
+    a.out_E = E;
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    if ((s = dense_pack_user(ctx, P, C, X->d, K)) != KM_OK) return s;
+    KM_CUDA(launch_drow(a, rho, nullptr, at<double>(ctx, P.rowe), at<long long>(ctx, P.rown), rowred_blocks(ctx),
+                        ctx->stream));
+    return KM_OK;
+}
+
+kmeans_status dense_update_call(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, const int32_t* rho, int K,
+                                const void* C_prev, void* C_out, int64_t* counts)
+{
+    kmeans_status s;
+    DenseArgs a = dense_args(ctx, P, reinterpret_cast<const float*>(X->X), X->N, X->d, K);
+    a.mode = MODE_STANDALONE;
+    a.rho_out = const_cast<int32_t*>(rho);     // read-only here: the labels of the update
+    KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    if ((s = dense_pack_user(ctx, P, C_prev, X->d, K)) != KM_OK) return s;
+    KM_CUDA(launch_dense_update(a, P.nbk, P.max_chunks, ctx->stream));
+    FinArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = MODE_STANDALONE;
+    f.K = K;
+    f.d = X->d;
+    f.nb = 1;
+    f.part_f64 = 1;
+    f.pS = a.S;
+    f.pCnt = a.counts;
+    f.KB = P.KB;
+    f.C_ref = C_prev;
+    f.C_out = C_out;
+    f.out_f64 = 0;
+    f.counts = counts;
+    f.st = a.st;
+    KM_CUDA(launch_fin(f, P.nfin, ctx->stream));
     return KM_OK;
 }
 
@@ -639,10 +963,10 @@ kmeans_status kmeans_assign(kmeans_ctx* ctx, const kmeans_data* X, const void* C
     if (s != KM_OK) return s;
     if (!C || !rho) return fail(ctx, KM_EINVAL, "C and rho must not be NULL");
     if (n_changed && !rho_prev) return fail(ctx, KM_EINVAL, "n_changed needs rho_prev");
-    if (X->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, X->prec, 0, false, P, false)) != KM_OK) return s;
+    if (P.dense) return dense_assign_call(ctx, P, X, C, K, rho, rho_prev, n_changed, dmin);
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, X->prec);
     a.mode = MODE_STANDALONE;
@@ -668,10 +992,11 @@ kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C
     if (s != KM_OK) return s;
     if (!C || !rho || !E) return fail(ctx, KM_EINVAL, "C, rho and E must not be NULL");
     KM_CUDA(cudaSetDevice(ctx->device));
-    const int prec = X->prec == KM_F64 ? KM_F64 : KM_F32;
+    const int prec = X->prec == KM_F64 ? KM_F64 : (X->d > 16 ? KM_BF16_F32 : KM_F32);
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P, false)) != KM_OK) return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    if (P.dense) return dense_energy_call(ctx, P, X, C, K, rho, E);
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
     a.mode = MODE_STANDALONE;
     a.flags = F_ENERGY | (prec != KM_F64 ? F_PACK : 0);
@@ -693,10 +1018,11 @@ kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t
     if (s != KM_OK) return s;
     if (!rho || !C_prev || !C_out) return fail(ctx, KM_EINVAL, "rho, C_prev and C_out must not be NULL");
     KM_CUDA(cudaSetDevice(ctx->device));
-    const int prec = X->prec == KM_F64 ? KM_F64 : KM_F32;
+    const int prec = X->prec == KM_F64 ? KM_F64 : (X->d > 16 ? KM_BF16_F32 : KM_F32);
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, prec, 0, false, P)) != KM_OK) return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    if (P.dense) return dense_update_call(ctx, P, X, rho, K, C_prev, C_out, counts);
     PassArgs a = base_pass(ctx, P, X->X, X->N, K, prec);
     a.mode = MODE_STANDALONE;
     a.flags = F_BINS | (prec != KM_F64 ? F_PACK : 0);
@@ -735,7 +1061,6 @@ kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     kmeans_params p;
     if (params) p = *params; else kmeans_default_params(&p);
     if ((s = validate_params(ctx, p)) != KM_OK) return s;
-    if (X->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
     if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P)) != KM_OK) return s;
@@ -755,7 +1080,6 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t 
     kmeans_params p;
     if (params) p = *params; else kmeans_default_params(&p);
     if ((s = validate_params(ctx, p)) != KM_OK) return s;
-    if (Xh->prec == KM_BF16_F32) return fail(ctx, KM_EINVAL, "KM_BF16_F32 needs d > 16 in this build");
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
     if ((s = make_plan(ctx, Xh->N, Xh->d, K, Xh->prec, p.lloyd_only ? 0 : p.m_max, true, P)) != KM_OK) return s;
@@ -768,6 +1092,11 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t 
     kmeans_data Xd = *Xh;
     Xd.X = at<void>(ctx, P.hX);
     Xd.X_bf16 = nullptr;
+    if (P.dense) {
+        KM_CUDA(cudaMemcpyAsync(at<void>(ctx, P.hXb), Xh->X_bf16, (size_t)Xh->N * Xh->d * 2, cudaMemcpyHostToDevice,
+                                ctx->stream));
+        Xd.X_bf16 = at<void>(ctx, P.hXb);
+    }
     s = solve_device(ctx, &Xd, K, at<void>(ctx, P.hC0), p, at<void>(ctx, P.hCout), at<int32_t>(ctx, P.hRho),
                      info, P);
     if (s != KM_OK && s != KM_ENONFINITE) return s;

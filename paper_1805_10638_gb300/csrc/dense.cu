@@ -1,0 +1,859 @@
+// Dense assignment (d = 17..128, d % 8 == 0) on sm_103a tensor cores, and the dense update.
+//
+// Assignment (Eq. 3): scores s_ij = ||c_j||^2 - 2 x_i.c_j with x.c from tcgen05.mma kind::f16
+// (BF16 operands, FP32 accumulation in TMEM).  One persistent CTA per SM walks 128-row tiles of X;
+// per tile it streams the centroids in tiles of 256 through a 2-stage shared-memory ring fed by
+// TMA (128-byte swizzle, K-major), and the epilogue warps read the 128 x 256 FP32 accumulator
+// from TMEM (double buffered, so the MMA of the next centroid tile overlaps the epilogue of this
+// one) and keep a per-row top-2 (value, lowest index).  Warp roles: warp 0 issues TMA, warp 1
+// allocates TMEM and issues the MMAs (one thread), warps 4..11 are the epilogue (two warps per
+// TMEM lane quadrant, each taking half of the columns).  Every wait on an mbarrier is bounded: on
+// timeout the kernel records an error and all roles leave their loops.
+//
+// Near ties: the BF16 scores carry a rigorous rounding-error bound
+//   B = (4 u_b + 2 d u) |x| max|c| + 2 u max|c|^2     (u_b = 2^-9, u = 2^-24);
+// rows whose top-2 gap is within 2B are queued and rescored over all K in FP32, direct form.
+//
+// Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
+// an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
+// fixed-order segment sums of the residuals x_i - c_j per cluster (FP32 within chunks of 64 rows,
+// FP64 across chunks).  The energy (Eq. 1) comes out of the same segment sums.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "controller.cuh"
+#include "dense.cuh"
+
+namespace km {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int TM = 128;            // rows per tile (MMA M)
+constexpr int TN = 256;            // centroids per tile (MMA N)
+constexpr int KBLK = 64;           // bf16 per 128-byte swizzle row
+constexpr int CST = 2;             // centroid-tile stages
+constexpr int DTHREADS = 384;      // 12 warps
+constexpr int SEG = 64;            // rows per segment-sum chunk
+constexpr unsigned SPIN_LIMIT = 1u << 28;
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and *abort set) if the phase did not complete within the spin limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort)
+{
+    for (unsigned i = 0; i < SPIN_LIMIT; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+    return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                     tmem_d),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Solver-mode gate shared by every kernel of a pass: returns the centroid set (0 = C^t,
+// 1 = C_AU) or -1 if this launch has nothing to do.
+__device__ __forceinline__ int pass_set(const SolveState* st, int mode)
+{
+    if (mode == MODE_STANDALONE) return 0;
+    if (mode == MODE_EPI) return (st->converged || st->status != KM_OK) ? -1 : 1;
+    if (st->done) return -1;
+    if (mode == MODE_REVERT) return st->revert ? 1 : -1;
+    return 0;
+}
+__device__ __forceinline__ int32_t* pass_rho(const DenseArgs& a, const SolveState* st)
+{
+    return a.mode == MODE_STANDALONE ? a.rho_out : a.rho_pair[st->cur];
+}
+
+// ------------------------------------------------------------------ assignment (tcgen05)
+struct SmemPlan {
+    uint32_t x, c, cn, merge, bar, slot, abort, total;
+};
+__host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
+{
+    SmemPlan p;
+    uint32_t o = 0;
+    p.x = o;     o += 2u * nkb * TM * 128;
+    p.c = o;     o += (uint32_t)CST * nkb * TN * 128;
+    p.cn = o;    o += (uint32_t)Kpad * 4;
+    p.merge = o; o += TM * 16;
+    p.bar = (o + 7) & ~7u; o = p.bar + 16 * 8;
+    p.slot = o;  o += 8;
+    p.abort = o; o += 16;
+    p.total = o + 1024;   // room to align the base to 1024 bytes
+    return p;
+}
+
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_dense_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC0,
+                   const __grid_constant__ CUtensorMap tmC1, DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int nkb = a.dpad / KBLK;
+    const SmemPlan P = dense_smem(nkb, a.Kpad);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sX = sbase + P.x, sC = sbase + P.c;
+    float* s_cn = reinterpret_cast<float*>(smem + P.cn);
+    float* s_merge = reinterpret_cast<float*>(smem + P.merge);
+    const uint32_t bar = sbase + P.bar;
+    // barriers: xfull[2] xempty[2] cfull[2] cempty[2] afull[2] aempty[2]
+    const uint32_t xfull = bar, xempty = bar + 16, cfull = bar + 32, cempty = bar + 48, afull = bar + 64,
+                   aempty = bar + 80;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem + P.slot);
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + P.abort);
+    const CUtensorMap* tmC = set ? &tmC1 : &tmC0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nct = a.Kpad / TN, nks = a.dpad / 16;
+    const int ntiles = (int)((a.N + TM - 1) / TM);
+    const uint32_t xbytes = (uint32_t)nkb * TM * 128, cbytes = (uint32_t)nkb * TN * 128;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(xfull + 8 * i, 1);
+            mbar_init(xempty + 8 * i, 1);
+            mbar_init(cfull + 8 * i, 1);
+            mbar_init(cempty + 8 * i, 1);
+            mbar_init(afull + 8 * i, 1);
+            mbar_init(aempty + 8 * i, 8);
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const float* cn = a.cn[set];
+    for (int i = tid; i < a.Kpad; i += blockDim.x) s_cn[i] = cn[i];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            uint32_t xit = 0, cit = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++xit) {
+                const uint32_t xs = xit & 1;
+                if (xit >= 2 && !mbar_wait(xempty + 8 * xs, ((xit >> 1) - 1) & 1, abort)) break;
+                mbar_expect_tx(xfull + 8 * xs, xbytes);
+                for (int kb = 0; kb < nkb; ++kb)
+                    tma_load_2d(sX + xs * xbytes + kb * (TM * 128), &tmX, kb * KBLK, tile * TM, xfull + 8 * xs);
+                for (int ct = 0; ct < nct; ++ct, ++cit) {
+                    const uint32_t cs = cit % CST;
+                    if (cit >= CST && !mbar_wait(cempty + 8 * cs, ((cit / CST) - 1) & 1, abort)) break;
+                    mbar_expect_tx(cfull + 8 * cs, cbytes);
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_2d(sC + cs * cbytes + kb * (TN * 128), tmC, kb * KBLK, ct * TN, cfull + 8 * cs);
+                }
+            }
+            if (*abort) {
+                // let the copies this thread issued land before the block exits (bounded)
+                for (uint32_t s2 = 0; s2 < 2; ++s2) {
+                    if (xit > s2) {
+                        const uint32_t n = (xit - 1 - s2);
+                        const uint32_t st2 = n & 1;
+                        for (unsigned i = 0; i < (1u << 20) && !mbar_try(xfull + 8 * st2, (n >> 1) & 1); ++i) {}
+                    }
+                    if (cit > s2) {
+                        const uint32_t n = (cit - 1 - s2);
+                        const uint32_t st2 = n % CST;
+                        for (unsigned i = 0; i < (1u << 20) && !mbar_try(cfull + 8 * st2, (n / CST) & 1); ++i) {}
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            // kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                   ((uint32_t)(TM >> 4) << 24);
+            uint32_t xit = 0, cit = 0, ait = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++xit) {
+                const uint32_t xs = xit & 1;
+                if (!mbar_wait(xfull + 8 * xs, (xit >> 1) & 1, abort)) break;
+                bool ok = true;
+                for (int ct = 0; ct < nct; ++ct, ++cit, ++ait) {
+                    const uint32_t cs = cit % CST, ab = ait & 1;
+                    if (!mbar_wait(cfull + 8 * cs, (cit / CST) & 1, abort)) { ok = false; break; }
+                    if (ait >= 2 && !mbar_wait(aempty + 8 * ab, ((ait >> 1) - 1) & 1, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    for (int ks = 0; ks < nks; ++ks) {
+                        const uint32_t kb = ks >> 2, off = (ks & 3) * 32;
+                        const uint64_t ad = sdesc(sX + xs * xbytes + kb * (TM * 128) + off);
+                        const uint64_t bd = sdesc(sC + cs * cbytes + kb * (TN * 128) + off);
+                        mma_bf16(tmem + ab * TN, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(cempty + 8 * cs);
+                    mma_commit(afull + 8 * ab);
+                }
+                if (!ok) break;
+                mma_commit(xempty + 8 * xs);
+            }
+        }
+    } else if (warp >= 4) {   // epilogue
+        const int q = warp & 3, h = (warp - 4) >> 2;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        float cmax2 = 0.f;
+        for (int j = 0; j < a.K; ++j) cmax2 = fmaxf(cmax2, s_cn[j]);
+        const float cmax = sqrtf(cmax2);
+        int32_t* rho = pass_rho(a, a.st);
+        volatile int* s_go = reinterpret_cast<volatile int*>(smem + P.abort + 4);
+        uint32_t ait = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            float b1 = __int_as_float(0x7f800000), b2 = b1;
+            int i1 = 0;
+            bool ok = true;
+            for (int ct = 0; ct < nct; ++ct, ++ait) {
+                const uint32_t ab = ait & 1;
+                // after a failed wait the remaining steps are skipped, but every warp still
+                // runs the same sequence of named barriers below
+                if (ok && !mbar_wait(afull + 8 * ab, (ait >> 1) & 1, abort)) ok = false;
+                if (ok) {
+                    tc_fence_after();
+#pragma unroll 1
+                    for (int c16 = 0; c16 < TN / 2 / 16; ++c16) {
+                        const int col = h * (TN / 2) + c16 * 16;
+                        float v[16];
+                        tmem_ld16(tmem + lane_base + ab * TN + col, v);
+                        const int j0 = ct * TN + col;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float s = fmaf(-2.f, v[e], s_cn[j0 + e]);
+                            b2 = fminf(b2, fmaxf(b1, s));
+                            const bool p = s < b1;
+                            b1 = p ? s : b1;
+                            i1 = p ? j0 + e : i1;
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(aempty + 8 * ab);
+            }
+            // merge the two column halves of each row (lexicographic on (value, index))
+            const int r = q * 32 + lane;
+            if (h == 1) {
+                s_merge[4 * r] = b1;
+                s_merge[4 * r + 1] = b2;
+                s_merge[4 * r + 2] = __int_as_float(i1);
+            }
+            named_bar(1, 256);
+            if (h == 0 && ok) {
+                const float o1 = s_merge[4 * r], o2 = s_merge[4 * r + 1];
+                const int oi = __float_as_int(s_merge[4 * r + 2]);
+                const float hi1 = fmaxf(b1, o1);
+                const bool other = (o1 < b1) || (o1 == b1 && oi < i1);
+                const float nb1 = other ? o1 : b1;
+                const int ni1 = other ? oi : i1;
+                const float nb2 = fminf(hi1, fminf(b2, o2));
+                const int64_t row = (int64_t)tile * TM + r;
+                if (row < a.N) {
+                    const float xn = a.xnorm[row];
+                    const float bnd = a.bcoef_a * xn * cmax + a.bcoef_b * cmax2;
+                    rho[row] = ni1;
+                    if (!(nb2 - nb1 > 2.f * bnd)) {
+                        const unsigned pos = atomicAdd(a.qcount, 1u);
+                        a.queue[pos] = (int)row;
+                    }
+                }
+            }
+            if (tid == 128) *s_go = (*abort == 0) ? 1 : 0;   // one snapshot for all epilogue warps
+            named_bar(1, 256);
+            const int go = *s_go;
+            named_bar(1, 256);
+            if (!go) break;
+        }
+    }
+    __syncthreads();
+    if (*abort && tid == 0) atomicExch(a.err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    }
+}
+
+// ------------------------------------------------------------------ near-tie rescoring
+// One warp per queued row: direct-form FP32 distances to all K centroids (lanes split K,
+// ascending j per lane), lexicographic (distance, index) butterfly.
+__global__ void __launch_bounds__(256) k_rescore(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    __shared__ float sx[8][128];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned n = *a.qcount;
+    const float* X = a.X;
+    const float* C = a.c32[set];
+    const int d = a.d, K = a.K;
+    int32_t* rho = pass_rho(a, a.st);
+    for (unsigned q = blockIdx.x * 8 + w; q < n; q += gridDim.x * 8) {
+        const int64_t row = a.queue[q];
+        for (int k = lane; k < d; k += 32) sx[w][k] = X[row * d + k];
+        __syncwarp();
+        float bd = __int_as_float(0x7f800000);
+        int bj = K;
+        for (int j = lane; j < K; j += 32) {
+            const float* c = C + (size_t)j * d;
+            float acc = 0.f;
+            for (int k = 0; k < d; ++k) {
+                const float t = sx[w][k] - c[k];
+                acc = fmaf(t, t, acc);
+            }
+            if (acc < bd) {
+                bd = acc;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, bd, o);
+            const int oj = __shfl_xor_sync(FULL, bj, o);
+            if (ob < bd || (ob == bd && oj < bj)) {
+                bd = ob;
+                bj = oj;
+            }
+        }
+        if (lane == 0) rho[row] = bj < K ? bj : 0;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ packing
+// Per centroid (one warp): BF16 copy (zero-padded to dpad, pad rows zero), ||c||^2 in FP32
+// (+inf for pad rows) and the FP32 copy used by the rescoring and the residuals.
+__global__ void __launch_bounds__(256) k_pack_dense(PackArgs a)
+{
+    if (a.st && a.check_done && a.st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= a.Kpad) return;
+    for (int s = 0; s < a.nsets; ++s) {
+        const double* src64 = a.src64[s];
+        const float* src32 = a.src32;
+        double nrm = 0.0;
+        for (int k = lane; k < a.dpad; k += 32) {
+            double v = 0.0;
+            if (j < a.K && k < a.d) {
+                v = src64 ? src64[(size_t)j * a.d + k] : (double)src32[(size_t)j * a.d + k];
+                a.c32[s][(size_t)j * a.d + k] = (float)v;
+            }
+            a.cb[s][(size_t)j * a.dpad + k] = __float2bfloat16_rn((float)v);
+            nrm += v * v;
+        }
+        nrm = warp_sum(nrm);
+        if (lane == 0) a.cn[s][j] = j < a.K ? (float)nrm : __int_as_float(0x7f800000);
+    }
+}
+
+// Row norms ||x|| (FP32, for the error bound) and the non-finite check, once per solve.
+__global__ void __launch_bounds__(256) k_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st)
+{
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* x = X + i * d;
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) {
+            bad |= !isfinite(x[k]);
+            s = fmaf(x[k], x[k], s);
+        }
+        xnorm[i] = sqrtf(s);
+    }
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0 && st) st->status = KM_ENONFINITE;
+}
+
+// ------------------------------------------------------------------ update chain
+// 1. Per-block label histograms (integer atomics, order-independent) and the change count.
+__global__ void __launch_bounds__(256) k_dcount(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    extern __shared__ int s_hist[];
+    const int K = a.K;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) s_hist[j] = 0;
+    __syncthreads();
+    const int32_t* rho = a.mode == MODE_EPI ? a.rho_pair[a.st->cur] : pass_rho(a, a.st);
+    const int32_t* prev = a.mode == MODE_STANDALONE ? a.rho_prev
+                          : (a.mode == MODE_EPI ? nullptr : a.rho_pair[a.st->cur ^ 1]);
+    const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_block;
+    const int64_t r1 = min(a.N, r0 + a.rows_per_block);
+    long long nch = 0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const int l = rho[i];
+        atomicAdd(&s_hist[l], 1);
+        if (prev) nch += prev[i] != l;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += blockDim.x) a.hist[(size_t)j * gridDim.x + blockIdx.x] = s_hist[j];
+    nch = warp_sum_ll(nch);
+    __shared__ long long s_n[8];
+    if ((threadIdx.x & 31) == 0) s_n[threadIdx.x >> 5] = nch;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_n[w];
+        a.pnch[blockIdx.x] = t;
+    }
+}
+
+// 2. One block: per cluster, the exclusive scan over blocks (warp per cluster), then the scan
+//    over clusters of the totals (offsets) and of the chunk counts.
+__global__ void __launch_bounds__(1024) k_dscan(DenseArgs a, int nbk)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, K = a.K;
+    for (int j = w; j < K; j += 32) {
+        int* h = a.hist + (size_t)j * nbk;
+        int run = 0;
+        for (int b0 = 0; b0 < nbk; b0 += 32) {
+            const int v = b0 + lane < nbk ? h[b0 + lane] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (b0 + lane < nbk) h[b0 + lane] = run + incl - v;
+            run += __shfl_sync(FULL, incl, 31);
+        }
+        if (lane == 0) a.counts[j] = run;
+    }
+    __syncthreads();
+    // scan over clusters: offsets of each cluster in perm, and of its chunks
+    __shared__ int s_tot[32], s_ch[32];
+    int tot = 0, chn = 0;
+    const int per = (K + 1023) / 1024;
+    const int j0 = threadIdx.x * per;
+    for (int j = j0; j < min(K, j0 + per); ++j) {
+        tot += a.counts[j];
+        chn += (a.counts[j] + SEG - 1) / SEG;
+    }
+    int it = tot, ic = chn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t1 = __shfl_up_sync(FULL, it, o), t2 = __shfl_up_sync(FULL, ic, o);
+        if (lane >= o) {
+            it += t1;
+            ic += t2;
+        }
+    }
+    if (lane == 31) {
+        s_tot[w] = it;
+        s_ch[w] = ic;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int v1 = s_tot[lane], v2 = s_ch[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t1 = __shfl_up_sync(FULL, v1, o), t2 = __shfl_up_sync(FULL, v2, o);
+            if (lane >= o) {
+                v1 += t1;
+                v2 += t2;
+            }
+        }
+        s_tot[lane] = v1 - s_tot[lane];
+        s_ch[lane] = v2 - s_ch[lane];
+    }
+    __syncthreads();
+    int off = s_tot[w] + it - tot, coff = s_ch[w] + ic - chn;
+    for (int j = j0; j < min(K, j0 + per); ++j) {
+        a.off[j] = off;
+        a.choff[j] = coff;
+        const int nc = (a.counts[j] + SEG - 1) / SEG;
+        for (int c = 0; c < nc; ++c) a.chunk_cluster[coff + c] = j;
+        off += a.counts[j];
+        coff += nc;
+    }
+    if (threadIdx.x == 1023) {
+        a.off[K] = off;
+        *a.nchunks = coff;
+    }
+}
+
+// 3. Stable scatter of row indices by label: one warp per block of rows, rows in order.
+__global__ void __launch_bounds__(32) k_dscatter(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    extern __shared__ int s_run[];   // [K] running positions, then [rows_per_block] labels
+    int* s_lab = s_run + a.K;
+    const int lane = threadIdx.x, K = a.K;
+    const int32_t* rho = a.mode == MODE_EPI ? a.rho_pair[a.st->cur] : pass_rho(a, a.st);
+    const int b = blockIdx.x, nbk = gridDim.x;
+    const int64_t r0 = (int64_t)b * a.rows_per_block;
+    const int nr = (int)min((int64_t)a.rows_per_block, a.N - r0);
+    for (int j = lane; j < K; j += 32) s_run[j] = a.off[j] + a.hist[(size_t)j * nbk + b];
+    for (int i = lane; i < nr; i += 32) s_lab[i] = rho[r0 + i];
+    __syncwarp();
+    for (int g = 0; g < nr; g += 32) {
+        const bool v = g + lane < nr;
+        const int l = v ? s_lab[g + lane] : -1;
+        const unsigned mm = __match_any_sync(FULL, l);
+        if (v) {
+            const int rank = __popc(mm & ((1u << lane) - 1u));
+            a.perm[s_run[l] + rank] = (int)(r0 + g + lane);
+        }
+        __syncwarp();
+        if (v && lane == __ffs(mm) - 1) s_run[l] += __popc(mm);
+        __syncwarp();
+    }
+}
+
+// 4. Residual sums per chunk of <= 64 rows of one cluster (rows in perm order), FP32 within the
+//    chunk, and the chunk's energy.  One warp per chunk, lanes over d.
+__global__ void __launch_bounds__(256) k_dsegsum(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, d = a.d;
+    const int nch = *a.nchunks;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= nch) return;
+    const int j = a.chunk_cluster[c];
+    const int lc = c - a.choff[j];
+    const int p0 = a.off[j] + lc * SEG;
+    const int p1 = min(a.off[j + 1], p0 + SEG);
+    const float* X = a.X;
+    float cj[4], acc[4];
+    const bool use64 = a.mode == MODE_EPI;   // G^t was not packed when the loop stopped at max_iter
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int k = lane + 32 * u;
+        cj[u] = k < d ? (use64 ? (float)a.c64[1][(size_t)j * d + k] : a.c32[set][(size_t)j * d + k]) : 0.f;
+        acc[u] = 0.f;
+    }
+    float e = 0.f;
+    for (int p = p0; p < p1; ++p) {
+        const int64_t row = a.perm[p];
+        const float* x = X + row * d;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = lane + 32 * u;
+            if (k < d) {
+                const float r = x[k] - cj[u];
+                acc[u] += r;
+                e = fmaf(r, r, e);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int k = lane + 32 * u;
+        if (k < d) a.part[(size_t)c * d + k] = acc[u];
+    }
+    const double ew = warp_sum((double)e);
+    if (lane == 0) a.pe[c] = ew;
+}
+
+// 5. Per cluster: fixed-order FP64 sum of its chunk partials -> S [K][d]; the last block sums the
+//    energy and the change count in a fixed order and runs the controller.
+__global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, d = a.d, K = a.K;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j < K) {
+        const int c0 = a.choff[j], nc = (a.counts[j] + SEG - 1) / SEG;
+        for (int k = lane; k < d; k += 32) {
+            double s = 0.0;
+            for (int c = c0; c < c0 + nc; ++c) s += (double)a.part[(size_t)(c)*d + k];
+            a.S[(size_t)j * d + k] = s;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    __shared__ double s_red[8];
+    __shared__ long long s_rl[8];
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nch = *a.nchunks;
+    double E = 0.0;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) E += __ldcg(a.pe + c);
+    long long ch = 0;
+    for (int b = threadIdx.x; b < nbk; b += blockDim.x) ch += __ldcg(a.pnch + b);
+    E = warp_sum(E);
+    ch = warp_sum_ll(ch);
+    if (lane == 0) {
+        s_red[threadIdx.x >> 5] = E;
+        s_rl[threadIdx.x >> 5] = ch;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    E = 0.0;
+    ch = 0;
+    for (int w = 0; w < 8; ++w) {
+        E += s_red[w];
+        ch += s_rl[w];
+    }
+    *a.counter = 0u;
+    if (a.mode == MODE_STANDALONE) {
+        if (a.out_E) *a.out_E = E;
+        if (a.out_nch) *a.out_nch = ch;
+        return;
+    }
+    if (a.mode != MODE_EPI) st->rescored += *a.qcount;
+    if (a.mode == MODE_EPI) {
+        st->E_final = E;
+    } else if (a.mode == MODE_INIT) {
+        st->passes += 1;
+        st->E_trial = E;
+    } else {
+        if (a.mode == MODE_TRIAL)
+            controller_trial(st, E, ch, a.thr, a.lloyd_only, a.eps1, a.eps2, a.m_max, a.max_iter);
+        else
+            controller_revert(st, E, ch, a.thr);
+        if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    }
+}
+
+// Standalone calls: per-row direct-form FP32 squared distance to the assigned centroid (optional
+// output), change count and energy; block partials summed in a fixed order by the last block.
+__global__ void __launch_bounds__(256) k_drow(DenseArgs a, const int32_t* rho_in, float* dmin, double* pe,
+                                              long long* pn)
+{
+    const int d = a.d;
+    const float* C = a.c32[0];
+    double e = 0.0;
+    long long nch = 0;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += T) {
+        const int j = rho_in[i];
+        const float* x = a.X + i * d;
+        const float* c = C + (size_t)j * d;
+        float acc = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float t = x[k] - c[k];
+            acc = fmaf(t, t, acc);
+        }
+        if (dmin) dmin[i] = acc;
+        e += acc;
+        if (a.rho_prev) nch += a.rho_prev[i] != j;
+    }
+    __shared__ double s_e[8];
+    __shared__ long long s_n[8];
+    e = warp_sum(e);
+    nch = warp_sum_ll(nch);
+    if ((threadIdx.x & 31) == 0) {
+        s_e[threadIdx.x >> 5] = e;
+        s_n[threadIdx.x >> 5] = nch;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double te = 0.0;
+        long long tn = 0;
+        for (int w = 0; w < 8; ++w) {
+            te += s_e[w];
+            tn += s_n[w];
+        }
+        pe[blockIdx.x] = te;
+        pn[blockIdx.x] = tn;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    double E = 0.0;
+    long long ch = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        E += __ldcg(pe + b);
+        ch += __ldcg(pn + b);
+    }
+    *a.counter = 0u;
+    if (a.out_E) *a.out_E = E;
+    if (a.out_nch) *a.out_nch = ch;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t dense_assign_smem(int dpad, int Kpad)
+{
+    return dense_smem(dpad / KBLK, Kpad).total;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] array, box = 64 columns x box_rows rows,
+// 128-byte swizzle, zero fill outside.
+bool make_tmap_bf16(void* map, const void* base, int64_t rows, int cols, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* tmC0, const void* tmC1, int nsm,
+                              cudaStream_t s)
+{
+    // assignment
+    cudaError_t e = cudaMemsetAsync(a.qcount, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = dense_assign_smem(a.dpad, a.Kpad);
+    e = cudaFuncSetAttribute(k_dense_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (int)((a.N + TM - 1) / TM);
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    k_dense_assign<<<grid, DTHREADS, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(tmX),
+                                                *reinterpret_cast<const CUtensorMap*>(tmC0),
+                                                *reinterpret_cast<const CUtensorMap*>(tmC1), a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rescore<<<nsm * 4, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cudaStream_t s)
+{
+    cudaError_t e;
+    k_dcount<<<nbk, 256, (size_t)a.K * 4, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_dscan<<<1, 1024, 0, s>>>(a, nbk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t sm_sc = (size_t)(a.K + a.rows_per_block) * 4;
+    if (sm_sc > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_dscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sc);
+        if (e != cudaSuccess) return e;
+    }
+    k_dscatter<<<nbk, 32, sm_sc, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_dsegsum<<<(max_chunks + 7) / 8, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    k_dsegfin<<<(a.K + 7) / 8, 256, 0, s>>>(a, nbk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,
+                        cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    k_drow<<<blocks, 256, 0, s>>>(a, rho_in, dmin, pe, pn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s)
+{
+    k_pack_dense<<<(p.Kpad * 32 + 255) / 256, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st, int nsm, cudaStream_t s)
+{
+    k_xnorm<<<nsm * 8, 256, 0, s>>>(X, N, d, xnorm, st);
+    return cudaGetLastError();
+}
+
+}  // namespace km

@@ -1,0 +1,79 @@
+// Declarations of the dense (tensor-core) assignment and the sort-based update.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "km_internal.cuh"
+
+namespace km {
+
+// Arguments shared by every kernel of one dense pass (assignment + rescoring + update chain).
+struct DenseArgs {
+    int64_t N;
+    int d;
+    int dpad;                 // d rounded up to 64 (BF16 K-blocks of 128 bytes)
+    int K;
+    int Kpad;                 // K rounded up to 256 (MMA N)
+    int mode;                 // PassMode
+    const float* X;           // [N][d] FP32
+    const float* xnorm;       // [N] ||x||
+    const float* cn[2];       // [Kpad] ||c||^2, +inf for pad rows; set 0 = C^t, set 1 = C_AU
+    const float* c32[2];      // [K][d] FP32 centroids
+    const double* c64[2];     // [K][d] FP64 centroids (C^t, C_AU)
+    float bcoef_a;            // error bound B = bcoef_a |x| max|c| + bcoef_b max|c|^2
+    float bcoef_b;
+    int32_t* rho_out;         // standalone output
+    const int32_t* rho_prev;  // standalone previous assignment (optional)
+    int32_t* rho_pair[2];     // solver ping-pong assignment
+    int* queue;               // [N] near-tie rows
+    unsigned int* qcount;
+    int* err;
+    // update chain
+    int rows_per_block;
+    int* hist;                // [K][nbk] per-block counts -> exclusive scans
+    int32_t* counts;          // [K]
+    int* off;                 // [K+1] cluster offsets in perm
+    int* choff;               // [K] first chunk of each cluster
+    int* chunk_cluster;       // [max_chunks]
+    int* nchunks;
+    int* perm;                // [N]
+    float* part;              // [max_chunks][d]
+    double* pe;               // [max_chunks]
+    long long* pnch;          // [nbk]
+    double* S;                // [K][d] residual sums (FP64)
+    unsigned int* counter;
+    double* out_E;
+    long long* out_nch;
+    // controller
+    SolveState* st;
+    long long thr;
+    int lloyd_only;
+    double eps1;
+    double eps2;
+    int m_max;
+    int max_iter;
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+};
+
+struct PackArgs {
+    int K, Kpad, d, dpad, nsets, check_done;
+    const double* src64[2];   // FP64 sources (solver) or NULL
+    const float* src32;       // FP32 source (standalone)
+    __nv_bfloat16* cb[2];     // [Kpad][dpad]
+    float* cn[2];             // [Kpad]
+    float* c32[2];            // [K][d]
+    SolveState* st;
+};
+
+size_t dense_assign_smem(int dpad, int Kpad);
+bool make_tmap_bf16(void* map, const void* base, int64_t rows, int cols, int box_rows);
+cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* tmC0, const void* tmC1, int nsm,
+                              cudaStream_t s);
+cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cudaStream_t s);
+cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s);
+cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,
+                        cudaStream_t s);
+cudaError_t launch_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st, int nsm, cudaStream_t s);
+
+}  // namespace km

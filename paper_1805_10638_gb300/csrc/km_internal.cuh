@@ -195,7 +195,7 @@ int fin_blocks(int K, int d, int* KB);
 cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
 cudaError_t launch_prep(const void* C0, bool f64, int K, int d, int Kpad, int DP, double* C64,
                         float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st, int m_init,
-                        int m_max, cudaStream_t s);
+                        int m_max, cudaStream_t s, int pack = 1);
 cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const double* CAU, void* C_out,
                        size_t n, const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N,
                        void* info, cudaStream_t s);

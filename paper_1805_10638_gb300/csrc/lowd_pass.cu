@@ -24,6 +24,7 @@
 // Determinism: per-cluster sums go to per-warp shared-memory bins; within a warp, lanes with the
 // same label are combined by the lowest such lane in lane order (__match_any_sync); warps are
 // combined in warp order and blocks in block order.  No floating-point atomics.
+#include "controller.cuh"
 #include "km_internal.cuh"
 
 #include <type_traits>
@@ -127,60 +128,6 @@ __device__ long long block_sum_ll(long long v, double* red)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += r[w];
     __syncthreads();
     return s;
-}
-
-// Head of Algorithm 1 after P^t = Assign(C^t): convergence, dynamic m, safeguard.
-__device__ void controller_trial(const PassArgs& a, SolveState* st, double E, long long nch)
-{
-    st->body_runs += 1;
-    if (st->status != KM_OK || st->body_runs > (unsigned)a.max_iter + 2u) {
-        // non-finite input found by the first pass, or the hard iteration guard
-        if (st->status == KM_OK) st->status = KM_ETIMEOUT;
-        st->done = 1;
-        return;
-    }
-    st->passes += 1;
-    st->n_changed = nch;
-    st->E_trial = E;
-    const bool conv = nch <= a.thr;
-    if (conv && st->from_lloyd) {                  // converged at a Lloyd iterate: return
-        st->done = 1;
-        st->converged = 1;
-        st->E_cur = E;
-        st->E_final = E;
-        st->final_src = 0;
-        return;
-    }
-    if (!a.lloyd_only && st->t >= 3) {             // dynamic m (only once E^{t-2} is finite)
-        const double num = st->E_prev - E, den = st->E_prev2 - st->E_prev;
-        if (num < a.eps1 * den)
-            st->m = st->m - 1 > 0 ? st->m - 1 : 0;
-        else if (num > a.eps2 * den)
-            st->m = st->m + 1 < a.m_max ? st->m + 1 : a.m_max;
-    }
-    const bool reject = !st->from_lloyd && (conv || E >= st->E_prev);
-    if (reject) {
-        st->revert = 1;                            // the revert pass runs next
-    } else {
-        st->revert = 0;
-        if (!st->from_lloyd) st->accepted += 1;
-        st->E_cur = E;
-    }
-}
-
-// After the revert pass P^t = Assign(C_AU): bookkeeping and the convergence test again.
-__device__ void controller_revert(const PassArgs& a, SolveState* st, double E, long long nch)
-{
-    st->passes += 1;
-    st->rejected += 1;
-    st->n_changed = nch;
-    st->E_cur = E;
-    if (nch <= a.thr) {
-        st->done = 1;
-        st->converged = 1;
-        st->E_final = E;
-        st->final_src = 1;
-    }
 }
 
 // Scan all centroids for R samples: per chunk of 8 centroids (4 interleaved pairs), each
@@ -674,9 +621,9 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
                 if (bd) st->status = KM_ENONFINITE;       // the first loop pass stops the solve
             } else {
                 if (a.mode == MODE_TRIAL)
-                    controller_trial(a, st, E, ch);
+                    controller_trial(st, E, ch, a.thr, a.lloyd_only, a.eps1, a.eps2, a.m_max, a.max_iter);
                 else
-                    controller_revert(a, st, E, ch);
+                    controller_revert(st, E, ch, a.thr);
                 // the kernel that ends the solve also ends the graph's while loop
                 if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
             }

@@ -1,0 +1,129 @@
+"""GPU parity of the dense path (BF16 tcgen05 distances, FP32 rescoring, sort-based update).
+
+Assignments identical to the FP64 oracle wherever the oracle's top-2 gap exceeds
+1e-6 * max(||x||^2, ||c_(1)||^2, ||c_(2)||^2); counts exact; centroids and energy within 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+import paper_1805_10638_gb300 as km
+from gpu_util import check_assignment, need_gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = km.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def dense_data(N, d, K, seed):
+    X = datagen.full_cov_mixture(N, d, max(K, 2), seed)
+    Xb = datagen.to_bf16_bits(X)
+    C0 = datagen.init_centroids(X, K, seed + 1000)
+    return X, Xb, C0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def dev_bf16(bits):
+    return torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+
+
+@pytest.mark.parametrize("N,d,K", [(20_000, 128, 1024), (9_999, 64, 300), (4_097, 96, 256), (1_000, 128, 7),
+                                   (128, 64, 128), (33, 24, 5)])
+def test_dense_assign_masked_parity(ctx, N, d, K):
+    X, Xb, C0 = dense_data(N, d, K, seed=N + d + K)
+    rho = km.kmeans_assign(ctx, dev(X), dev(C0), X_bf16=dev_bf16(Xb)).cpu().numpy()
+    check_assignment(X, C0, rho, f"N={N} d={d} K={K}")
+
+
+def test_dense_assign_n_changed_and_dmin(ctx):
+    X, Xb, C0 = dense_data(8_000, 64, 50, seed=3)
+    Xd, Xbd = dev(X), dev_bf16(Xb)
+    r0 = km.kmeans_assign(ctx, Xd, dev(C0), X_bf16=Xbd)
+    C1 = C0 + np.float32(0.5)
+    nch = torch.zeros((), dtype=torch.int64, device="cuda")
+    dmin = torch.empty(8_000, dtype=torch.float32, device="cuda")
+    r1 = km.kmeans_assign(ctx, Xd, dev(C1), rho_prev=r0, n_changed=nch, dmin=dmin, X_bf16=Xbd)
+    a0, a1 = r0.cpu().numpy(), r1.cpu().numpy()
+    assert int(nch.item()) == int((a0 != a1).sum())
+    ref = ((X.astype(np.float64) - C1.astype(np.float64)[a1]) ** 2).sum(1)
+    np.testing.assert_allclose(dmin.cpu().numpy(), ref, rtol=1e-5)
+
+
+@pytest.mark.parametrize("N,d,K", [(50_001, 128, 1000), (3_000, 32, 17)])
+def test_dense_update_parity_deterministic(ctx, N, d, K):
+    r = np.random.default_rng(N)
+    X = (r.normal(size=(N, d)) * 3).astype(np.float32)
+    rho = r.integers(0, K - 2, size=N).astype(np.int32)       # two empty clusters
+    Cp = r.normal(size=(K, d)).astype(np.float32)
+    Xd, rd, Cd = dev(X), dev(rho), dev(Cp)
+    C1, n1 = km.kmeans_update(ctx, Xd, rd, K, Cd)
+    C1 = C1.clone()
+    C2, n2 = km.kmeans_update(ctx, Xd, rd, K, Cd)
+    assert torch.equal(C1, C2) and torch.equal(n1, n2)
+    Co, no = oracle.update(X, rho, K, Cp)
+    np.testing.assert_array_equal(n1.cpu().numpy(), no)
+    assert rel_err(C1.cpu().numpy(), Co) < 1e-6
+    np.testing.assert_array_equal(C1.cpu().numpy()[no == 0], Cp[no == 0])
+
+
+def test_dense_energy_parity(ctx):
+    X, Xb, C0 = dense_data(30_000, 64, 100, seed=5)
+    rho, _, _ = oracle.assign(X, C0)
+    E = km.kmeans_energy(ctx, dev(X), dev(C0), dev(rho)).item()
+    Eo = oracle.energy(X, C0, rho)
+    assert abs(E - Eo) / Eo < 1e-6
+
+
+@pytest.mark.parametrize("method", ["lloyd", "aa"])
+def test_dense_solve_matches_oracle(ctx, method):
+    X, Xb, C0 = dense_data(20_000, 64, 64, seed=7)
+    kw = dict(lloyd_only=1) if method == "lloyd" else {}
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(C0), X_bf16=dev_bf16(Xb), **kw)
+    Ch, rh = C.cpu().numpy(), rho.cpu().numpy()
+    assert info["converged"] == 1, info
+    Eo_at = oracle.energy(X, Ch, rh)
+    assert abs(info["E"] - Eo_at) / Eo_at < 1e-6
+    Cm, _ = oracle.update(X, rh, Ch.shape[0], Ch)
+    assert rel_err(Ch, Cm) < 1e-6
+    check_assignment(X, Ch, rh, "fixed point")
+    Co, ro, io = oracle.solve(X, C0, lloyd=(method == "lloyd"))
+    assert abs(info["E"] - io["E"]) / io["E"] < 1e-6, (info, io)
+    if method == "lloyd":
+        assert info["iters"] == io["iters"], (info, io)
+
+
+def test_dense_solve_repeatable_and_host(ctx):
+    X, Xb, C0 = dense_data(10_000, 32, 40, seed=9)
+    Xd, Xbd, Cd = dev(X), dev_bf16(Xb), dev(C0)
+    C1, r1, i1 = km.kmeans_solve(ctx, Xd, Cd, X_bf16=Xbd)
+    C1, r1 = C1.clone(), r1.clone()
+    C2, r2, i2 = km.kmeans_solve(ctx, Xd, Cd, X_bf16=Xbd)
+    assert torch.equal(C1, C2) and torch.equal(r1, r2)
+
+
+@pytest.mark.slow
+def test_dense_solve_full_size_sampled(ctx):
+    """Full-size dense workload (N=1M, d=128, K=1024): properties at any size and sampled rows."""
+    X, Xb, C0 = datagen.dense_1m(seed=0)
+    C, rho, info = km.kmeans_solve(ctx, dev(X), dev(C0), X_bf16=dev_bf16(Xb), max_iter=60)
+    Ch, rh = C.cpu().numpy(), rho.cpu().numpy()
+    idx = np.sort(np.random.default_rng(1).choice(X.shape[0], 4_000, replace=False))
+    if info["converged"]:
+        check_assignment(X[idx], Ch, rh[idx], "sampled rows at the solution")
+    Cm, cnt = oracle.update(X, rh, Ch.shape[0], Ch)
+    assert cnt.sum() == X.shape[0]
+    assert rel_err(Ch, Cm) < 1e-6
+    Eo = oracle.energy(X, Ch, rh)
+    assert abs(info["E"] - Eo) / Eo < 1e-6

@@ -156,7 +156,7 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.cn0 = take((size_t)P.Kpad * 4);
     P.cn1 = take((size_t)P.Kpad * 4);
     P.xnorm = take((size_t)N * 4);
-    P.queue = take((size_t)N * 4);
+    P.queue = take((size_t)N * 4 * 4);   // full-rescore rows, then (row, i1, i2) candidate pairs
     P.qcount = take(256);
     P.err = take(256);
     P.hist = take((size_t)K * P.nbk * 4);
@@ -372,11 +372,12 @@ DenseArgs dense_args(kmeans_ctx* ctx, const Plan& P, const float* X32, int64_t N
     // BF16 score error bound: 2 (2 u_b + d u) |x| max|c| for 2 x.c, u max|c|^2 for ||c||^2, with a
     // factor 2 of allowance for the accumulation order inside the MMA
     const double ub = 1.0 / 512.0, u = 5.9604644775390625e-8;
-    a.bcoef_a = (float)(2.0 * (2.0 * (2.0 * ub + d * u)));
+    a.bcoef_a = (float)(2.0 * (2.0 * (2.0 * ub + d * u)) * (1.0 + 2.0 * ub));
     a.bcoef_b = (float)(2.0 * 2.0 * u);
     a.rho_pair[0] = at<int32_t>(ctx, P.rhoA);
     a.rho_pair[1] = at<int32_t>(ctx, P.rhoB);
     a.queue = at<int>(ctx, P.queue);
+    a.cand = at<int>(ctx, P.queue) + N;
     a.qcount = at<unsigned int>(ctx, P.qcount);
     a.err = at<int>(ctx, P.err);
     a.rows_per_block = P.rpb;
@@ -512,6 +513,7 @@ Launch make_launch(kmeans_ctx* ctx, const Plan& P, const kmeans_data* X, int K, 
         ma.fp32_path = 0;                // the mix only writes C; the BF16 packing is separate
         DenseArgs& da = L.da;
         da = dense_args(ctx, P, L.X32, X->N, d, K);
+        da.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
         da.thr = thr;
         da.lloyd_only = p.lloyd_only;
         da.eps1 = p.eps1;
@@ -809,6 +811,7 @@ kmeans_status dense_assign_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
     const float* X32 = reinterpret_cast<const float*>(X->X);
     DenseArgs a = dense_args(ctx, P, X32, X->N, X->d, K);
     a.mode = MODE_STANDALONE;
+    a.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
     a.rho_out = rho;
     a.rho_prev = rho_prev;
     a.out_nch = reinterpret_cast<long long*>(n_changed);
@@ -816,7 +819,6 @@ kmeans_status dense_assign_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
     if (!dense_maps(ctx, P, X->X_bf16, X->N, X->d, tmX, tmC, tmC1))
         return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
     KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
-    KM_CUDA(launch_xnorm(X32, X->N, X->d, const_cast<float*>(a.xnorm), nullptr, ctx->nsm, ctx->stream));
     if ((s = dense_pack_user(ctx, P, C, X->d, K)) != KM_OK) return s;
     KM_CUDA(launch_dense_pass(a, tmX, tmC, tmC, ctx->nsm, ctx->stream));
     if (n_changed || dmin)

@@ -6,13 +6,15 @@
 // TMA (128-byte swizzle, K-major), and the epilogue warps read the 128 x 256 FP32 accumulator
 // from TMEM (double buffered, so the MMA of the next centroid tile overlaps the epilogue of this
 // one) and keep a per-row top-2 (value, lowest index).  Warp roles: warp 0 issues TMA, warp 1
-// allocates TMEM and issues the MMAs (one thread), warps 4..11 are the epilogue (two warps per
-// TMEM lane quadrant, each taking half of the columns).  Every wait on an mbarrier is bounded: on
+// allocates TMEM and issues the MMAs (one thread), warps 2..17 are the epilogue (four warps per
+// TMEM lane quadrant, each taking a quarter of the columns).  Every wait on an mbarrier is bounded: on
 // timeout the kernel records an error and all roles leave their loops.
 //
 // Near ties: the BF16 scores carry a rigorous rounding-error bound
 //   B = (4 u_b + 2 d u) |x| max|c| + 2 u max|c|^2     (u_b = 2^-9, u = 2^-24);
-// rows whose top-2 gap is within 2B are queued and rescored over all K in FP32, direct form.
+// the epilogue keeps per row the two best (value, lowest index) and the third-best value.  If the
+// top-2 gap is within 2B but the third value is clear, only the two best can be the argmin and
+// they are compared in FP32 (direct form); otherwise the row is rescored over all K in FP32.
 //
 // Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
@@ -34,7 +36,7 @@ constexpr int TM = 128;            // rows per tile (MMA M)
 constexpr int TN = 256;            // centroids per tile (MMA N)
 constexpr int KBLK = 64;           // bf16 per 128-byte swizzle row
 constexpr int CST = 2;             // centroid-tile stages
-constexpr int DTHREADS = 384;      // 12 warps
+constexpr int DTHREADS = 576;      // 18 warps: TMA, MMA, 16 epilogue
 constexpr int SEG = 64;            // rows per segment-sum chunk
 constexpr unsigned SPIN_LIMIT = 1u << 28;
 
@@ -156,7 +158,7 @@ __host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
     p.x = o;     o += 2u * nkb * TM * 128;
     p.c = o;     o += (uint32_t)CST * nkb * TN * 128;
     p.cn = o;    o += (uint32_t)Kpad * 4;
-    p.merge = o; o += TM * 16;
+    p.merge = o; o += 3 * TM * 5 * 4;
     p.bar = (o + 7) & ~7u; o = p.bar + 16 * 8;
     p.slot = o;  o += 8;
     p.abort = o; o += 16;
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             mbar_init(cfull + 8 * i, 1);
             mbar_init(cempty + 8 * i, 1);
             mbar_init(afull + 8 * i, 1);
-            mbar_init(aempty + 8 * i, 8);
+            mbar_init(aempty + 8 * i, 16);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 mma_commit(xempty + 8 * xs);
             }
         }
-    } else if (warp >= 4) {   // epilogue
-        const int q = warp & 3, h = (warp - 4) >> 2;
+    } else if (warp >= 2) {   // epilogue: 16 warps = 4 TMEM lane quadrants x 4 column quarters
+        const int q = warp & 3, h = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         float cmax2 = 0.f;
         for (int j = 0; j < a.K; ++j) cmax2 = fmaxf(cmax2, s_cn[j]);
@@ -285,8 +287,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
         volatile int* s_go = reinterpret_cast<volatile int*>(smem + P.abort + 4);
         uint32_t ait = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            float b1 = __int_as_float(0x7f800000), b2 = b1;
-            int i1 = 0;
+            // per row and quarter: the two best (value, lowest index) and the third-best value
+            float v1 = __int_as_float(0x7f800000), v2 = v1, v3 = v1;
+            int i1 = 0, i2 = 0;
             bool ok = true;
             for (int ct = 0; ct < nct; ++ct, ++ait) {
                 const uint32_t ab = ait & 1;
@@ -296,18 +299,21 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 if (ok) {
                     tc_fence_after();
 #pragma unroll 1
-                    for (int c16 = 0; c16 < TN / 2 / 16; ++c16) {
-                        const int col = h * (TN / 2) + c16 * 16;
+                    for (int c16 = 0; c16 < TN / 4 / 16; ++c16) {
+                        const int col = h * (TN / 4) + c16 * 16;
                         float v[16];
                         tmem_ld16(tmem + lane_base + ab * TN + col, v);
                         const int j0 = ct * TN + col;
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const float s = fmaf(-2.f, v[e], s_cn[j0 + e]);
-                            b2 = fminf(b2, fmaxf(b1, s));
-                            const bool p = s < b1;
-                            b1 = p ? s : b1;
-                            i1 = p ? j0 + e : i1;
+                            const int j = j0 + e;
+                            v3 = fminf(v3, fmaxf(v2, s));
+                            const bool p1 = s < v1, p2 = s < v2;
+                            i2 = p1 ? i1 : (p2 ? j : i2);
+                            v2 = fminf(v2, fmaxf(v1, s));
+                            i1 = p1 ? j : i1;
+                            v1 = fminf(v1, s);
                         }
                     }
                 }
@@ -315,37 +321,76 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(aempty + 8 * ab);
             }
-            // merge the two column halves of each row (lexicographic on (value, index))
+            // merge the four column quarters of each row (lexicographic on (value, index))
             const int r = q * 32 + lane;
-            if (h == 1) {
-                s_merge[4 * r] = b1;
-                s_merge[4 * r + 1] = b2;
-                s_merge[4 * r + 2] = __int_as_float(i1);
+            if (h > 0) {
+                float* m = s_merge + ((h - 1) * TM + r) * 5;
+                m[0] = v1;
+                m[1] = v2;
+                m[2] = v3;
+                m[3] = __int_as_float(i1);
+                m[4] = __int_as_float(i2);
             }
-            named_bar(1, 256);
+            named_bar(1, 512);
             if (h == 0 && ok) {
-                const float o1 = s_merge[4 * r], o2 = s_merge[4 * r + 1];
-                const int oi = __float_as_int(s_merge[4 * r + 2]);
-                const float hi1 = fmaxf(b1, o1);
-                const bool other = (o1 < b1) || (o1 == b1 && oi < i1);
-                const float nb1 = other ? o1 : b1;
-                const int ni1 = other ? oi : i1;
-                const float nb2 = fminf(hi1, fminf(b2, o2));
+                for (int hh = 0; hh < 3; ++hh) {
+                    const float* m = s_merge + (hh * TM + r) * 5;
+                    const float w[2] = {m[0], m[1]};
+                    const int wj[2] = {__float_as_int(m[3]), __float_as_int(m[4])};
+                    for (int u = 0; u < 2; ++u) {
+                        if (w[u] < v1 || (w[u] == v1 && wj[u] < i1)) {
+                            v3 = fminf(v3, v2);
+                            v2 = v1;
+                            i2 = i1;
+                            v1 = w[u];
+                            i1 = wj[u];
+                        } else if (w[u] < v2 || (w[u] == v2 && wj[u] < i2)) {
+                            v3 = fminf(v3, v2);
+                            v2 = w[u];
+                            i2 = wj[u];
+                        } else {
+                            v3 = fminf(v3, w[u]);
+                        }
+                    }
+                    v3 = fminf(v3, m[2]);
+                }
+                const float nb1 = v1, nb2 = v2;
+                const int ni1 = i1;
                 const int64_t row = (int64_t)tile * TM + r;
                 if (row < a.N) {
-                    const float xn = a.xnorm[row];
+                    // ||x^|| of the BF16 row (the operand the MMA saw); ||x|| <= ||x^|| / (1 - u_b)
+                    const uint4* xr = reinterpret_cast<const uint4*>(a.Xb + row * a.d);
+                    float xs = 0.f;
+                    for (int u = 0; u < a.d / 8; ++u) {
+                        const uint4 w = __ldg(xr + u);
+                        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const float lo = __uint_as_float(ws[t] << 16), hi = __uint_as_float(ws[t] & 0xffff0000u);
+                            xs = fmaf(lo, lo, fmaf(hi, hi, xs));
+                        }
+                    }
+                    const float xn = sqrtf(xs);
                     const float bnd = a.bcoef_a * xn * cmax + a.bcoef_b * cmax2;
                     rho[row] = ni1;
                     if (!(nb2 - nb1 > 2.f * bnd)) {
-                        const unsigned pos = atomicAdd(a.qcount, 1u);
-                        a.queue[pos] = (int)row;
+                        if (v3 - nb1 > 2.f * bnd) {
+                            // only the two best can be the argmin: compare them exactly later
+                            const unsigned pos = atomicAdd(a.qcount + 1, 1u);
+                            a.cand[3 * pos] = (int)row;
+                            a.cand[3 * pos + 1] = ni1;
+                            a.cand[3 * pos + 2] = i2;
+                        } else {
+                            const unsigned pos = atomicAdd(a.qcount, 1u);
+                            a.queue[pos] = (int)row;
+                        }
                     }
                 }
             }
-            if (tid == 128) *s_go = (*abort == 0) ? 1 : 0;   // one snapshot for all epilogue warps
-            named_bar(1, 256);
+            if (tid == 64) *s_go = (*abort == 0) ? 1 : 0;   // one snapshot for all epilogue warps
+            named_bar(1, 512);
             const int go = *s_go;
-            named_bar(1, 256);
+            named_bar(1, 512);
             if (!go) break;
         }
     }
@@ -358,48 +403,112 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ near-tie rescoring
-// One warp per queued row: direct-form FP32 distances to all K centroids (lanes split K,
-// ascending j per lane), lexicographic (distance, index) butterfly.
+// FP32 direct form sum_k (x_k - c_jk)^2 for the queued rows.  Pairs (row, i1, i2): one warp
+// compares the two candidates (lanes split d, fixed butterfly).  Full rows: one warp scans all K
+// (lanes split K, ascending j per lane) and a lexicographic (distance, index) butterfly.
 __global__ void __launch_bounds__(256) k_rescore(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
     __shared__ float sx[8][128];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned n = *a.qcount;
+    const unsigned nfull = a.qcount[0], npair = a.qcount[1];
     const float* X = a.X;
     const float* C = a.c32[set];
     const int d = a.d, K = a.K;
     int32_t* rho = pass_rho(a, a.st);
-    for (unsigned q = blockIdx.x * 8 + w; q < n; q += gridDim.x * 8) {
-        const int64_t row = a.queue[q];
-        for (int k = lane; k < d; k += 32) sx[w][k] = X[row * d + k];
-        __syncwarp();
-        float bd = __int_as_float(0x7f800000);
-        int bj = K;
-        for (int j = lane; j < K; j += 32) {
-            const float* c = C + (size_t)j * d;
-            float acc = 0.f;
-            for (int k = 0; k < d; ++k) {
-                const float t = sx[w][k] - c[k];
-                acc = fmaf(t, t, acc);
-            }
-            if (acc < bd) {
-                bd = acc;
-                bj = j;
-            }
+    for (unsigned q = blockIdx.x * 8 + w; q < npair; q += gridDim.x * 8) {
+        const int64_t row = a.cand[3 * q];
+        const int j1 = a.cand[3 * q + 1], j2 = a.cand[3 * q + 2];
+        float s1 = 0.f, s2 = 0.f;
+        for (int k = lane; k < d; k += 32) {
+            const float x = X[row * d + k];
+            const float t1 = x - C[(size_t)j1 * d + k], t2 = x - C[(size_t)j2 * d + k];
+            s1 = fmaf(t1, t1, s1);
+            s2 = fmaf(t2, t2, s2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(FULL, bd, o);
-            const int oj = __shfl_xor_sync(FULL, bj, o);
-            if (ob < bd || (ob == bd && oj < bj)) {
-                bd = ob;
-                bj = oj;
-            }
+            s1 += __shfl_xor_sync(FULL, s1, o);
+            s2 += __shfl_xor_sync(FULL, s2, o);
         }
-        if (lane == 0) rho[row] = bj < K ? bj : 0;
-        __syncwarp();
+        if (lane == 0) rho[row] = (s2 < s1 || (s2 == s1 && j2 < j1)) ? j2 : j1;
+    }
+    (void)sx;
+    (void)nfull;
+}
+
+// Full rescans: 16 queued rows per block (two per warp) share each tile of 64 centroids staged in
+// shared memory (row stride d+1 floats: lanes reading different centroids hit different banks).
+// Lane l scores centroids c0+l and c0+l+32 of every tile, so each lane visits its centroids in
+// ascending order; a lexicographic (distance, index) butterfly finishes each row.
+__global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const unsigned nfull = a.qcount[0];
+    if (blockIdx.x * 16u >= nfull) return;
+    extern __shared__ float sm_f[];
+    const int d = a.d, K = a.K, ds = d + 1;
+    float* sx = sm_f;                 // [16][d]
+    float* sc = sm_f + 16 * d;        // [64][d+1]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float* X = a.X;
+    const float* C = a.c32[set];
+    int32_t* rho = pass_rho(a, a.st);
+    for (unsigned g = blockIdx.x * 16u; g < nfull; g += gridDim.x * 16u) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 16 * d; i += blockDim.x) {
+            const unsigned q = g + i / d;
+            sx[i] = q < nfull ? X[(int64_t)a.queue[q] * d + i % d] : 0.f;
+        }
+        float bd[2] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+        int bj[2] = {K, K};
+        for (int c0 = 0; c0 < K; c0 += 64) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < 64 * d; i += blockDim.x) {
+                const int jl = i / d, k = i % d;
+                sc[jl * ds + k] = c0 + jl < K ? C[(size_t)(c0 + jl) * d + k] : 0.f;
+            }
+            __syncthreads();
+            float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+            const float* x0 = sx + (2 * w) * d;
+            const float* x1 = x0 + d;
+            const float* ca = sc + lane * ds;
+            const float* cb = sc + (lane + 32) * ds;
+            for (int k = 0; k < d; ++k) {
+                const float xa = x0[k], xb = x1[k], u = ca[k], v = cb[k];
+                const float t00 = xa - u, t01 = xa - v, t10 = xb - u, t11 = xb - v;
+                acc[0][0] = fmaf(t00, t00, acc[0][0]);
+                acc[0][1] = fmaf(t01, t01, acc[0][1]);
+                acc[1][0] = fmaf(t10, t10, acc[1][0]);
+                acc[1][1] = fmaf(t11, t11, acc[1][1]);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const int j = c0 + lane + 32 * s2;
+                    if (j < K && acc[r][s2] < bd[r]) {
+                        bd[r] = acc[r][s2];
+                        bj[r] = j;
+                    }
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(FULL, bd[r], o);
+                const int oj = __shfl_xor_sync(FULL, bj[r], o);
+                if (ob < bd[r] || (ob == bd[r] && oj < bj[r])) {
+                    bd[r] = ob;
+                    bj[r] = oj;
+                }
+            }
+            const unsigned q = g + 2 * w + r;
+            if (lane == 0 && q < nfull) rho[a.queue[q]] = bj[r] < K ? bj[r] : 0;
+        }
     }
 }
 
@@ -682,7 +791,7 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
         if (a.out_nch) *a.out_nch = ch;
         return;
     }
-    if (a.mode != MODE_EPI) st->rescored += *a.qcount;
+    if (a.mode != MODE_EPI) st->rescored += a.qcount[0] + a.qcount[1];
     if (a.mode == MODE_EPI) {
         st->E_final = E;
     } else if (a.mode == MODE_INIT) {
@@ -798,7 +907,7 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* t
                               cudaStream_t s)
 {
     // assignment
-    cudaError_t e = cudaMemsetAsync(a.qcount, 0, sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(a.qcount, 0, 2 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     const size_t smem = dense_assign_smem(a.dpad, a.Kpad);
     e = cudaFuncSetAttribute(k_dense_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -810,6 +919,9 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* t
                                                 *reinterpret_cast<const CUtensorMap*>(tmC1), a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rescore<<<nsm * 4, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t sm_full = (size_t)(16 * a.d + 64 * (a.d + 1)) * sizeof(float);
+    k_rescore_full<<<nsm * 4, 256, sm_full, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@ struct DenseArgs {
     int Kpad;                 // K rounded up to 256 (MMA N)
     int mode;                 // PassMode
     const float* X;           // [N][d] FP32
+    const __nv_bfloat16* Xb;  // [N][d] BF16 copy (the MMA operand)
     const float* xnorm;       // [N] ||x||
     const float* cn[2];       // [Kpad] ||c||^2, +inf for pad rows; set 0 = C^t, set 1 = C_AU
     const float* c32[2];      // [K][d] FP32 centroids
@@ -25,8 +26,9 @@ struct DenseArgs {
     int32_t* rho_out;         // standalone output
     const int32_t* rho_prev;  // standalone previous assignment (optional)
     int32_t* rho_pair[2];     // solver ping-pong assignment
-    int* queue;               // [N] near-tie rows
-    unsigned int* qcount;
+    int* queue;               // [N] rows to rescore over all K
+    int* cand;                // [N][3] (row, i1, i2): rows whose argmin is one of two candidates
+    unsigned int* qcount;     // [2]: full rows, candidate pairs
     int* err;
     // update chain
     int rows_per_block;

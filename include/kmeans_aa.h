@@ -176,6 +176,30 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* X_host, int3
                                 const void* C0_host, const kmeans_params* params,
                                 void* C_out_host, int32_t* rho_out_host, kmeans_info* info);
 
+/* kmeans_update without any allocation, for callers that must not allocate device memory:
+ * an allocator or memory pool of the caller's own that calls back into K-Means and must not
+ * re-enter cudaMalloc, and real-time or embedded programs that allocate everything at start-up
+ * and treat any later allocation (with its device-wide synchronisation) as an error.  Those
+ * callers also cannot own a context, whose workspace grows on demand.
+ * The paper has no counterpart; it is the same update step (Eq. 4) as kmeans_update.
+ *   - No context: the work goes to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
+ *     on the current device.  X, rho, C_prev, C_out and counts are as for kmeans_update.
+ *   - Low-d path only: 1 <= d <= 16 (KM_F64, KM_F32; KM_BF16_F32 is treated as KM_F32).
+ *   - Scratch: a fixed array of 8 MiB in device memory that the library holds on every GPU that
+ *     loads it, until the process exits.  The array stores one block partial of K*d sums and K
+ *     counts per thread block; shapes whose single block partial does not fit return KM_EINVAL.
+ *   - The first call on a device looks the array's address up (cudaGetSymbolAddress, with that
+ *     device current) and caches it; later calls on that device reuse the cached address.
+ *   - Every call shares the array and leaves its contents behind; each call clears what must
+ *     start at zero.  Calls that overlap on the GPU (other streams, unordered host threads) race
+ *     on the array: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Asynchronous on cuda_stream; returns KM_EINVAL for bad arguments, KM_ECUDA if a launch
+ *     fails. */
+kmeans_status kmeans_update_static(const kmeans_data* X, const int32_t* rho, int32_t K,
+                                   const void* C_prev, void* C_out, int64_t* counts,
+                                   void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,4 +4,5 @@ The compute path is the CUDA library ``libkmeans_aa.so`` (C ABI in ``include/kme
 this package is its thin ctypes binding.  See ``_lib`` for the calls.
 """
 from ._lib import (KM_BF16_F32, KM_F32, KM_F64, Context, KmeansError, default_params,  # noqa: F401
-                   kmeans_assign, kmeans_energy, kmeans_solve, kmeans_solve_host, kmeans_update, load)
+                   kmeans_assign, kmeans_energy, kmeans_solve, kmeans_solve_host, kmeans_update,
+                   kmeans_update_static, load)

@@ -86,8 +86,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                ctypes.POINTER(kmeans_info)]
     L.kmeans_solve_host.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
                                     ctypes.POINTER(kmeans_info)]
+    L.kmeans_update_static.argtypes = [pd, vp, i32, vp, vp, vp, vp]
     for name in ("kmeans_create", "kmeans_destroy", "kmeans_set_stream", "kmeans_assign",
-                 "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host"):
+                 "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host",
+                 "kmeans_update_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -180,6 +182,27 @@ def kmeans_update(ctx: Context, X, rho, K: int, C_prev, C_out=None, counts=None)
     data = make_data(X)
     _check(ctx, load().kmeans_update(ctx.handle, ctypes.byref(data), _ptr(rho), K, _ptr(C_prev), _ptr(C_out),
                                      _ptr(counts)))
+    return C_out, counts
+
+
+def kmeans_update_static(X, rho, K: int, C_prev, C_out=None, counts=None, stream=None):
+    """kmeans_update without allocation (no context; scratch in a fixed device array).
+
+    For callers that must not allocate device memory: pass C_out and counts, otherwise this
+    wrapper allocates them with torch before the call.  Runs on `stream` (default: torch's
+    current stream of X's device); returns (C_out, counts).
+    """
+    if C_out is None:
+        C_out = torch.empty_like(C_prev)
+    if counts is None:
+        counts = torch.empty(K, dtype=torch.int64, device=X.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device).cuda_stream
+    data = make_data(X)
+    st = load().kmeans_update_static(ctypes.byref(data), _ptr(rho), K, _ptr(C_prev), _ptr(C_out), _ptr(counts),
+                                     ctypes.c_void_p(stream))
+    if st != KM_OK:
+        raise KmeansError(st, "kmeans_update_static failed")
     return C_out, counts
 
 

@@ -91,7 +91,9 @@ typedef struct {
  *   E              final energy E(P, C) (Eq. 1)
  *   rescored_rows  rows whose reduced-precision top-2 gap was inside the error bound and
  *                  were rescored in FP32, summed over all passes
- *   device_ms      device time of the solve measured with CUDA events */
+ *   device_ms      device time of the solve measured with CUDA events (batched solves: of the
+ *                  whole batch)
+ *   status         kmeans_status of this solve (KM_OK, KM_ENONFINITE, KM_ETIMEOUT) */
 typedef struct {
     int32_t iters;
     int32_t accepted;
@@ -102,6 +104,8 @@ typedef struct {
     double E;
     int64_t rescored_rows;
     double device_ms;
+    int32_t status;
+    int32_t reserved;
 } kmeans_info;
 
 typedef struct kmeans_ctx kmeans_ctx;
@@ -175,6 +179,88 @@ kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
 kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* X_host, int32_t K,
                                 const void* C0_host, const kmeans_params* params,
                                 void* C_out_host, int32_t* rho_out_host, kmeans_info* info);
+
+/* One instance of a batched solve.  All pointers are device pointers owned by the caller. */
+typedef struct {
+    kmeans_data X;       /* samples: d <= 16 (KM_F64 or KM_F32), or d > 16 with KM_BF16_F32 and X_bf16 */
+    int32_t K;
+    const void* C0;      /* [K, d] initial centroids (element type of X) */
+    void* C_out;         /* [K, d] final centroids (element type of X) */
+    int32_t* rho_out;    /* [N] final assignment */
+} kmeans_problem;
+
+/* Solve n independent instances together (Lloyd or Algorithm 1 each, per its parameters).  The
+ * low-d instances (d <= 16) advance one loop pass per step; every step of every instance runs
+ * inside one CUDA graph launch (a conditional while node that ends when all of them are done),
+ * each batched kernel being one persistent grid over (instance, block) work items.  Instances with
+ * d > 16 run the tensor-core path as chains of their own in the same graph, beside the low-d chain.
+ * Each instance's results are bitwise those of kmeans_solve on it alone (same kernels, same
+ * per-instance block decomposition).  The grids of the low-d assignment kernels are picked by
+ * timing candidates on the batch's data the first time a batch shape is seen (KM_TUNE=0 in the
+ * environment turns that off); the choice does not change any result.
+ *   problems  host array of n instances (d > 16 needs KM_BF16_F32 with X_bf16: KM_EINVAL otherwise)
+ *   params    host array of n parameter sets, or NULL for the defaults
+ *   infos     host array of n results (may be NULL); device_ms is the time of the whole batch
+ * Synchronous like kmeans_solve.  Returns the first non-OK instance status (every info is filled). */
+kmeans_status kmeans_solve_batched(kmeans_ctx* ctx, const kmeans_problem* problems, int32_t n,
+                                   const kmeans_params* params, kmeans_info* infos);
+
+/* One line describing the last batched plan: work-item groups, the timed launch-shape candidates
+ * and the grids chosen.  Valid until the next call on the context. */
+const char* kmeans_batch_describe(const kmeans_ctx* ctx);
+
+/* ---- Serving: requests of different N, d and K arriving over time ----------------------------
+ * A server owns one device allocation of hbm_budget_bytes, carved by a first-fit allocator.  A
+ * submitted request waits until its device footprint fits (and, for a low-d request, one of
+ * max_slots batch slots is free; for a large request, one of max_large lanes).  Low-d requests
+ * (d <= 16) run in one continuously stepping batch: each kmeans_server_step() runs the prologue of
+ * newly admitted requests, one loop pass of every active request, and the epilogue and result
+ * copies of finished ones, so requests join and leave between steps.  Large requests (d > 16,
+ * KM_BF16_F32 with its BF16 copy) run their whole solve on their lane's own stream, overlapping the
+ * batch and each other.
+ * Each request's results are bitwise those of kmeans_solve on it alone.  A server is used from one
+ * host thread. */
+typedef struct kmeans_server kmeans_server;
+
+typedef struct {
+    int32_t waiting;        /* submitted, not admitted */
+    int32_t active_small;   /* admitted low-d requests not yet handed back */
+    int32_t active_large;
+    int32_t completed;      /* results on the host so far */
+    int64_t steps;          /* batch steps run */
+    size_t pool_bytes;      /* the HBM budget */
+    size_t pool_used;
+    size_t pool_peak;
+} kmeans_server_stats;
+
+/* Create a server on `device`: 1 <= max_slots <= 65536, 0 <= max_large <= 64.  Allocates the pool
+ * (KM_ENOMEM if it does not fit). */
+kmeans_status kmeans_server_create(kmeans_server** srv, int device, size_t hbm_budget_bytes, int32_t max_slots,
+                                   int32_t max_large);
+
+/* Wait for the server's streams and free everything.  NULL is accepted. */
+kmeans_status kmeans_server_destroy(kmeans_server* srv);
+
+/* Queue one request.  X_host, C0_host, C_out_host and rho_out_host are HOST buffers that must stay
+ * valid until the request is reported done (pinned memory keeps the copies asynchronous).  The
+ * inputs are copied to the device at admission; the results are written to C_out_host and
+ * rho_out_host.  *ticket identifies the request.  KM_ENOMEM if the request can never fit. */
+kmeans_status kmeans_server_submit(kmeans_server* srv, const kmeans_data* X_host, int32_t K, const void* C0_host,
+                                   const kmeans_params* params, void* C_out_host, int32_t* rho_out_host,
+                                   int64_t* ticket);
+
+/* Admit what fits, run one batch step, hand back finished requests.  *completed (may be NULL) =
+ * requests whose results reached the host during this call.  At most two steps are in flight. */
+kmeans_status kmeans_server_step(kmeans_server* srv, int32_t* completed);
+
+/* *done = 1 once the request's results are on the host; info (may be NULL) is then filled and the
+ * ticket is released. */
+kmeans_status kmeans_server_poll(kmeans_server* srv, int64_t ticket, int32_t* done, kmeans_info* info);
+
+kmeans_status kmeans_server_get_stats(const kmeans_server* srv, kmeans_server_stats* stats);
+
+/* Last error message of the server ("" if none). */
+const char* kmeans_server_last_error(const kmeans_server* srv);
 
 /* kmeans_update without any allocation, for callers that must not allocate device memory:
  * an allocator or memory pool of the caller's own that calls back into K-Means and must not

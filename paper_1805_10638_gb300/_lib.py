@@ -38,14 +38,25 @@ class kmeans_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double)]
 
 
+class kmeans_problem(ctypes.Structure):
+    _fields_ = [("X", kmeans_data), ("K", ctypes.c_int32), ("C0", ctypes.c_void_p), ("C_out", ctypes.c_void_p),
+                ("rho_out", ctypes.c_void_p)]
+
+
 class kmeans_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
                 ("assign_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("m_final", ctypes.c_int32), ("E", ctypes.c_double), ("rescored_rows", ctypes.c_int64),
-                ("device_ms", ctypes.c_double)]
+                ("device_ms", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class kmeans_server_stats(ctypes.Structure):
+    _fields_ = [("waiting", ctypes.c_int32), ("active_small", ctypes.c_int32), ("active_large", ctypes.c_int32),
+                ("completed", ctypes.c_int32), ("steps", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t),
+                ("pool_used", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t)]
 
 
 _lib = None
@@ -87,9 +98,24 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmeans_solve_host.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
                                     ctypes.POINTER(kmeans_info)]
     L.kmeans_update_static.argtypes = [pd, vp, i32, vp, vp, vp, vp]
+    L.kmeans_solve_batched.argtypes = [vp, ctypes.POINTER(kmeans_problem), i32, ctypes.POINTER(kmeans_params),
+                                       ctypes.POINTER(kmeans_info)]
+    L.kmeans_batch_describe.argtypes = [vp]
+    L.kmeans_batch_describe.restype = ctypes.c_char_p
+    L.kmeans_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, i32, i32]
+    L.kmeans_server_destroy.argtypes = [vp]
+    L.kmeans_server_submit.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
+                                       ctypes.POINTER(i64)]
+    L.kmeans_server_step.argtypes = [vp, ctypes.POINTER(i32)]
+    L.kmeans_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(kmeans_info)]
+    L.kmeans_server_get_stats.argtypes = [vp, ctypes.POINTER(kmeans_server_stats)]
+    L.kmeans_server_last_error.argtypes = [vp]
+    L.kmeans_server_last_error.restype = ctypes.c_char_p
     for name in ("kmeans_create", "kmeans_destroy", "kmeans_set_stream", "kmeans_assign",
                  "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host",
-                 "kmeans_update_static"):
+                 "kmeans_update_static", "kmeans_solve_batched", "kmeans_server_create",
+                 "kmeans_server_destroy", "kmeans_server_submit", "kmeans_server_step",
+                 "kmeans_server_poll", "kmeans_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -242,6 +268,105 @@ def kmeans_solve_host(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None
     _check(ctx, load().kmeans_solve_host(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0),
                                          ctypes.byref(p), _ptr(C_out), _ptr(rho_out), ctypes.byref(info)))
     return C_out, rho_out, info.as_dict()
+
+
+def kmeans_solve_batched(ctx: Context, Xs, C0s, C_outs=None, rho_outs=None, params=None, check=True,
+                         X_bf16s=None):
+    """Solve independent instances together.
+
+    Xs, C0s: lists of device tensors; X_bf16s: list of BF16 copies (None entries for d <= 16);
+    params: one dict for all instances or a list of dicts.
+    Returns (C_outs, rho_outs, infos, status).  With check=True a non-OK status raises."""
+    n = len(Xs)
+    if C_outs is None:
+        C_outs = [torch.empty_like(c) for c in C0s]
+    if rho_outs is None:
+        rho_outs = [torch.empty(x.shape[0], dtype=torch.int32, device=x.device) for x in Xs]
+    probs = (kmeans_problem * n)()
+    for i in range(n):
+        xb = X_bf16s[i] if X_bf16s is not None else None
+        probs[i] = kmeans_problem(make_data(Xs[i], xb), C0s[i].shape[0], _ptr(C0s[i]), _ptr(C_outs[i]),
+                                  _ptr(rho_outs[i]))
+    if params is None or isinstance(params, dict):
+        params = [params or {}] * n
+    ps = (kmeans_params * n)(*[default_params(**q) for q in params])
+    infos = (kmeans_info * n)()
+    st = load().kmeans_solve_batched(ctx.handle, probs, n, ps, infos)
+    if check:
+        _check(ctx, st)
+    return C_outs, rho_outs, [infos[i].as_dict() for i in range(n)], st
+
+
+class Server:
+    """kmeans_server: requests of different shapes admitted against an HBM budget and solved in a
+    continuously stepping batch (low-d) or on a second stream (d > 16, BF16).
+
+    submit() takes host arrays (numpy or CPU torch tensors; pinned memory keeps the copies
+    asynchronous) and returns a ticket; step() advances the server; poll(ticket) returns
+    None while pending, else (C_out, rho_out, info)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 1 << 30, max_slots: int = 512, max_large: int = 1):
+        L = load()
+        h = ctypes.c_void_p()
+        st = L.kmeans_server_create(ctypes.byref(h), device, hbm_budget, max_slots, max_large)
+        if st != KM_OK:
+            raise KmeansError(st, "kmeans_server_create failed")
+        self.handle = h
+        self._keep = {}
+
+    def _raise(self, st):
+        if st != KM_OK:
+            msg = load().kmeans_server_last_error(self.handle)
+            raise KmeansError(st, msg.decode() if msg else "")
+
+    def submit(self, X, C0, X_bf16=None, C_out=None, rho_out=None, **params) -> int:
+        if C_out is None:
+            C_out = (torch.empty(C0.shape, dtype=C0.dtype).pin_memory() if torch.is_tensor(C0)
+                     else np.empty_like(C0))
+        if rho_out is None:
+            rho_out = (torch.empty(X.shape[0], dtype=torch.int32).pin_memory() if torch.is_tensor(X)
+                       else np.empty(X.shape[0], np.int32))
+        data = make_data(X, X_bf16)
+        p = default_params(**params)
+        t = ctypes.c_int64()
+        self._raise(load().kmeans_server_submit(self.handle, ctypes.byref(data), C0.shape[0], _ptr(C0),
+                                                ctypes.byref(p), _ptr(C_out), _ptr(rho_out), ctypes.byref(t)))
+        self._keep[t.value] = (X, X_bf16, C0, C_out, rho_out)
+        return t.value
+
+    def step(self) -> int:
+        n = ctypes.c_int32()
+        self._raise(load().kmeans_server_step(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, ticket: int):
+        done = ctypes.c_int32()
+        info = kmeans_info()
+        self._raise(load().kmeans_server_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(info)))
+        if not done.value:
+            return None
+        _, _, _, C_out, rho_out = self._keep.pop(ticket)
+        return C_out, rho_out, info.as_dict()
+
+    def stats(self) -> dict:
+        s = kmeans_server_stats()
+        self._raise(load().kmeans_server_get_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().kmeans_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_describe(ctx: Context) -> str:
+    return load().kmeans_batch_describe(ctx.handle).decode()
 
 
 def exported_symbols():

@@ -5,8 +5,8 @@
 //          (F_j = 0 for an empty cluster, which keeps its centroid).  In the solver it also
 //          forms dF = F^t - F^{t-1} and dG = G^t - G^{t-1} (the differences of Eq. 7 / Eq. 8)
 //          into the history rings, and the new row of the FP64 Gram matrix of the dF columns
-//          plus the right-hand side <dF_j, F^t> (the "m inner products between (Kd)-dimensional
-//          vectors" of Section 2.1).  The last block solves the m_t x m_t least-squares problem
+//          plus the right-hand side <dF_j, F^t> (m inner products of length K*d, the per-
+//          iteration cost Section 2.1 counts).  The last block solves the m_t x m_t least-squares problem
 //          through the Cholesky factor of the Gram matrix (= the R factor of the QR of dF),
 //          dropping columns from the first with R_kk <= rank_tol * R_00 on, closes the iteration
 //          of Algorithm 1 and, when K*d is small, also forms the accelerated iterate.
@@ -128,20 +128,20 @@ __device__ void mix_pack_centroid(int j, int K, int d, int DP, int fp32_path, do
     }
 }
 
-__global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
+// The work of block `bid` of a finalize launch with `nblk` blocks (see k_fin / k_fin_batch).
+__device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const int nblk, unsigned char* smem)
 {
     SolveState* st = a.st;
     const bool solver = a.mode != MODE_STANDALONE;
     if (solver && st->done) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K, d = a.d, nb = a.nb;
-    const int j0 = blockIdx.x * a.KB;
+    const int j0 = bid * a.KB;
     const int kb = min(a.KB, K - j0);
     const int E = kb * (d + 1);
     int split = FIN_THREADS / max(E, 1);
     split = split < 1 ? 1 : (split > 32 ? 32 : split);
 
-    extern __shared__ __align__(16) unsigned char smem[];
     double* s_tot = reinterpret_cast<double*>(smem);             // [E]
     double* s_dfn = s_tot + E;                                    // [kb*d]
     double* s_F = s_dfn + (size_t)kb * d;                         // [kb*d]
@@ -300,14 +300,14 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
         for (int v = tid; v < 2 * nage; v += blockDim.x) {
             double acc = 0.0;
             for (int w = 0; w < nw; ++w) acc += s_red[v * 8 + w];
-            a.pDots[(size_t)blockIdx.x * DOTS + v] = acc;
+            a.pDots[(size_t)bid * DOTS + v] = acc;
         }
     }
 
     // ---- last block: Gram update, least squares, end of the iteration
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&st->ctr_fin, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (tid == 0) s_last = (atomicAdd(&st->ctr_fin, 1u) == (unsigned)nblk - 1u) ? 1u : 0u;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
             const int v = t >> 3, sp = t & 7;
             double acc = 0.0;
 #pragma unroll 8
-            for (int b = sp; b < (int)gridDim.x; b += 8) acc += __ldcg(a.pDots + (size_t)b * DOTS + v);
+            for (int b = sp; b < nblk; b += 8) acc += __ldcg(a.pDots + (size_t)b * DOTS + v);
             s_part[t] = acc;
         }
         __syncthreads();
@@ -426,12 +426,31 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
     }
 }
 
-__global__ void __launch_bounds__(256) k_mix(MixArgs a)
+__global__ void __launch_bounds__(FIN_THREADS) k_fin(FinArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    fin_body(a, blockIdx.x, gridDim.x, smem);
+}
+
+// Persistent batched finalize over work items (instance, block of that instance).
+__global__ void __launch_bounds__(FIN_THREADS) k_fin_batch(BatchFin b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const int2 w = b.items[it];
+        FinArgs a = b.args[w.x];
+        a.mode = b.mode;
+        a.use_cond = 0;
+        fin_body(a, w.y, a.nblk, smem);
+        __syncthreads();
+    }
+}
+
+// Block `bid` (256 threads, 8 centroids) of the mix.
+__device__ __forceinline__ void mix_body(const MixArgs& a, const int bid)
 {
     SolveState* st = a.st;
     if (st->done) return;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= a.K) return;
     __shared__ double s_th[MMAX];
     __shared__ int s_sl[MMAX];
     const int rank = a.mode == MODE_INIT ? 0 : st->rank;
@@ -441,14 +460,32 @@ __global__ void __launch_bounds__(256) k_mix(MixArgs a)
         s_sl[threadIdx.x] = (head - (int)threadIdx.x + m_max) % m_max;
     }
     __syncthreads();
-    mix_pack_centroid(j, a.K, a.d, a.DP, a.fp32_path, a.C64, a.CAU, a.dG, s_th, s_sl, rank, a.origin, a.cpk,
-                      a.c32);
+    const int j = (bid * blockDim.x + threadIdx.x) >> 5;
+    if (j < a.K)
+        mix_pack_centroid(j, a.K, a.d, a.DP, a.fp32_path, a.C64, a.CAU, a.dG, s_th, s_sl, rank, a.origin, a.cpk,
+                          a.c32);
+}
+
+__global__ void __launch_bounds__(256) k_mix(MixArgs a)
+{
+    mix_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_mix_batch(BatchMix b)
+{
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const int2 w = b.items[it];
+        MixArgs a = b.args[w.x];
+        a.mode = b.mode;
+        mix_body(a, w.y);
+        __syncthreads();
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_prep(const T* C0, int K, int d, int Kpad, int DP, int fp32_path,
-                                               double* C64, float* origin, float* cpk0, float* cpk1, float* c32_0,
-                                               SolveState* st, int m_init, int m_max)
+__device__ __forceinline__ void prep_body(const T* C0, int K, int d, int Kpad, int DP, int fp32_path, double* C64,
+                                          float* origin, float* cpk0, float* cpk1, float* c32_0, SolveState* st,
+                                          int m_init, int m_max)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ double s_red[32];
@@ -507,6 +544,30 @@ __global__ void __launch_bounds__(1024) k_prep(const T* C0, int K, int d, int Kp
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) k_prep(const T* C0, int K, int d, int Kpad, int DP, int fp32_path,
+                                               double* C64, float* origin, float* cpk0, float* cpk1, float* c32_0,
+                                               SolveState* st, int m_init, int m_max)
+{
+    prep_body<T>(C0, K, d, Kpad, DP, fp32_path, C64, origin, cpk0, cpk1, c32_0, st, m_init, m_max);
+}
+
+// One block per instance: the pass counter, then what k_prep does for a single solve.
+__global__ void __launch_bounds__(1024) k_prep_batch(BatchPrep b)
+{
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const PrepArgs p = b.args[b.items[it].x];
+        if (threadIdx.x < 64) p.counter[threadIdx.x] = 0u;
+        if (p.f64)
+            prep_body<double>(reinterpret_cast<const double*>(p.C0), p.K, p.d, p.Kpad, p.DP, 0, p.C64, p.origin,
+                              p.cpk0, p.cpk1, p.c32_0, p.st, p.m_init, p.m_max);
+        else
+            prep_body<float>(reinterpret_cast<const float*>(p.C0), p.K, p.d, p.Kpad, p.DP, p.pack, p.C64, p.origin,
+                             p.cpk0, p.cpk1, p.c32_0, p.st, p.m_init, p.m_max);
+        __syncthreads();
+    }
+}
+
 struct DevInfo {
     int iters, accepted, rejected, passes, converged, m_final, status, pad;
     double E;
@@ -514,12 +575,13 @@ struct DevInfo {
 };
 
 template <typename T>
-__global__ void k_epi(const SolveState* st, const double* C64, const double* CAU, T* C_out, size_t n,
-                      const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N, DevInfo* info)
+__device__ __forceinline__ void epi_body(const SolveState* st, const double* C64, const double* CAU, T* C_out,
+                                         size_t n, const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out,
+                                         int64_t N, DevInfo* info, int bid, int nblk)
 {
     const double* src = st->final_src ? CAU : C64;
     const int32_t* rho = st->cur ? rhoB : rhoA;
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, T_ = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = (size_t)bid * blockDim.x + threadIdx.x, T_ = (size_t)nblk * blockDim.x;
     for (size_t i = tid; i < n; i += T_) C_out[i] = (T)src[i];
     for (size_t i = tid; i < (size_t)N; i += T_) rho_out[i] = rho[i];
     if (tid == 0) {
@@ -538,6 +600,61 @@ __global__ void k_epi(const SolveState* st, const double* C64, const double* CAU
     }
 }
 
+template <typename T>
+__global__ void k_epi(const SolveState* st, const double* C64, const double* CAU, T* C_out, size_t n,
+                      const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N, DevInfo* info)
+{
+    epi_body<T>(st, C64, CAU, C_out, n, rhoA, rhoB, rho_out, N, info, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_epi_batch(BatchEpi b)
+{
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const int2 w = b.items[it];
+        const EpiArgs& e = b.args[w.x];
+        if (e.f64)
+            epi_body<double>(e.st, e.C64, e.CAU, reinterpret_cast<double*>(e.C_out), e.n, e.rhoA, e.rhoB, e.rho_out,
+                             e.N, reinterpret_cast<DevInfo*>(e.info), w.y, e.nblk);
+        else
+            epi_body<float>(e.st, e.C64, e.CAU, reinterpret_cast<float*>(e.C_out), e.n, e.rhoA, e.rhoB, e.rho_out,
+                            e.N, reinterpret_cast<DevInfo*>(e.info), w.y, e.nblk);
+    }
+}
+
+// End of one batched loop pass: every instance done (or the guard) ends the while loop.
+__global__ void __launch_bounds__(256) k_batch_done(BatchDone b)
+{
+    __shared__ int s_open;
+    if (threadIdx.x == 0) s_open = 0;
+    __syncthreads();
+    const unsigned int loops = *b.loops + 1u;
+    const bool guard = loops > b.max_loops;
+    int open = 0;
+    for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
+        SolveState* st = b.st[i];
+        if (!st) continue;
+        if (!st->done) {
+            if (guard) {
+                st->status = KM_ETIMEOUT;
+                st->done = 1;
+            } else {
+                open = 1;
+            }
+        }
+    }
+    if (open) atomicOr(&s_open, 1);
+    __syncthreads();
+    if (b.flags)
+        for (int i = threadIdx.x; i < b.n; i += blockDim.x) b.flags[i] = b.st[i] ? b.st[i]->done : 0;
+    if (threadIdx.x == 0) {
+        *b.loops = loops;
+        if (!s_open) {
+            *b.all_done = 1;
+            if (b.use_cond) cudaGraphSetConditional(b.cond, 0);
+        }
+    }
+}
+
 }  // namespace
 
 int fin_blocks(int K, int d, int* KB)
@@ -548,10 +665,15 @@ int fin_blocks(int K, int d, int* KB)
     return (K + kb - 1) / kb;
 }
 
+size_t fin_smem(int KB, int d)
+{
+    const int E = KB * (d + 1);
+    return sizeof(double) * ((size_t)E + 2 * (size_t)KB * d + 2 * FIN_THREADS + 2 * MMAX * 8);
+}
+
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s)
 {
-    const int E = a.KB * (a.d + 1);
-    const size_t smem = sizeof(double) * ((size_t)E + 2 * (size_t)a.KB * a.d + 2 * FIN_THREADS + 2 * MMAX * 8);
+    const size_t smem = fin_smem(a.KB, a.d);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -595,5 +717,40 @@ cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const 
 }
 
 size_t devinfo_bytes() { return sizeof(DevInfo); }
+
+cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_fin_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_fin_batch<<<grid, FIN_THREADS, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mix_batch(const BatchMix& b, int grid, cudaStream_t s)
+{
+    k_mix_batch<<<grid, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(const BatchPrep& b, cudaStream_t s)
+{
+    const int grid = b.nitems < 1024 ? b.nitems : 1024;
+    k_prep_batch<<<grid, 1024, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epi_batch(const BatchEpi& b, int grid, cudaStream_t s)
+{
+    k_epi_batch<<<grid, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_done(const BatchDone& b, cudaStream_t s)
+{
+    k_batch_done<<<1, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
 
 }  // namespace km

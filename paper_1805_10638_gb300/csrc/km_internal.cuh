@@ -119,6 +119,7 @@ struct PassArgs {
     double eps1;
     double eps2;
     long long thr;
+    int nblk;                // blocks of this instance's pass (batched launches only)
 };
 
 // Arguments of the update / Anderson-finalize kernel.
@@ -157,6 +158,7 @@ struct FinArgs {
     const float* origin;
     float* cpk[2];
     float* c32[2];
+    int nblk;             // blocks of this instance's finalize launch (batched launches only)
 };
 
 // Arguments of the mix + pack kernel.
@@ -175,6 +177,84 @@ struct MixArgs {
     float* cpk[2];
     float* c32[2];
     SolveState* st;
+};
+
+// Once-per-solve setup of one instance (k_prep) and its result copy (k_epi).
+struct PrepArgs {
+    const void* C0;
+    int f64;
+    int K, d, Kpad, DP, pack;
+    double* C64;
+    float* origin;
+    float* cpk0;
+    float* cpk1;
+    float* c32_0;
+    SolveState* st;
+    int m_init, m_max;
+    unsigned int* counter;   // the pass counter, cleared here in batched solves
+};
+
+struct EpiArgs {
+    int f64;
+    const SolveState* st;
+    const double* C64;
+    const double* CAU;
+    void* C_out;
+    size_t n;
+    const int32_t* rhoA;
+    const int32_t* rhoB;
+    int32_t* rho_out;
+    int64_t N;
+    void* info;
+    int nblk;
+};
+
+// Batched launches: one persistent grid walks a list of work items (instance, block of that
+// instance); the per-instance arguments live in device tables.
+struct BatchPass {
+    const PassArgs* args;
+    const int2* items;
+    int nitems;
+    int mode;
+    int flags;
+};
+
+struct BatchFin {
+    const FinArgs* args;
+    const int2* items;
+    int nitems;
+    int mode;
+};
+
+struct BatchMix {
+    const MixArgs* args;
+    const int2* items;
+    int nitems;
+    int mode;
+};
+
+struct BatchPrep {
+    const PrepArgs* args;
+    const int2* items;       // (instance, 0)
+    int nitems;
+};
+
+struct BatchEpi {
+    const EpiArgs* args;
+    const int2* items;
+    int nitems;
+};
+
+// End-of-step check of a batched solve: all instances done -> end the graph's while loop.
+struct BatchDone {
+    SolveState* const* st;   // [n]; NULL entries (free serving slots) are skipped
+    int* flags;              // [n] or NULL: st[i]->done per entry, for the host
+    int n;
+    unsigned int* loops;     // loop passes so far (device counter, cleared by the prologue)
+    unsigned int max_loops;  // hard guard: unfinished instances get KM_ETIMEOUT
+    int* all_done;           // 1 once every instance is done (read by the host-loop mode)
+    int use_cond;
+    cudaGraphConditionalHandle cond;
 };
 
 // Packed scoring centroids of the FP32 path, pair-interleaved so that one fma.rn.f32x2 scores a
@@ -200,5 +280,15 @@ cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const 
                        size_t n, const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N,
                        void* info, cudaStream_t s);
 size_t devinfo_bytes();
+
+// Batched launchers (persistent grids over work items).
+cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s);
+int pass_lowd_batch_occupancy(int prec, int d, size_t smem);
+cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s);
+size_t fin_smem(int KB, int d);
+cudaError_t launch_mix_batch(const BatchMix& b, int grid, cudaStream_t s);
+cudaError_t launch_prep_batch(const BatchPrep& b, cudaStream_t s);
+cudaError_t launch_epi_batch(const BatchEpi& b, int grid, cudaStream_t s);
+cudaError_t launch_batch_done(const BatchDone& b, cudaStream_t s);
 
 }  // namespace km

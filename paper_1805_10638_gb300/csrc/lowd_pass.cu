@@ -255,13 +255,15 @@ __device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int
     return idx;
 }
 
+// The work of block `bid` of a pass launched with `nblk` blocks.  The standalone kernel calls it
+// with (blockIdx.x, gridDim.x); the batched kernel with a work item's (block, blocks of that
+// instance), so that every instance gets exactly the arithmetic of its own launch.
 template <typename T, int D>
-__global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
+__device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, const int nblk, unsigned char* smem)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int DP = Shape<D>::DP;
     constexpr int R = F32 ? Shape<D>::R : 1;
-    extern __shared__ __align__(16) unsigned char smem[];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     SolveState* st = a.st;
@@ -381,8 +383,8 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
 
     const T* X = reinterpret_cast<const T*>(a.X);
     const int64_t N = a.N;
-    const int64_t TT = (int64_t)gridDim.x * blockDim.x;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + tid;
+    const int64_t TT = (int64_t)nblk * blockDim.x;
+    const int64_t g = (int64_t)bid * blockDim.x + tid;
     const int64_t n_g = g < N ? (N - 1 - g) / TT + 1 : 0;
     const int64_t n_min = __shfl_sync(FULL, n_g, 31);
     const int64_t n_max = __shfl_sync(FULL, n_g, 0);
@@ -562,20 +564,20 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
     const long long nb_rs = block_sum_ll(resc, s_red);
     const long long nb_bad = block_sum_ll(bad, s_red);
     if (tid == 0) {
-        a.pE[blockIdx.x] = eb;
-        a.pNch[blockIdx.x] = nb_ch;
-        a.pResc[blockIdx.x] = nb_rs;
-        a.pBad[blockIdx.x] = (int)(nb_bad != 0);
+        a.pE[bid] = eb;
+        a.pNch[bid] = nb_ch;
+        a.pResc[bid] = nb_rs;
+        a.pBad[bid] = (int)(nb_bad != 0);
     }
     if (do_bins) {
         __syncthreads();
-        T* pS = reinterpret_cast<T*>(a.pS) + (size_t)blockIdx.x * K * D;
+        T* pS = reinterpret_cast<T*>(a.pS) + (size_t)bid * K * D;
         for (int e = tid; e < K * D; e += blockDim.x) {
             T s = T(0);
             for (int w = 0; w < W; ++w) s += s_bS[(size_t)w * K * D + e];
             pS[e] = s;
         }
-        int32_t* pC = a.pCnt + (size_t)blockIdx.x * K;
+        int32_t* pC = a.pCnt + (size_t)bid * K;
         for (int j = tid; j < K; j += blockDim.x) {
             int s = 0;
             for (int w = 0; w < W; ++w) s += s_bC[w * K + j];
@@ -589,14 +591,14 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
     unsigned int* sflag = reinterpret_cast<unsigned int*>(s_red + 40);
     if (tid == 0) {
         const unsigned int prev = atomicAdd(a.counter, 1u);
-        *sflag = (prev == gridDim.x - 1) ? 1u : 0u;
+        *sflag = (prev == (unsigned)nblk - 1u) ? 1u : 0u;
     }
     __syncthreads();
     if (*sflag == 0u) return;
     __threadfence();
     double E = 0.0;
     long long ch = 0, rs = 0, bd = 0;
-    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = tid; b < nblk; b += blockDim.x) {
         E += __ldcg(a.pE + b);
         ch += __ldcg(a.pNch + b);
         rs += __ldcg(a.pResc + b);
@@ -632,6 +634,32 @@ __global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
 }
 
 template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd(PassArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    pass_body<T, D>(a, blockIdx.x, gridDim.x, smem);
+}
+
+// Persistent batched pass: each block takes work items (instance, block of that instance) in
+// turn; an item does what that block of the instance's own launch would do (same rows, same
+// partial slot, the instance's last item runs its reduction and controller).  No item waits for
+// another, so any grid size is safe.
+template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS) k_pass_lowd_batch(BatchPass b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const int2 w = b.items[it];
+        PassArgs a = b.args[w.x];
+        a.mode = b.mode;
+        a.flags = b.flags;
+        a.use_cond = 0;
+        pass_body<T, D>(a, w.y, a.nblk, smem);
+        __syncthreads();
+    }
+}
+
+template <typename T, int D>
 cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
 {
     auto kern = k_pass_lowd<T, D>;
@@ -643,6 +671,30 @@ cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
     }
     kern<<<nb, LOWD_THREADS, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t launch_batch_one(const BatchPass& b, int grid, size_t smem, cudaStream_t s)
+{
+    auto kern = k_pass_lowd_batch<T, D>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<grid, LOWD_THREADS, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+int batch_occ(size_t smem)
+{
+    int n = 0;
+    auto kern = k_pass_lowd_batch<T, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
 }
 
 }  // namespace
@@ -684,6 +736,63 @@ cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStr
         KM_LOWD_CASE(16)
         default:
             return cudaErrorInvalidValue;
+    }
+}
+
+#define KM_BATCH_CASE(DD)                                                             \
+    case DD:                                                                          \
+        return prec == KM_F64 ? launch_batch_one<double, DD>(b, grid, smem, s)        \
+                              : launch_batch_one<float, DD>(b, grid, smem, s);
+
+cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s)
+{
+    switch (d) {
+        KM_BATCH_CASE(1)
+        KM_BATCH_CASE(2)
+        KM_BATCH_CASE(3)
+        KM_BATCH_CASE(4)
+        KM_BATCH_CASE(5)
+        KM_BATCH_CASE(6)
+        KM_BATCH_CASE(7)
+        KM_BATCH_CASE(8)
+        KM_BATCH_CASE(9)
+        KM_BATCH_CASE(10)
+        KM_BATCH_CASE(11)
+        KM_BATCH_CASE(12)
+        KM_BATCH_CASE(13)
+        KM_BATCH_CASE(14)
+        KM_BATCH_CASE(15)
+        KM_BATCH_CASE(16)
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+#define KM_OCC_CASE(DD)                                                               \
+    case DD:                                                                          \
+        return prec == KM_F64 ? batch_occ<double, DD>(smem) : batch_occ<float, DD>(smem);
+
+int pass_lowd_batch_occupancy(int prec, int d, size_t smem)
+{
+    switch (d) {
+        KM_OCC_CASE(1)
+        KM_OCC_CASE(2)
+        KM_OCC_CASE(3)
+        KM_OCC_CASE(4)
+        KM_OCC_CASE(5)
+        KM_OCC_CASE(6)
+        KM_OCC_CASE(7)
+        KM_OCC_CASE(8)
+        KM_OCC_CASE(9)
+        KM_OCC_CASE(10)
+        KM_OCC_CASE(11)
+        KM_OCC_CASE(12)
+        KM_OCC_CASE(13)
+        KM_OCC_CASE(14)
+        KM_OCC_CASE(15)
+        KM_OCC_CASE(16)
+        default:
+            return 1;
     }
 }
 

@@ -1,0 +1,814 @@
+// Host runtime shared by the solver entry points (api.cu) and the batched / serving entry points
+// (batch.cu): context, workspace plans, arena addressing, launch argument resolution and the
+// launch sequences of one solve (prologue, loop body, epilogue).
+#pragma once
+
+#include "dense.cuh"
+#include "km_internal.cuh"
+
+#include <cstdio>
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace km;
+
+namespace {
+
+struct GraphKey {
+    const void* X;
+    const void* Xb;
+    int64_t N;
+    int d, K, prec;
+    const void* C0;
+    void* C_out;
+    int32_t* rho_out;
+    kmeans_params p;
+    void* arena;
+    size_t arena_bytes;
+};
+
+struct Plan {
+    // offsets into the arena
+    size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
+    size_t pS, pCnt, pE, pNch, pResc, pBad, pDots, counter, info;
+    size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
+    // dense path (tensor-core assignment, sort-based update)
+    size_t cb0, cb1, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
+        part, pe, pnch, S, rowe, rown;
+    size_t total;
+    int nb, nfin, KB, Kpad, DP;
+    bool dense;
+    int dpad, nbk, rpb, max_chunks;
+    size_t smem;
+};
+
+constexpr int DENSE_RPB = 4096;   // rows per block of the dense update's histogram and scatter
+constexpr int DENSE_SEG = 64;     // rows per segment-sum chunk
+
+}  // namespace
+
+struct kmeans_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    size_t budget = 0;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    int nsm = 0;
+    std::string err;
+    bool have_graph = false;
+    GraphKey key{};
+    cudaGraphExec_t exec = nullptr;
+    void* h_info = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::mutex mu;
+    // batched solves: the graph of the last batch shape and its launch shapes
+    bool have_bgraph = false;
+    std::string bkey;
+    cudaGraphExec_t bexec = nullptr;
+    std::string bdesc;
+    std::vector<int> bgrids;
+    void* h_binfo = nullptr;
+    size_t h_binfo_bytes = 0;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+kmeans_status fail(kmeans_ctx* c, kmeans_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+kmeans_status cuda_fail(kmeans_ctx* c, cudaError_t e, const char* where)
+{
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    return fail(c, KM_ECUDA, buf);
+}
+
+#define KM_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+kmeans_status check_data(kmeans_ctx* ctx, const kmeans_data* X, int K, bool need_bf16)
+{
+    if (!X || !X->X) return fail(ctx, KM_EINVAL, "X is NULL");
+    if (X->N < 1 || X->d < 1 || X->d > 4096) return fail(ctx, KM_EINVAL, "need N >= 1 and 1 <= d <= 4096");
+    if (K < 1 || (int64_t)K > X->N) return fail(ctx, KM_EINVAL, "need 1 <= K <= N");
+    if (X->prec != KM_F64 && X->prec != KM_F32 && X->prec != KM_BF16_F32)
+        return fail(ctx, KM_EINVAL, "unknown precision");
+    if (X->prec == KM_BF16_F32 && need_bf16 && !X->X_bf16) return fail(ctx, KM_EINVAL, "X_bf16 is NULL");
+    return KM_OK;
+}
+
+int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem)
+{
+    int per_sm = (int)((200 * 1024) / (smem + 2048));
+    if (per_sm > 2) per_sm = 2;           // register-limited: 256 threads x ~128 registers
+    if (per_sm < 1) per_sm = 1;
+    int64_t nb = (int64_t)ctx->nsm * per_sm;
+    const int64_t need = (N + LOWD_THREADS - 1) / LOWD_THREADS;
+    if (nb > need) nb = need;
+    if (nb < 1) nb = 1;
+    return (int)nb;
+}
+
+// Workspace layout of one problem shape (bins = fused per-block update partials).
+// Dense path: BF16 tensor-core assignment, sort-based update (d in 17..128, d % 8 == 0).
+kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_max, bool host_copies, Plan& P)
+{
+    if (d > 128 || d % 8 != 0)
+        return fail(ctx, KM_EINVAL, "the tensor-core path needs d <= 128 and d % 8 == 0");
+    if (K > 4096) return fail(ctx, KM_EINVAL, "the tensor-core path supports K <= 4096");
+    P.dense = true;
+    P.dpad = (d + 63) / 64 * 64;
+    P.Kpad = (K + 255) / 256 * 256;
+    P.DP = 0;
+    P.nb = 1;
+    P.nfin = fin_blocks(K, d, &P.KB);
+    P.rpb = DENSE_RPB;
+    P.nbk = (int)((N + DENSE_RPB - 1) / DENSE_RPB);
+    P.max_chunks = (int)((N + DENSE_SEG - 1) / DENSE_SEG) + K;
+    P.smem = 0;
+    const size_t n = (size_t)K * d;
+    const int mm = m_max > 0 ? m_max : 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
+    P.counter = take(256);
+    P.st = take(sizeof(SolveState));
+    P.rhoA = take((size_t)N * 4);
+    P.rhoB = take((size_t)N * 4);
+    P.C64 = take(n * 8);
+    P.CAU = take(n * 8);
+    P.Fprev = take(n * 8);
+    P.dF = take((size_t)mm * n * 8);
+    P.dG = take((size_t)mm * n * 8);
+    P.cpk0 = P.cpk1 = 0;
+    P.c32_0 = take(n * 4);
+    P.c32_1 = take(n * 4);
+    P.origin = take(256);
+    P.cb0 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cb1 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cn0 = take((size_t)P.Kpad * 4);
+    P.cn1 = take((size_t)P.Kpad * 4);
+    P.xnorm = take((size_t)N * 4);
+    P.queue = take((size_t)N * 4 * 4);   // full-rescore rows, then (row, i1, i2) candidate pairs
+    P.qcount = take(256);
+    P.err = take(256);
+    P.hist = take((size_t)K * P.nbk * 4);
+    P.counts = take((size_t)K * 4);
+    P.off = take((size_t)(K + 1) * 4);
+    P.choff = take((size_t)K * 4);
+    P.chunk_cluster = take((size_t)P.max_chunks * 4);
+    P.nchunks = take(256);
+    P.perm = take((size_t)N * 4);
+    P.part = take((size_t)P.max_chunks * d * 4);
+    P.pe = take((size_t)P.max_chunks * 8);
+    P.pnch = take((size_t)P.nbk * 8);
+    P.S = take(n * 8);
+    P.rowe = take(4096 * 8);
+    P.rown = take(4096 * 8);
+    P.pS = P.S;
+    P.pCnt = P.counts;
+    P.pE = P.pNch = P.pResc = P.pBad = 0;
+    P.pDots = take((size_t)P.nfin * DOTS * 8);
+    P.info = take(256);
+    if (host_copies) {
+        P.hX = take((size_t)N * d * 4);
+        P.hXb = take((size_t)N * d * 2);
+        P.hC0 = take(n * 4);
+        P.hCout = take(n * 4);
+        P.hRho = take((size_t)N * 4);
+    } else {
+        P.hX = P.hXb = P.hC0 = P.hCout = P.hRho = 0;
+    }
+    P.total = o;
+    return KM_OK;
+}
+
+kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
+                        Plan& P, bool bins = true)
+{
+    P.dense = false;
+    P.dpad = P.nbk = P.rpb = P.max_chunks = 0;
+    if (prec == KM_BF16_F32 && d > 16) return make_plan_dense(ctx, N, d, K, m_max, host_copies, P);
+    if (d > 16) return fail(ctx, KM_EINVAL, "d > 16 needs KM_BF16_F32 (the tensor-core path)");
+    const bool f32 = prec != KM_F64;
+    const size_t esz = f32 ? 4 : 8;
+    P.DP = pass_lowd_dp(d);
+    P.Kpad = (K + CH - 1) / CH * CH;
+    P.smem = pass_lowd_smem(prec, d, K, P.Kpad, bins);
+    if (P.smem > 200 * 1024)
+        return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
+    P.nb = pass_blocks(ctx, N, P.smem);
+    P.nfin = fin_blocks(K, d, &P.KB);
+    const size_t n = (size_t)K * d;
+    const int mm = m_max > 0 ? m_max : 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
+    P.counter = take(256);          // fixed offset 0 for every plan; zeroed at the start of every call
+    P.st = take(sizeof(SolveState));
+    P.rhoA = take((size_t)N * 4);
+    P.rhoB = take((size_t)N * 4);
+    P.C64 = take(n * 8);
+    P.CAU = take(n * 8);
+    P.Fprev = take(n * 8);
+    P.dF = take((size_t)mm * n * 8);
+    P.dG = take((size_t)mm * n * 8);
+    P.cpk0 = take((size_t)P.Kpad * P.DP * 4);
+    P.cpk1 = take((size_t)P.Kpad * P.DP * 4);
+    P.c32_0 = take(n * 4);
+    P.c32_1 = take(n * 4);
+    P.origin = take(64 * 4);
+    P.pS = take((size_t)P.nb * n * esz);
+    P.pCnt = take((size_t)P.nb * K * 4);
+    P.pE = take((size_t)P.nb * 8);
+    P.pNch = take((size_t)P.nb * 8);
+    P.pResc = take((size_t)P.nb * 8);
+    P.pBad = take((size_t)P.nb * 4);
+    P.pDots = take((size_t)P.nfin * DOTS * 8);
+    P.info = take(256);
+    if (host_copies) {
+        P.hX = take((size_t)N * d * esz);
+        P.hXb = 0;
+        P.hC0 = take(n * esz);
+        P.hCout = take(n * esz);
+        P.hRho = take((size_t)N * 4);
+    } else {
+        P.hX = P.hXb = P.hC0 = P.hCout = P.hRho = 0;
+    }
+    P.total = o;
+    return KM_OK;
+}
+
+kmeans_status ensure_arena(kmeans_ctx* ctx, size_t bytes)
+{
+    if (ctx->arena && ctx->arena_bytes >= bytes) return KM_OK;
+    if (ctx->budget && bytes > ctx->budget) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "workspace of %zu bytes exceeds the HBM budget of %zu bytes", bytes, ctx->budget);
+        return fail(ctx, KM_ENOMEM, buf);
+    }
+    if (ctx->have_graph) {
+        cudaGraphExecDestroy(ctx->exec);
+        ctx->have_graph = false;
+    }
+    if (ctx->have_bgraph) {
+        cudaGraphExecDestroy(ctx->bexec);
+        ctx->have_bgraph = false;
+        ctx->bkey.clear();
+    }
+    if (ctx->arena) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset");
+    ctx->arena = p;
+    ctx->arena_bytes = bytes;
+    return KM_OK;
+}
+
+template <typename T>
+T* at(char* base, size_t off)
+{
+    return reinterpret_cast<T*>(base + off);
+}
+
+inline char* arena_base(kmeans_ctx* ctx) { return static_cast<char*>(ctx->arena); }
+
+PassArgs base_pass(char* base, const Plan& P, const void* X, int64_t N, int K, int prec)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.N = N;
+    a.K = K;
+    a.Kpad = P.Kpad;
+    a.cpk[0] = at<float>(base, P.cpk0);
+    a.cpk[1] = at<float>(base, P.cpk1);
+    a.c32[0] = at<float>(base, P.c32_0);
+    a.c32[1] = at<float>(base, P.c32_1);
+    a.c64[0] = at<double>(base, P.C64);
+    a.c64[1] = at<double>(base, P.CAU);
+    a.origin = at<float>(base, P.origin);
+    a.rho[0] = at<int32_t>(base, P.rhoA);
+    a.rho[1] = at<int32_t>(base, P.rhoB);
+    a.pS = at<void>(base, P.pS);
+    a.pCnt = at<int32_t>(base, P.pCnt);
+    a.pE = at<double>(base, P.pE);
+    a.pNch = at<long long>(base, P.pNch);
+    a.pResc = at<long long>(base, P.pResc);
+    a.pBad = at<int>(base, P.pBad);
+    a.counter = at<unsigned int>(base, P.counter);
+    a.st = at<SolveState>(base, P.st);
+    (void)prec;
+    return a;
+}
+
+// First-order rounding-error bound of the FP32 score ||c'||^2 - 2 x'.c' (u = 2^-24), with a 1%
+// allowance for second-order terms:  D FMAs on partial sums <= ||c'||^2 + 2|x'||c'|, the rounding of
+// ||c'||^2, of c' = fl(c - o) and of x' = fl(x - o):
+//   |err| <= u * ((D + 3) max|c'|^2 + (2D + 4) |x'| max|c'|).
+void set_bound(PassArgs& a, int d)
+{
+    const double u = 5.9604644775390625e-8;
+    a.bound_coef = (float)(1.01 * (d + 3) * u);
+    a.bound_coef2 = (float)(1.01 * (2 * d + 4) * u);
+}
+
+
+// The accelerated iterate is formed inside k_fin's last block when K*d is small (saves a launch).
+inline bool fuse_mix_rule(int K, int d) { return K <= 1024 && (size_t)K * d <= 16384; }
+
+// Everything one solve launches, resolved to device pointers once.
+struct Launch {
+    PassArgs pa;
+    FinArgs fa;
+    MixArgs ma;
+    Plan P;
+    kmeans_params p;
+    const void* C0;
+    void* C_out;
+    int32_t* rho_out;
+    SolveState* st;
+    void* info;
+    int32_t* rhoA;
+    int32_t* rhoB;
+    int64_t N;
+    int d, K, prec, m_max;
+    bool f64;
+    // dense path
+    DenseArgs da;
+    PackArgs pk;
+    const float* X32;
+    int nsm;
+    alignas(64) unsigned char tmX[128];
+    alignas(64) unsigned char tmC0[128];
+    alignas(64) unsigned char tmC1[128];
+    bool maps_ok = true;
+};
+
+// Dense-path arguments over the plan's buffers (centroid sets 0 = C^t, 1 = C_AU).
+DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int d, int K)
+{
+    DenseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.N = N;
+    a.d = d;
+    a.dpad = P.dpad;
+    a.K = K;
+    a.Kpad = P.Kpad;
+    a.X = X32;
+    a.xnorm = at<float>(base, P.xnorm);
+    a.cn[0] = at<float>(base, P.cn0);
+    a.cn[1] = at<float>(base, P.cn1);
+    a.c32[0] = at<float>(base, P.c32_0);
+    a.c32[1] = at<float>(base, P.c32_1);
+    a.c64[0] = at<double>(base, P.C64);
+    a.c64[1] = at<double>(base, P.CAU);
+    // BF16 score error bound: 2 (2 u_b + d u) |x| max|c| for 2 x.c, u max|c|^2 for ||c||^2, with a
+    // factor 2 of allowance for the accumulation order inside the MMA
+    const double ub = 1.0 / 512.0, u = 5.9604644775390625e-8;
+    a.bcoef_a = (float)(2.0 * (2.0 * (2.0 * ub + d * u)) * (1.0 + 2.0 * ub));
+    a.bcoef_b = (float)(2.0 * 2.0 * u);
+    a.rho_pair[0] = at<int32_t>(base, P.rhoA);
+    a.rho_pair[1] = at<int32_t>(base, P.rhoB);
+    a.queue = at<int>(base, P.queue);
+    a.cand = at<int>(base, P.queue) + N;
+    a.qcount = at<unsigned int>(base, P.qcount);
+    a.err = at<int>(base, P.err);
+    a.rows_per_block = P.rpb;
+    a.hist = at<int>(base, P.hist);
+    a.counts = at<int32_t>(base, P.counts);
+    a.off = at<int>(base, P.off);
+    a.choff = at<int>(base, P.choff);
+    a.chunk_cluster = at<int>(base, P.chunk_cluster);
+    a.nchunks = at<int>(base, P.nchunks);
+    a.perm = at<int>(base, P.perm);
+    a.part = at<float>(base, P.part);
+    a.pe = at<double>(base, P.pe);
+    a.pnch = at<long long>(base, P.pnch);
+    a.S = at<double>(base, P.S);
+    a.counter = at<unsigned int>(base, P.counter);
+    a.st = at<SolveState>(base, P.st);
+    return a;
+}
+
+PackArgs pack_args(char* base, const Plan& P, int d, int K)
+{
+    PackArgs p;
+    memset(&p, 0, sizeof(p));
+    p.K = K;
+    p.Kpad = P.Kpad;
+    p.d = d;
+    p.dpad = P.dpad;
+    p.nsets = 2;
+    p.src64[0] = at<double>(base, P.C64);
+    p.src64[1] = at<double>(base, P.CAU);
+    p.cb[0] = at<__nv_bfloat16>(base, P.cb0);
+    p.cb[1] = at<__nv_bfloat16>(base, P.cb1);
+    p.cn[0] = at<float>(base, P.cn0);
+    p.cn[1] = at<float>(base, P.cn1);
+    p.c32[0] = at<float>(base, P.c32_0);
+    p.c32[1] = at<float>(base, P.c32_1);
+    p.st = at<SolveState>(base, P.st);
+    return p;
+}
+
+bool dense_maps(char* base, const Plan& P, const void* Xb, int64_t N, int d, void* tmX, void* tmC0, void* tmC1)
+{
+    return make_tmap_bf16(tmX, Xb, N, d, 128) &&
+           make_tmap_bf16(tmC0, at<void>(base, P.cb0), P.Kpad, P.dpad, 256) &&
+           make_tmap_bf16(tmC1, at<void>(base, P.cb1), P.Kpad, P.dpad, 256);
+}
+
+Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int K, const void* C0,
+                   const kmeans_params& p, void* C_out, int32_t* rho_out)
+{
+    Launch L;
+    L.P = P;
+    L.p = p;
+    L.C0 = C0;
+    L.C_out = C_out;
+    L.rho_out = rho_out;
+    L.N = X->N;
+    L.d = X->d;
+    L.K = K;
+    L.prec = X->prec;
+    L.f64 = X->prec == KM_F64;
+    L.m_max = p.lloyd_only ? 0 : p.m_max;
+    L.st = at<SolveState>(base, P.st);
+    L.info = at<void>(base, P.info);
+    L.rhoA = at<int32_t>(base, P.rhoA);
+    L.rhoB = at<int32_t>(base, P.rhoB);
+    const int d = X->d;
+    const int64_t thr = p.tol > 0 ? (int64_t)(p.tol * (double)X->N) : 0;
+
+    PassArgs& pa = L.pa;
+    pa = base_pass(base, P, X->X, X->N, K, X->prec);
+    set_bound(pa, d);
+    pa.m_max = L.m_max;
+    pa.max_iter = p.max_iter;
+    pa.lloyd_only = p.lloyd_only;
+    pa.eps1 = p.eps1;
+    pa.eps2 = p.eps2;
+    pa.thr = thr;
+
+    FinArgs& fa = L.fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.K = K;
+    fa.d = d;
+    fa.nb = P.nb;
+    fa.part_f64 = L.f64;
+    fa.pS = at<void>(base, P.pS);
+    fa.pCnt = at<int32_t>(base, P.pCnt);
+    fa.KB = P.KB;
+    fa.C64 = at<double>(base, P.C64);
+    fa.CAU = at<double>(base, P.CAU);
+    fa.Fprev = at<double>(base, P.Fprev);
+    fa.dF = at<double>(base, P.dF);
+    fa.dG = at<double>(base, P.dG);
+    fa.pDots = at<double>(base, P.pDots);
+    fa.st = L.st;
+    fa.m_max = L.m_max;
+    fa.max_iter = p.max_iter;
+    fa.lloyd_only = p.lloyd_only;
+    fa.rank_tol = p.rank_tol;
+    fa.fuse_mix = fuse_mix_rule(K, d) ? 1 : 0;
+    fa.DP = P.DP;
+    fa.fp32_path = !L.f64;
+    fa.origin = at<float>(base, P.origin);
+    fa.cpk[0] = at<float>(base, P.cpk0);
+    fa.cpk[1] = at<float>(base, P.cpk1);
+    fa.c32[0] = at<float>(base, P.c32_0);
+    fa.c32[1] = at<float>(base, P.c32_1);
+
+    MixArgs& ma = L.ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.K = K;
+    ma.d = d;
+    ma.Kpad = P.Kpad;
+    ma.DP = P.DP;
+    ma.fp32_path = !L.f64;
+    ma.C64 = at<double>(base, P.C64);
+    ma.CAU = at<double>(base, P.CAU);
+    ma.dG = at<double>(base, P.dG);
+    ma.m_max = L.m_max > 0 ? L.m_max : 1;
+    ma.origin = at<float>(base, P.origin);
+    ma.cpk[0] = at<float>(base, P.cpk0);
+    ma.cpk[1] = at<float>(base, P.cpk1);
+    ma.c32[0] = at<float>(base, P.c32_0);
+    ma.c32[1] = at<float>(base, P.c32_1);
+    ma.st = L.st;
+
+    L.nsm = nsm;
+    L.X32 = reinterpret_cast<const float*>(X->X);
+    if (P.dense) {
+        fa.part_f64 = 1;                 // S: FP64 residual sums per cluster, one "partial block"
+        fa.fuse_mix = 0;
+        fa.fp32_path = 0;
+        ma.fp32_path = 0;                // the mix only writes C; the BF16 packing is separate
+        DenseArgs& da = L.da;
+        da = dense_args(base, P, L.X32, X->N, d, K);
+        da.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
+        da.thr = thr;
+        da.lloyd_only = p.lloyd_only;
+        da.eps1 = p.eps1;
+        da.eps2 = p.eps2;
+        da.m_max = L.m_max;
+        da.max_iter = p.max_iter;
+        L.pk = pack_args(base, P, d, K);
+        L.pk.check_done = 1;
+        L.maps_ok = dense_maps(base, P, X->X_bf16, X->N, d, L.tmX, L.tmC0, L.tmC1);
+    }
+    return L;
+}
+
+// One dense pass (assignment, rescoring, update chain with the controller) in the given mode.
+cudaError_t dense_pass(const Launch& L, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s,
+                       bool assign = true)
+{
+    DenseArgs a = L.da;
+    a.mode = mode;
+    a.use_cond = use_cond;
+    a.cond = h;
+    cudaError_t e = cudaSuccess;
+    if (assign) e = launch_dense_pass(a, L.tmX, L.tmC0, L.tmC1, L.nsm, s);
+    if (e == cudaSuccess) e = launch_dense_update(a, L.P.nbk, L.P.max_chunks, s);
+    return e;
+}
+
+// Prologue: C^0 -> P^0 -> G^0 = C^1 (Algorithm 1's first line).
+cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditionalHandle h)
+{
+    if (L.P.dense) {
+        cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
+        if (e == cudaSuccess)
+            e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
+                            nullptr, L.st, L.p.m_init, L.m_max, s, 0);
+        if (e == cudaSuccess) e = launch_xnorm(L.X32, L.N, L.d, const_cast<float*>(L.da.xnorm), L.st, L.nsm, s);
+        PackArgs pk = L.pk;
+        pk.nsets = 1;
+        pk.check_done = 0;
+        if (e == cudaSuccess) e = launch_pack_dense(pk, s);
+        if (e == cudaSuccess) e = dense_pass(L, MODE_INIT, 0, h, s);
+        FinArgs f = L.fa;
+        f.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+        MixArgs m = L.ma;
+        m.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+        pk = L.pk;
+        pk.check_done = 0;
+        if (e == cudaSuccess) e = launch_pack_dense(pk, s);
+        return e;
+    }
+    cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
+    if (e == cudaSuccess)
+        e = launch_prep(L.C0, L.f64, L.K, L.d, L.P.Kpad, L.P.DP, L.ma.C64, const_cast<float*>(L.ma.origin),
+                        L.ma.cpk[0], L.ma.cpk[1], L.ma.c32[0], L.st, L.p.m_init, L.m_max, s);
+    PassArgs a = L.pa;
+    a.mode = MODE_INIT;
+    a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
+    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    FinArgs f = L.fa;
+    f.mode = MODE_INIT;
+    if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+    if (!L.fa.fuse_mix) {
+        MixArgs m = L.ma;
+        m.mode = MODE_INIT;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+    }
+    (void)h;
+    return e;
+}
+
+// One loop pass t of Algorithm 1 (or Lloyd): trial assignment + controller, conditional revert,
+// update + history + least squares, accelerated iterate (which also ends the graph loop).
+cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h)
+{
+    if (L.P.dense) {
+        cudaError_t e = dense_pass(L, MODE_TRIAL, use_cond, h, s);
+        if (e == cudaSuccess) e = dense_pass(L, MODE_REVERT, use_cond, h, s);
+        FinArgs f = L.fa;
+        f.mode = MODE_TRIAL;
+        f.use_cond = use_cond;
+        f.cond = h;
+        if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+        MixArgs m = L.ma;
+        m.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+        if (e == cudaSuccess) e = launch_pack_dense(L.pk, s);
+        return e;
+    }
+    PassArgs a = L.pa;
+    a.mode = MODE_TRIAL;
+    a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
+    a.use_cond = use_cond;
+    a.cond = h;
+    cudaError_t e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    a.mode = MODE_REVERT;
+    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    FinArgs f = L.fa;
+    f.mode = MODE_TRIAL;
+    f.use_cond = use_cond;
+    f.cond = h;
+    if (e == cudaSuccess) e = launch_fin(f, L.P.nfin, s);
+    if (!L.fa.fuse_mix) {
+        MixArgs m = L.ma;
+        m.mode = MODE_TRIAL;
+        if (e == cudaSuccess) e = launch_mix(m, s);
+    }
+    return e;
+}
+
+// Epilogue: the energy of (P^t, G^t) if the loop stopped at max_iter, results and info.
+cudaError_t launch_epilogue(const Launch& L, cudaStream_t s)
+{
+    cudaError_t e;
+    if (L.P.dense) {
+        e = dense_pass(L, MODE_EPI, 0, 0, s, false);
+    } else {
+        PassArgs a = L.pa;
+        a.mode = MODE_EPI;
+        a.flags = F_ENERGY;
+        e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    }
+    if (e == cudaSuccess)
+        e = launch_epi(L.f64, L.st, L.ma.C64, L.ma.CAU, L.C_out, (size_t)L.K * L.d, L.rhoA, L.rhoB, L.rho_out, L.N,
+                       L.info, s);
+    return e;
+}
+
+// KM_GRAPH=0 in the environment launches the same kernels from a host loop (one wait per
+// iteration) instead of the graph; profilers cannot see kernels inside conditional graphs.
+bool graph_mode()
+{
+    const char* v = getenv("KM_GRAPH");
+    return !(v && v[0] == '0');
+}
+
+struct DevInfoH {
+    int iters, accepted, rejected, passes, converged, m_final, status, pad;
+    double E;
+    long long rescored;
+};
+
+kmeans_status validate_params(kmeans_ctx* ctx, const kmeans_params& p)
+{
+    if (p.m_max < 0 || p.m_max > MMAX) return fail(ctx, KM_EINVAL, "m_max must be in [0, 32]");
+    if (p.max_iter < 1) return fail(ctx, KM_EINVAL, "max_iter must be >= 1");
+    if (!(p.tol >= 0.0)) return fail(ctx, KM_EINVAL, "tol must be >= 0");
+    if (!(p.rank_tol >= 0.0)) return fail(ctx, KM_EINVAL, "rank_tol must be >= 0");
+    return KM_OK;
+}
+
+// Once-per-solve setup and result-copy arguments of one low-d solve (batched and serving paths).
+PrepArgs prep_args(const Launch& L, int m_init)
+{
+    PrepArgs pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.C0 = L.C0;
+    pp.f64 = L.f64;
+    pp.K = L.K;
+    pp.d = L.d;
+    pp.Kpad = L.P.Kpad;
+    pp.DP = L.P.DP;
+    pp.pack = 1;
+    pp.C64 = L.ma.C64;
+    pp.origin = const_cast<float*>(L.ma.origin);
+    pp.cpk0 = L.ma.cpk[0];
+    pp.cpk1 = L.ma.cpk[1];
+    pp.c32_0 = L.ma.c32[0];
+    pp.st = L.st;
+    pp.m_init = m_init;
+    pp.m_max = L.m_max;
+    pp.counter = L.pa.counter;
+    return pp;
+}
+
+int epi_blocks(int64_t N, size_t n)
+{
+    const int64_t big = std::max<int64_t>(N, (int64_t)n);
+    return (int)std::min<int64_t>(64, (big + 2047) / 2048);
+}
+
+EpiArgs epi_args(const Launch& L, void* info)
+{
+    EpiArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    ea.f64 = L.f64;
+    ea.st = L.st;
+    ea.C64 = L.ma.C64;
+    ea.CAU = L.ma.CAU;
+    ea.C_out = L.C_out;
+    ea.n = (size_t)L.K * L.d;
+    ea.rhoA = L.rhoA;
+    ea.rhoB = L.rhoB;
+    ea.rho_out = L.rho_out;
+    ea.N = L.N;
+    ea.info = info;
+    ea.nblk = epi_blocks(L.N, ea.n);
+    return ea;
+}
+
+// Work items of the mix kernel of a low-d solve (none when the accelerated iterate is fused).
+int mix_blocks(int K, int d) { return fuse_mix_rule(K, d) ? 0 : (K * 32 + 255) / 256; }
+
+void fill_info(kmeans_info* info, const DevInfoH* di, float ms)
+{
+    info->iters = di->iters;
+    info->accepted = di->accepted;
+    info->rejected = di->rejected;
+    info->assign_passes = di->passes;
+    info->converged = di->converged;
+    info->m_final = di->m_final;
+    info->E = di->E;
+    info->rescored_rows = di->rescored;
+    info->device_ms = ms;
+    info->status = di->status;
+    info->reserved = 0;
+}
+
+// Add  prologue -> while (cond) { body } -> epilogue  to graph g as an independent chain.  The
+// prologue and the epilogue are captured into child graphs, the body straight into the conditional
+// node's body graph; the body's kernels end the loop with cudaGraphSetConditional(h, 0).
+template <typename Pro, typename Body, typename Epi>
+kmeans_status add_while_chain(kmeans_ctx* ctx, cudaGraph_t g, Pro pro, Body body, Epi epi)
+{
+    cudaGraph_t gp = nullptr, ge = nullptr;
+    cudaGraphConditionalHandle h;
+    KM_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+
+    KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = pro(ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &gp);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "prologue launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "prologue capture");
+    }
+    cudaGraphNode_t np, nc, ne;
+    KM_CUDA(cudaGraphAddChildGraphNode(&np, g, nullptr, 0, gp));
+
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    KM_CUDA(cudaGraphAddNode(&nc, g, &np, nullptr, 1, &cp));
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    KM_CUDA(cudaStreamBeginCaptureToGraph(ctx->cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = body(ctx->cap, h);
+        cudaGraph_t bout = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &bout);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "loop body launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "loop body capture");
+    }
+
+    KM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = epi(ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &ge);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "epilogue launch");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "epilogue capture");
+    }
+    KM_CUDA(cudaGraphAddChildGraphNode(&ne, g, &nc, 1, ge));
+    cudaGraphDestroy(gp);
+    cudaGraphDestroy(ge);
+    return KM_OK;
+}
+
+// One executable graph holding one such chain.
+template <typename Pro, typename Body, typename Epi>
+kmeans_status record_while_graph(kmeans_ctx* ctx, Pro pro, Body body, Epi epi, cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    KM_CUDA(cudaGraphCreate(&g, 0));
+    kmeans_status s = add_while_chain(ctx, g, pro, body, epi);
+    if (s == KM_OK) {
+        cudaError_t e = cudaGraphInstantiate(out, g, 0);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    cudaGraphDestroy(g);
+    return s;
+}
+
+}  // namespace

@@ -48,6 +48,17 @@ def _env_int(k, d):
         return d
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest replica sets the job time); `dist`
+    is torch.distributed or None for a single process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def pct(v, q):
     v = sorted(v)
     if not v:
@@ -493,10 +504,7 @@ def run_ours(args, rank, world, local_rank):
 
     tot_aa = sum(ms_aa) / 1e3
     tot_ll = sum(ms_ll) / 1e3
-    if dist:
-        t = torch.tensor([tot_aa, tot_ll], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_aa, tot_ll = float(t[0]), float(t[1])
+    tot_aa, tot_ll = max_over_ranks([tot_aa, tot_ll], dist, "cuda")
 
     # ---- roofline of the dominant kernel: the assignment pass, timed standalone (CUDA events)
     rho_prev = rho.clone()
@@ -561,10 +569,7 @@ def run_ours(args, rank, world, local_rank):
         km.kmeans_solve_host(ctx, Xh, C0h[args.warmup + s], Coh, rh, X_bf16=Xbh, m_max=wl["m_max"], **solve_kw)
         e2e_t.append(time.perf_counter() - t0)
     e2e_tot = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t[0])
+    (e2e_tot,) = max_over_ranks([e2e_tot], dist, "cuda")
 
     # our kernels per solve: dense 13 (prologue) + 17 per loop pass + 6 (epilogue);
     # low-d with the accelerated iterate fused into the update kernel 3 + 3 per pass + 2

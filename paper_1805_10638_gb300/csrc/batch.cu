@@ -155,28 +155,35 @@ cudaError_t batch_epilogue(const Batch& B, cudaStream_t s)
     return e;
 }
 
-// Launch shapes of the pass kernels: for each group, time a standalone-mode pass (the same scan
-// over the group's data with the initial centroids) at every persistent grid from 1 block per SM
-// up to the occupancy limit, and with one block per work item; keep the fastest.
+// Launch shapes of the pass kernels.  After running the batch's prologue (so every instance holds
+// its packed C^1), time for each group a pass that does the loop pass's work (assignment, bins,
+// energy) at every persistent grid from 1 block per SM up to the occupancy limit, and with one
+// block per work item; keep the fastest.  The timed passes write only scratch (the second
+// assignment buffer and the block partials); the solve's own prologue runs again afterwards.
 kmeans_status tune_batch(kmeans_ctx* ctx, Batch& B, std::string& desc)
 {
     const char* env = getenv("KM_TUNE");
-    const bool tune = !(env && env[0] == '0');
+    const bool tune = !(env && env[0] == '0') && B.n_lowd > 0;
     char buf[256];
+    std::vector<int> occs;
     for (BGroup& g : B.groups) {
-        const int occ = pass_lowd_batch_occupancy(g.prec, g.d, g.smem);
+        occs.push_back(pass_lowd_batch_occupancy(g.prec, g.d, g.smem));
+        g.grid = std::min((int)g.items.size(), ctx->nsm * std::min(occs.back(), 2));
+    }
+    if (tune) KM_CUDA(batch_prologue(B, ctx->stream));
+    for (size_t gi = 0; gi < B.groups.size(); ++gi) {
+        BGroup& g = B.groups[gi];
+        const int occ = occs[gi];
         const int nit = (int)g.items.size();
         std::vector<int> cand;
         for (int bps = 1; bps <= occ; ++bps) cand.push_back(std::min(nit, ctx->nsm * bps));
         cand.push_back(nit);
         std::sort(cand.begin(), cand.end());
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        g.grid = std::min(nit, ctx->nsm * std::min(occ, 2));
         snprintf(buf, sizeof(buf), "%s d=%d items=%d occ=%d", g.prec == KM_F64 ? "f64" : "f32", g.d, nit, occ);
         desc += buf;
         if (tune && cand.size() > 1) {
-            const int fl = F_ASSIGN | (g.prec == KM_F64 ? 0 : F_PACK);
-            const BatchPass b = pass_launch(B, g, MODE_STANDALONE, fl, true);
+            const BatchPass b = pass_launch(B, g, MODE_STANDALONE, F_ASSIGN | F_BINS | F_ENERGY, true);
             float best = 1e30f;
             for (int grid : cand) {
                 KM_CUDA(launch_pass_lowd_batch(b, g.prec, g.d, grid, g.smem, ctx->stream));
@@ -308,10 +315,8 @@ kmeans_status batch_solve(kmeans_ctx* ctx, const kmeans_problem* pr, int n, cons
         PassArgs pa = Ln.pa;
         pa.nblk = bi.P.nb;
         put(L.t_pass + i * sizeof(PassArgs), &pa, sizeof(pa));
-        PassArgs tu = pa;
+        PassArgs tu = pa;          // standalone mode on the packed C^1 the prologue leaves
         tu.rho[0] = Ln.rhoB;
-        if (Ln.f64) tu.c64[0] = reinterpret_cast<const double*>(q.C0);
-        else tu.rawC = reinterpret_cast<const float*>(q.C0);
         put(L.t_tune + i * sizeof(PassArgs), &tu, sizeof(tu));
         FinArgs fa = Ln.fa;
         fa.nblk = bi.P.nfin;

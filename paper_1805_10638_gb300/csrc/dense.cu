@@ -10,8 +10,9 @@
 // TMEM lane quadrant, each taking a quarter of the columns).  Every wait on an mbarrier is bounded: on
 // timeout the kernel records an error and all roles leave their loops.
 //
-// Near ties: the BF16 scores carry a rigorous rounding-error bound
-//   B = (4 u_b + 2 d u) |x| max|c| + 2 u max|c|^2     (u_b = 2^-9, u = 2^-24);
+// Near ties: the BF16 scores carry a rigorous rounding-error bound (derived where the kernel
+// arguments are built)
+//   B ~= (4 u_b + 4 d u) |x| max|c| + 4 u max|c|^2     (u_b = 2^-9, u = 2^-24);
 // the epilogue keeps per row the two best (value, lowest index) and the third-best value.  If the
 // top-2 gap is within 2B but the third value is clear, only the two best can be the argmin and
 // they are compared in FP32 (direct form); otherwise the row is rescored over all K in FP32.

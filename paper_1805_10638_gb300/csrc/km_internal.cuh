@@ -23,6 +23,8 @@ constexpr int CH = 8;               // centroids per argmin chunk in the low-d F
 constexpr int LOWD_THREADS = 256;   // threads per block of the low-d pass kernel
 constexpr int FIN_THREADS = 256;    // threads per block of the update/finalize kernel
 constexpr int DOTS = 2 * MMAX;      // per-block dot partials: Gram row + right-hand side
+constexpr int LOWD_SMEM_MAX = 227 * 1024;   // opt-in dynamic shared memory per block on sm_103a
+constexpr int SM_SMEM = 228 * 1024;         // shared memory per SM
 
 // Pass kinds of the assignment kernel.
 enum PassMode : int {
@@ -284,6 +286,7 @@ size_t devinfo_bytes();
 // Batched launchers (persistent grids over work items).
 cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s);
 int pass_lowd_batch_occupancy(int prec, int d, size_t smem);
+int pass_lowd_occupancy(int prec, int d, size_t smem);   // resident blocks per SM (CUDA occupancy API)
 cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s);
 size_t fin_smem(int KB, int d);
 cudaError_t launch_mix_batch(const BatchMix& b, int grid, cudaStream_t s);

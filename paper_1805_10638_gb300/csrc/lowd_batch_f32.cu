@@ -1,0 +1,32 @@
+// Batched (persistent, work-item) low-d pass kernels, float instantiations (one kernel per d).
+#include "lowd_pass.cuh"
+#include "lowd_inst.cuh"
+
+namespace km {
+
+#define KM_LAUNCH(DD) \
+    case DD:          \
+        return launch_batch_one<float, DD>(b, grid, smem, s);
+#define KM_OCC(DD) \
+    case DD:       \
+        return batch_occ<float, DD>(smem);
+
+cudaError_t lowd_batch_launch_f32(const BatchPass& b, int d, int grid, size_t smem, cudaStream_t s)
+{
+    switch (d) {
+        KM_FOR_EACH_D(KM_LAUNCH)
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+int lowd_batch_occupancy_f32(int d, size_t smem)
+{
+    switch (d) {
+        KM_FOR_EACH_D(KM_OCC)
+        default:
+            return 1;
+    }
+}
+
+}  // namespace km

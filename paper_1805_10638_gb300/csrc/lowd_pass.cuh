@@ -1,0 +1,701 @@
+// Templates of the low-d assignment pass (see lowd_pass.cu for what one pass computes).  Each
+// instantiation unit (lowd_inst.cuh) includes this header for one precision and one of the
+// standalone / batched kernels, so that the four sets compile in parallel.
+#pragma once
+
+#include "controller.cuh"
+#include "km_internal.cuh"
+
+#include <type_traits>
+
+namespace km {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int W = LOWD_THREADS / 32;
+
+__device__ __forceinline__ float fmin3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <int D>
+struct Shape {
+    static constexpr int DP = ((2 * (D + 1) + 3) / 4 * 4) / 2;   // packed floats per centroid
+    static constexpr int R = (D <= 8) ? 4 : 2;             // samples per thread in the scan
+};
+
+// Resident blocks per SM the compiler must allow (register budget): the FP32 scan with few
+// dimensions is latency-bound at 2 blocks per SM (16 warps), so it is compiled for more.
+#ifndef KM_LOWD_MINB_SMALL
+#define KM_LOWD_MINB_SMALL 4
+#endif
+template <typename T, int D>
+struct MinBlocks {
+    static constexpr int value = (std::is_same<T, float>::value && D <= 8) ? KM_LOWD_MINB_SMALL : 1;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct Layout {
+    size_t red, org, cpk, rec, c, stage, bS, bC, total;
+};
+
+// Skewed copy of the packed centroids for the per-row recovery reads: chunk b (8 centroids of
+// D+1 floats) starts at b * RS floats, RS = 8(D+1)+1 is odd, so lanes recovering different chunks
+// read different banks (the unskewed layout puts every chunk's element (q,k) in the same bank).
+template <int D>
+__host__ __device__ constexpr int rec_stride() { return 8 * (D + 1) + 1; }
+
+__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins)
+{
+    const size_t esz = f32 ? 4 : 8;
+    Layout L;
+    size_t o = 0;
+    L.red = o;   o += 64 * sizeof(double);
+    L.org = o;   o += 64 * sizeof(float);
+    if (f32) {
+        L.cpk = o; o += al16((size_t)Kpad * DP * 4);
+        L.rec = o; o += al16((size_t)(Kpad / 8) * (8 * (D + 1) + 1) * 4);
+        L.c = o;   o += al16((size_t)K * D * 4);
+    } else {
+        L.cpk = 0;
+        L.rec = 0;
+        L.c = o;   o += al16((size_t)K * D * 8);
+    }
+    L.stage = o; o += al16((size_t)W * 32 * D * esz);
+    if (bins) {
+        L.bS = o; o += al16((size_t)W * K * D * esz);
+        L.bC = o; o += al16((size_t)W * K * 4);
+    } else {
+        L.bS = L.bC = 0;
+    }
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Block-wide fixed-order sums (result valid in thread 0).
+__device__ double block_sum_d(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+__device__ long long block_sum_ll(long long v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long* r = reinterpret_cast<long long*>(red);
+    v = warp_sum_ll(v);
+    __syncthreads();
+    if (lane == 0) r[warp] = v;
+    __syncthreads();
+    long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += r[w];
+    __syncthreads();
+    return s;
+}
+
+// Scan all centroids for R samples: per chunk of 8 centroids (4 interleaved pairs), each
+// fma.rn.f32x2 scores one sample against two centroids; xd holds each sample coordinate twice.
+template <int D, int R>
+__device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int Kpad,
+                                            const float2 (&xd)[R][D], float (&best)[R],
+                                            float (&sec)[R], int (&bc)[R])
+{
+    constexpr int PP = 2 * Shape<D>::DP;        // floats per centroid pair
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        best[r] = __int_as_float(0x7f800000);
+        sec[r] = __int_as_float(0x7f800000);
+        bc[r] = 0;
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < Kpad; c0 += CH) {
+        float2 s[R][CH / 2];
+#pragma unroll
+        for (int p = 0; p < CH / 2; ++p) {
+            float cv[PP];
+            const float4* p4 = reinterpret_cast<const float4*>(s_cpk + (size_t)((c0 >> 1) + p) * PP);
+#pragma unroll
+            for (int v = 0; v < PP / 4; ++v) {
+                const float4 t = p4[v];
+                cv[4 * v] = t.x;
+                cv[4 * v + 1] = t.y;
+                cv[4 * v + 2] = t.z;
+                cv[4 * v + 3] = t.w;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 acc = make_float2(cv[2 * D], cv[2 * D + 1]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc = __ffma2_rn(make_float2(cv[2 * k], cv[2 * k + 1]), xd[r][k], acc);
+                s[r][p] = acc;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float m = fmin3f(fmin3f(s[r][0].x, s[r][0].y, s[r][1].x), fmin3f(s[r][1].y, s[r][2].x, s[r][2].y),
+                                   fminf(s[r][3].x, s[r][3].y));
+            sec[r] = fminf(sec[r], fmaxf(best[r], m));
+            const bool p = m < best[r];
+            best[r] = p ? m : best[r];
+            bc[r] = p ? c0 : bc[r];
+        }
+    }
+}
+
+// Re-score the best chunk with the same arithmetic; lowest index attaining `best` and the
+// smallest other value in the chunk.
+template <int D>
+__device__ __forceinline__ int recover(const float* __restrict__ s_rec, const float (&x)[D], float best,
+                                       int bc, float& second_in)
+{
+    constexpr int RS = rec_stride<D>();
+    const float* base = s_rec + (size_t)(bc >> 3) * RS;
+    int jj = -1;
+    float sv = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+        const float* cp = base + q * (D + 1);
+        float acc = cp[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc = fmaf(cp[k], x[k], acc);
+        if (acc == best && jj < 0)
+            jj = q;
+        else
+            sv = fminf(sv, acc);
+    }
+    second_in = sv;
+    if (jj < 0) {                 // cannot happen with identical arithmetic; force a rescore
+        second_in = -__int_as_float(0x7f800000);
+        return bc;
+    }
+    return bc + jj;
+}
+
+// Warp-cooperative FP32 direct-form rescoring of the rows some lanes flagged: for each flagged
+// row in turn, the 32 lanes split the K centroids (ascending j per lane, strict '<'), then a
+// lexicographic (distance, index) butterfly gives the lowest index attaining the minimum.
+template <int D>
+__device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int K, const float* __restrict__ X,
+                                            int64_t my_row, bool need, int idx, int lane, long long& resc)
+{
+    unsigned bal = __ballot_sync(FULL, need);
+    while (bal) {
+        const int l = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const int64_t row = __shfl_sync(FULL, my_row, l);
+        float xo[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xo[k] = X[row * D + k];
+        float bd = __int_as_float(0x7f800000);
+        int bj = K;
+        for (int j = lane; j < K; j += 32) {
+            const float* c = s_c32 + (size_t)j * D;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = xo[k] - c[k];
+                acc = fmaf(t, t, acc);
+            }
+            if (acc < bd) {
+                bd = acc;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, bd, o);
+            const int oj = __shfl_xor_sync(FULL, bj, o);
+            if (ob < bd || (ob == bd && oj < bj)) {
+                bd = ob;
+                bj = oj;
+            }
+        }
+        if (lane == l) {
+            idx = bj;
+            resc += 1;
+        }
+    }
+    return idx;
+}
+
+// The work of block `bid` of a pass launched with `nblk` blocks.  The standalone kernel calls it
+// with (blockIdx.x, gridDim.x); the batched kernel with a work item's (block, blocks of that
+// instance), so that every instance gets exactly the arithmetic of its own launch.
+template <typename T, int D>
+__device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, const int nblk, unsigned char* smem)
+{
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int DP = Shape<D>::DP;
+    constexpr int R = F32 ? Shape<D>::R : 1;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    SolveState* st = a.st;
+    int which = 0;
+    int32_t* rho_out = a.rho[0];
+    const int32_t* rho_prev = a.rho_prev;
+    const int32_t* rho_in = a.rho_in;
+    if (a.mode == MODE_EPI) {
+        // energy of (P^t, G^t) when the loop stopped at max_iter
+        if (st->converged || st->status != KM_OK) return;
+        which = 1;
+        rho_in = a.rho[st->cur];
+    } else if (a.mode != MODE_STANDALONE) {
+        if (st->done) return;
+        if (a.mode == MODE_REVERT) {
+            if (!st->revert) return;
+            which = 1;
+        }
+        const int cur = st->cur;
+        rho_out = a.rho[cur];
+        rho_prev = (a.mode == MODE_INIT) ? nullptr : a.rho[cur ^ 1];
+    }
+    const int flags = a.flags;
+    const bool do_assign = flags & F_ASSIGN;
+    const bool do_bins = flags & F_BINS;
+    const int K = a.K;
+    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins);
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    T* s_stage = reinterpret_cast<T*>(smem + L.stage);
+    T* s_bS = reinterpret_cast<T*>(smem + L.bS);
+    int* s_bC = reinterpret_cast<int*>(smem + L.bC);
+    const float* s_cpk = reinterpret_cast<const float*>(smem + L.cpk);
+    const T* s_c = reinterpret_cast<const T*>(smem + L.c);
+
+    // ---- stage centroids and clear bins
+    const float* s_rec = reinterpret_cast<const float*>(smem + L.rec);
+    float* s_org = reinterpret_cast<float*>(smem + L.org);
+    if constexpr (F32) {
+        float* dst = reinterpret_cast<float*>(smem + L.cpk);
+        float* dc = reinterpret_cast<float*>(smem + L.c);
+        if (flags & F_PACK) {
+            // standalone call: o = mean of the given centroids (FP64, fixed order), then pack
+            const float* Cr = a.rawC;
+            for (int k = 0; k < D; ++k) {
+                double v = 0.0;
+                for (int j = tid; j < K; j += blockDim.x) v += (double)Cr[(size_t)j * D + k];
+                v = block_sum_d(v, s_red);
+                if (tid == 0) s_org[k] = (float)(v / K);
+            }
+            __syncthreads();
+            for (int j = tid; j < a.Kpad; j += blockDim.x) {
+#pragma unroll
+                for (int k = 0; k < DP; ++k) dst[pk_index(j, k, DP)] = 0.f;
+                if (j < K) {
+                    double nrm = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float c = Cr[(size_t)j * D + k];
+                        dc[(size_t)j * D + k] = c;
+                        const float cc = (float)((double)c - (double)s_org[k]);
+                        dst[pk_index(j, k, DP)] = -2.f * cc;
+                        nrm += (double)cc * (double)cc;
+                    }
+                    dst[pk_index(j, D, DP)] = (float)nrm;
+                } else {
+                    dst[pk_index(j, D, DP)] = __int_as_float(0x7f800000);
+                }
+            }
+        } else {
+            const float4* src = reinterpret_cast<const float4*>(a.cpk[which]);
+            float4* dst4 = reinterpret_cast<float4*>(dst);
+            for (int i = tid; i < a.Kpad * DP / 4; i += blockDim.x) dst4[i] = src[i];
+            if (a.mode == MODE_EPI) {          // G^t was not packed: round it here
+                const double* g64 = a.c64[1];
+                for (int i = tid; i < K * D; i += blockDim.x) dc[i] = (float)g64[i];
+            } else {
+                const float* c32 = a.c32[which];
+                for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c32[i];
+            }
+            if (tid < D) s_org[tid] = a.origin[tid];
+        }
+    } else {
+        const double* c64 = a.c64[which];
+        double* dc = reinterpret_cast<double*>(smem + L.c);
+        for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c64[i];
+    }
+    if (do_bins) {
+        for (int i = tid; i < W * K * D; i += blockDim.x) s_bS[i] = T(0);
+        for (int i = tid; i < W * K; i += blockDim.x) s_bC[i] = 0;
+    }
+    __syncthreads();
+
+    // ---- skewed recovery copy and the rounding-error bound's max|c'| (FP32 path)
+    float cmax = 0.f;
+    float o[D];
+    if constexpr (F32) {
+        constexpr int RS = rec_stride<D>();
+        float* sr = reinterpret_cast<float*>(smem + L.rec);
+        for (int i = tid; i < a.Kpad * (D + 1); i += blockDim.x) {
+            const int j = i / (D + 1), k = i % (D + 1);
+            sr[(size_t)(j >> 3) * RS + (j & 7) * (D + 1) + k] = s_cpk[pk_index(j, k, DP)];
+        }
+        float mx = 0.f;
+        for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, s_cpk[pk_index(j, D, DP)]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+        float* fr = reinterpret_cast<float*>(s_red);
+        if (lane == 0) fr[warp] = mx;
+        __syncthreads();
+        mx = 0.f;
+        for (int w = 0; w < W; ++w) mx = fmaxf(mx, fr[w]);
+        cmax = sqrtf(mx);
+#pragma unroll
+        for (int k = 0; k < D; ++k) o[k] = s_org[k];
+        __syncthreads();
+    }
+
+    const T* X = reinterpret_cast<const T*>(a.X);
+    const int64_t N = a.N;
+    const int64_t TT = (int64_t)nblk * blockDim.x;
+    const int64_t g = (int64_t)bid * blockDim.x + tid;
+    const int64_t n_g = g < N ? (N - 1 - g) / TT + 1 : 0;
+    const int64_t n_min = __shfl_sync(FULL, n_g, 31);
+    const int64_t n_max = __shfl_sync(FULL, n_g, 0);
+
+    T eacc = T(0);
+    long long nch = 0, resc = 0;
+    int bad = 0;
+
+    // Everything after the label is known, for one sample (warp-uniform call).
+    auto finish = [&](int64_t row, bool valid, int idx) {
+        idx = idx < K ? idx : K - 1;           // only reachable with non-finite data
+        T res[D];
+        T e = T(0);
+        if (valid) {
+            const T* xr = X + row * D;
+            const T* c = s_c + (size_t)idx * D;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if constexpr (F32) {
+                    res[k] = xr[k] - c[k];
+                    e = fmaf(res[k], res[k], e);
+                } else {
+                    res[k] = __dsub_rn(xr[k], c[k]);
+                    e = __dadd_rn(e, __dmul_rn(res[k], res[k]));
+                }
+            }
+            if (do_assign) rho_out[row] = idx;
+            if ((flags & F_CHANGED) && rho_prev) nch += (rho_prev[row] != idx);
+            if (flags & F_DMIN) reinterpret_cast<T*>(a.dmin)[row] = e;
+            eacc += e;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) res[k] = T(0);
+        }
+        if (do_bins) {
+            const int lab = valid ? idx : -1;
+            const unsigned mm = __match_any_sync(FULL, lab);
+            T* stg = s_stage + (size_t)warp * 32 * D;
+#pragma unroll
+            for (int k = 0; k < D; ++k) stg[lane * D + k] = res[k];
+            __syncwarp();
+            if (valid && lane == __ffs(mm) - 1) {
+                T acc[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc[k] = T(0);
+                unsigned m2 = mm;
+                while (m2) {
+                    const int l = __ffs(m2) - 1;
+                    m2 &= m2 - 1;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc[k] += stg[l * D + k];
+                }
+                T* bin = s_bS + ((size_t)warp * K + lab) * D;
+#pragma unroll
+                for (int k = 0; k < D; ++k) bin[k] += acc[k];
+                s_bC[warp * K + lab] += __popc(mm);
+            }
+            __syncwarp();
+        }
+    };
+
+    auto check = [&](const T* xr) {
+        if (flags & F_CHECK) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) bad |= !isfinite(xr[k]);
+        }
+    };
+
+    int64_t kk = 0;
+    if (do_assign) {
+        if constexpr (F32) {
+            const float cA = a.bound_coef, cB = a.bound_coef2;
+            const int64_t main_iters = n_min / R;
+            for (int64_t it = 0; it < main_iters; ++it, kk += R) {
+                float x[R][D];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float* xr = X + (g + (kk + r) * TT) * D;
+                    check(xr);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) x[r][k] = xr[k] - o[k];
+                }
+                float2 xd[R][D];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xd[r][k] = make_float2(x[r][k], x[r][k]);
+                float best[R], sec[R];
+                int bc[R];
+                scan_chunks<D, R>(s_cpk, a.Kpad, xd, best, sec, bc);
+                int idxr[R];
+                bool need[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float xn = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xn = fmaf(x[r][k], x[r][k], xn);
+                    float sin_;
+                    idxr[r] = recover<D>(s_rec, x[r], best[r], bc[r], sin_);
+                    const float second = fminf(sec[r], sin_);
+                    const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                    need[r] = second - best[r] <= 2.f * bnd;
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    idxr[r] = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, g + (kk + r) * TT, need[r],
+                                              idxr[r], lane, resc);
+#pragma unroll
+                for (int r = 0; r < R; ++r) finish(g + (kk + r) * TT, true, idxr[r]);
+            }
+            for (; kk < n_max; ++kk) {
+                const bool valid = kk < n_g;
+                const int64_t row = valid ? g + kk * TT : 0;
+                float x[1][D];
+                const float* xr = X + row * D;
+                if (valid) check(xr);
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[0][k] = xr[k] - o[k];
+                float2 xd[1][D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) xd[0][k] = make_float2(x[0][k], x[0][k]);
+                float best[1], sec[1];
+                int bc[1];
+                scan_chunks<D, 1>(s_cpk, a.Kpad, xd, best, sec, bc);
+                float xn = 0.f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) xn = fmaf(x[0][k], x[0][k], xn);
+                float sin_;
+                int idx = recover<D>(s_rec, x[0], best[0], bc[0], sin_);
+                const float second = fminf(sec[0], sin_);
+                const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                const bool need = valid && second - best[0] <= 2.f * bnd;
+                idx = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, row, need, idx, lane, resc);
+                finish(row, valid, idx);
+            }
+        } else {
+            for (; kk < n_max; ++kk) {
+                const bool valid = kk < n_g;
+                const int64_t row = valid ? g + kk * TT : 0;
+                const double* xr = X + row * D;
+                if (valid) check(xr);
+                double x[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[k] = xr[k];
+                double bd = __longlong_as_double(0x7ff0000000000000LL);
+                int bj = 0;
+                for (int j = 0; j < K; ++j) {
+                    const double* c = s_c + (size_t)j * D;
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const double t = __dsub_rn(x[k], c[k]);
+                        s = __dadd_rn(s, __dmul_rn(t, t));
+                    }
+                    if (s < bd) {
+                        bd = s;
+                        bj = j;
+                    }
+                }
+                finish(row, valid, bj);
+            }
+        }
+    } else {
+        // labels given: energy / update from rho_in
+        for (; kk < n_max; ++kk) {
+            const bool valid = kk < n_g;
+            const int64_t row = valid ? g + kk * TT : 0;
+            int idx = valid ? rho_in[row] : 0;
+            idx = (idx >= 0 && idx < K) ? idx : 0;
+            finish(row, valid, idx);
+        }
+    }
+
+    // ---- block partials
+    const double eb = block_sum_d((double)eacc, s_red);
+    const long long nb_ch = block_sum_ll(nch, s_red);
+    const long long nb_rs = block_sum_ll(resc, s_red);
+    const long long nb_bad = block_sum_ll(bad, s_red);
+    if (tid == 0) {
+        a.pE[bid] = eb;
+        a.pNch[bid] = nb_ch;
+        a.pResc[bid] = nb_rs;
+        a.pBad[bid] = (int)(nb_bad != 0);
+    }
+    if (do_bins) {
+        __syncthreads();
+        T* pS = reinterpret_cast<T*>(a.pS) + (size_t)bid * K * D;
+        for (int e = tid; e < K * D; e += blockDim.x) {
+            T s = T(0);
+            for (int w = 0; w < W; ++w) s += s_bS[(size_t)w * K * D + e];
+            pS[e] = s;
+        }
+        int32_t* pC = a.pCnt + (size_t)bid * K;
+        for (int j = tid; j < K; j += blockDim.x) {
+            int s = 0;
+            for (int w = 0; w < W; ++w) s += s_bC[w * K + j];
+            pC[j] = s;
+        }
+    }
+
+    // ---- last block: fixed-order reduction over blocks and the controller
+    __threadfence();
+    __syncthreads();
+    unsigned int* sflag = reinterpret_cast<unsigned int*>(s_red + 40);
+    if (tid == 0) {
+        const unsigned int prev = atomicAdd(a.counter, 1u);
+        *sflag = (prev == (unsigned)nblk - 1u) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (*sflag == 0u) return;
+    __threadfence();
+    double E = 0.0;
+    long long ch = 0, rs = 0, bd = 0;
+    for (int b = tid; b < nblk; b += blockDim.x) {
+        E += __ldcg(a.pE + b);
+        ch += __ldcg(a.pNch + b);
+        rs += __ldcg(a.pResc + b);
+        bd += __ldcg(a.pBad + b);
+    }
+    E = block_sum_d(E, s_red);
+    ch = block_sum_ll(ch, s_red);
+    rs = block_sum_ll(rs, s_red);
+    bd = block_sum_ll(bd, s_red);
+    if (tid == 0) {
+        *a.counter = 0u;
+        if (a.mode == MODE_STANDALONE) {
+            if (a.out_nch) *a.out_nch = ch;
+            if (a.out_E) *a.out_E = E;
+        } else {
+            st->rescored += rs;
+            if (a.mode == MODE_EPI) {
+                st->E_final = E;
+            } else if (a.mode == MODE_INIT) {
+                st->passes += 1;
+                st->E_trial = E;
+                if (bd) st->status = KM_ENONFINITE;       // the first loop pass stops the solve
+            } else {
+                if (a.mode == MODE_TRIAL)
+                    controller_trial(st, E, ch, a.thr, a.lloyd_only, a.eps1, a.eps2, a.m_max, a.max_iter);
+                else
+                    controller_revert(st, E, ch, a.thr);
+                // the kernel that ends the solve also ends the graph's while loop
+                if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+            }
+        }
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_lowd(PassArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    pass_body<T, D>(a, blockIdx.x, gridDim.x, smem);
+}
+
+// Persistent batched pass: each block takes work items (instance, block of that instance) in
+// turn; an item does what that block of the instance's own launch would do (same rows, same
+// partial slot, the instance's last item runs its reduction and controller).  No item waits for
+// another, so any grid size is safe.
+template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_lowd_batch(BatchPass b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const int2 w = b.items[it];
+        PassArgs a = b.args[w.x];
+        a.mode = b.mode;
+        a.flags = b.flags;
+        a.use_cond = 0;
+        pass_body<T, D>(a, w.y, a.nblk, smem);
+        __syncthreads();
+    }
+}
+
+template <typename T, int D>
+cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
+{
+    auto kern = k_pass_lowd<T, D>;
+    static bool attr_set = false;
+    if (!attr_set || smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<nb, LOWD_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t launch_batch_one(const BatchPass& b, int grid, size_t smem, cudaStream_t s)
+{
+    auto kern = k_pass_lowd_batch<T, D>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<grid, LOWD_THREADS, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+int pass_occ(size_t smem)
+{
+    int n = 0;
+    auto kern = k_pass_lowd<T, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+template <typename T, int D>
+int batch_occ(size_t smem)
+{
+    int n = 0;
+    auto kern = k_pass_lowd_batch<T, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+}  // namespace km

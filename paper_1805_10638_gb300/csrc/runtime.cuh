@@ -110,13 +110,18 @@ kmeans_status check_data(kmeans_ctx* ctx, const kmeans_data* X, int K, bool need
     return KM_OK;
 }
 
-int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem)
+// Blocks of a low-d pass: as many as are resident at once (the kernel's occupancy for this shared
+// memory size, at most 4 per SM), and at least 1024 rows per block on the FP32 path (256 on the
+// FP64 path) so that the per-block staging and partial sums stay small against the scan.  The
+// count fixes the order of the update's sums; batched solves reuse it per instance.
+int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem, int prec, int d)
 {
-    int per_sm = (int)((200 * 1024) / (smem + 2048));
-    if (per_sm > 2) per_sm = 2;           // register-limited: 256 threads x ~128 registers
+    int per_sm = pass_lowd_occupancy(prec, d, smem);
+    if (per_sm > 4) per_sm = 4;
     if (per_sm < 1) per_sm = 1;
     int64_t nb = (int64_t)ctx->nsm * per_sm;
-    const int64_t need = (N + LOWD_THREADS - 1) / LOWD_THREADS;
+    const int64_t rows = prec == KM_F64 ? LOWD_THREADS : 4 * LOWD_THREADS;
+    const int64_t need = (N + rows - 1) / rows;
     if (nb > need) nb = need;
     if (nb < 1) nb = 1;
     return (int)nb;
@@ -207,9 +212,9 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.DP = pass_lowd_dp(d);
     P.Kpad = (K + CH - 1) / CH * CH;
     P.smem = pass_lowd_smem(prec, d, K, P.Kpad, bins);
-    if (P.smem > 200 * 1024)
+    if (P.smem > (size_t)LOWD_SMEM_MAX)
         return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
-    P.nb = pass_blocks(ctx, N, P.smem);
+    P.nb = pass_blocks(ctx, N, P.smem, prec, d);
     P.nfin = fin_blocks(K, d, &P.KB);
     const size_t n = (size_t)K * d;
     const int mm = m_max > 0 ? m_max : 1;
@@ -384,11 +389,19 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.c32[1] = at<float>(base, P.c32_1);
     a.c64[0] = at<double>(base, P.C64);
     a.c64[1] = at<double>(base, P.CAU);
-    // BF16 score error bound: 2 (2 u_b + d u) |x| max|c| for 2 x.c, u max|c|^2 for ||c||^2, with a
-    // factor 2 of allowance for the accumulation order inside the MMA
+    // Rigorous bound on |s - s*| for the score s = fl(||c||^2 - 2 v), v = the MMA's x^.c^ (BF16
+    // operands x^ = bf16(x), c^ = bf16(c): relative error <= u_b = 2^-9 each; their products are
+    // exact in FP32), s* = ||c||^2 - 2 x.c (c, x the FP32 values the rescoring uses):
+    //   2 |x^.c^ - x.c|  <= 2 (2 u_b + u_b^2) |x||c|              (quantisation of the operands)
+    //   2 |v - x^.c^|    <= 2 (2 d u) |x^||c^|                    (FP32 accumulation, allowing 2u
+    //                                                              per addition: truncating adders)
+    //   fl of the fma    <= u (||c||^2 + 2 |x||c|),  ||c||^2 rounded from FP64: u ||c||^2
+    // with |x| <= |x^| (1 + 2 u_b), |c^| <= |c| (1 + u_b).  The epilogue takes |x^| from the BF16
+    // row and max|c| over the centroids.
     const double ub = 1.0 / 512.0, u = 5.9604644775390625e-8;
-    a.bcoef_a = (float)(2.0 * (2.0 * (2.0 * ub + d * u)) * (1.0 + 2.0 * ub));
-    a.bcoef_b = (float)(2.0 * 2.0 * u);
+    a.bcoef_a = (float)((2.0 * (2.0 * ub + ub * ub) + 4.0 * d * u * (1.0 + ub) * (1.0 + ub) + 2.0 * u) *
+                        (1.0 + 2.0 * ub));
+    a.bcoef_b = (float)(4.0 * u);
     a.rho_pair[0] = at<int32_t>(base, P.rhoA);
     a.rho_pair[1] = at<int32_t>(base, P.rhoB);
     a.queue = at<int>(base, P.queue);

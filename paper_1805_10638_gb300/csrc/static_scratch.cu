@@ -61,7 +61,7 @@ extern "C" kmeans_status kmeans_update_static(const kmeans_data* X, const int32_
     const size_t esz = prec == KM_F64 ? 8 : 4;
     const int Kpad = (K + CH - 1) / CH * CH;
     const size_t smem = pass_lowd_smem(prec, d, K, Kpad, true);
-    if (smem > 200 * 1024) return KM_EINVAL;   // K*d too large for the per-warp shared-memory bins
+    if (smem > (size_t)LOWD_SMEM_MAX) return KM_EINVAL;   // K*d too large for the per-warp shared-memory bins
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return KM_ECUDA;

@@ -48,6 +48,17 @@ def _env_int(k, d):
         return d
 
 
+def profiled_traffic(name: str):
+    """DRAM bytes per launch (read + write) of the dominant kernel from its committed ncu summary."""
+    try:
+        for ln in open(os.path.join(ROOT, "profiles", name)):
+            if ln.startswith("| traffic per launch"):
+                return int(ln.split("|")[2].split()[0])
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
+
+
 def max_over_ranks(values, dist, device):
     """Element-wise maximum of per-rank timings (the slowest replica sets the job time); `dist`
     is torch.distributed or None for a single process."""
@@ -569,7 +580,6 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "TFLOP/s",
                 "note": "2*N*K*d BF16 MMA flops per assignment call over its CUDA-event time; peak = "
                         "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"}
-        tkey = "k_dense_assign"
     else:
         # ALU work of a brute-force assignment pass: per (sample, centroid) pair d FMAs of the
         # score plus about two argmin operations (compare, select), one lane operation each
@@ -582,14 +592,7 @@ def run_ours(args, rank, world, local_rank):
                 "note": "N*K*(d+2) lane operations per pass (d FMAs + ~2 argmin ops per sample-centroid "
                         "pair) over the launch's CUDA-event time; peak = 152 SMs x 128 FP32 lanes x 2070 MHz "
                         "(derived from unit counts and the maximum clock, not measured)"}
-        tkey = "k_pass_lowd<float,3>"
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get(tkey)
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic("k_pass_lowd_lowd_2m.md" if not dense else "k_dense_assign_dense_1m.md")
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": traffic,
                  "assign_ms": assign_ms})
 

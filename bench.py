@@ -238,25 +238,21 @@ def batched_data(n_inst: int, seed: int = 0):
     return out
 
 
-def lane_ops(N, K, d):
-    """ALU work of one brute-force low-d assignment pass (d FMAs + ~2 argmin ops per pair)."""
-    return float(N) * K * (d + 2)
-
-
 def parse_tuning(desc: str):
-    """Per low-d group of kmeans_batch_describe: (d, chosen grid, its time in us)."""
+    """Per low-d group of kmeans_batch_describe: (d, lane ops of one pass, chosen grid, its time in us)."""
     out = []
     for part in desc.split(";"):
         part = part.strip()
         if " d=" not in part or "-> grid" not in part:
             continue
         d = int(part.split(" d=")[1].split()[0])
+        ops = float(part.split(" ops=")[1].split()[0])
         grid = int(part.split("-> grid")[1].split()[0])
         t = None
         for tok in part.split():
             if tok.startswith(f"{grid}:") and tok.endswith("us"):
                 t = float(tok[len(str(grid)) + 1:-2])
-        out.append((part.split()[0], d, grid, t))
+        out.append((d, ops, grid, t))
     return out
 
 
@@ -315,10 +311,10 @@ def run_batched(args, rank, world, local_rank):
     # roofline of the batched low-d assignment pass: the tuner's timing of the chosen grid per group
     groups = parse_tuning(desc)
     work, t_us = 0.0, 0.0
-    for prec, d, grid, t in groups:
+    for d, ops, grid, t in groups:
         if t is None:
             continue
-        work += sum(lane_ops(X.shape[0], K, X.shape[1]) for X, _, K, _ in data if X.shape[1] == d)
+        work += ops
         t_us += t
     peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2070.0 * 1e6 / 1e12
     achieved = work / (t_us * 1e-6) / 1e12 if t_us else None
@@ -429,9 +425,9 @@ def run_serving(args, rank, world, local_rank):
     budget = int(args.serve_budget_gb * (1 << 30))
 
     def run(lloyd: bool):
-        srv = km.Server(local_rank, hbm_budget=budget, max_slots=512, max_large=4)
+        srv = km.Server(local_rank, hbm_budget=budget, max_slots=512, max_large=args.serve_lanes)
         prm = dict(lloyd_only=1) if lloyd else dict(m_max=10)
-        lat, nxt, inflight, iters, rejected = [], 0, {}, [], []
+        lat, nxt, inflight, iters, rejected, kind = [], 0, {}, [], [], []
         t0 = time.perf_counter()
         while nxt < len(reqs) or inflight:
             now = time.perf_counter() - t0
@@ -448,18 +444,24 @@ def run_serving(args, rank, world, local_rank):
                 if res is not None:
                     i, ta = inflight.pop(t)
                     lat.append((time.perf_counter() - t0) - ta)
+                    kind.append("large" if reqs[i]["large"] else ("tensor" if reqs[i]["d"] > 16 else "lowd"))
                     iters.append(res[2]["iters"])
             if not inflight and nxt < len(reqs):
                 time.sleep(max(0.0, min(0.001, reqs[nxt]["t_arrival"] - (time.perf_counter() - t0))))
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        return lat, wall, st, iters, rejected
+        by = {k: [l for l, c in zip(lat, kind) if c == k] for k in ("lowd", "tensor", "large")}
+        return lat, wall, st, iters, rejected, by
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    lat_aa, wall_aa, st_aa, it_aa, rej_aa = run(False)
-    lat_ll, wall_ll, st_ll, it_ll, rej_ll = run(True)
+    lat_aa, wall_aa, st_aa, it_aa, rej_aa, by_aa = run(False)
+    lat_ll, wall_ll, st_ll, it_ll, rej_ll, by_ll = run(True)
+
+    def classes(by):
+        return {k: {"n": len(v), "p50_ms": 1e3 * pct(v, 50) if v else None, "p99_ms": 1e3 * pct(v, 99) if v else None}
+                for k, v in by.items()}
     clk = clocks.stop()
     n = len(reqs)
     line = {
@@ -469,13 +471,15 @@ def run_serving(args, rank, world, local_rank):
         "dtype": "f32 (bf16 distances for d > 16)", "data": "synthetic",
         "config": {"workload": "serving", "requests": n, "rate_per_s": args.serve_rate, "arrival_seed": 7,
                    "large_frac": 0.02, "large": "N=4e6, d=96, K=4096", "budget_gb": args.serve_budget_gb,
-                   "max_slots": 512, "max_large": 4, "parallelism": "replicas x1"},
+                   "max_slots": 512, "max_large": args.serve_lanes, "parallelism": "replicas x1",
+                   "classes": "lowd = d <= 16 (continuous batch), tensor = d = 64 and large = N=4e6 (lanes)"},
         "p50_ms": 1e3 * pct(lat_aa, 50), "p99_ms": 1e3 * pct(lat_aa, 99),
         "aa": {"solves_per_s": len(lat_aa) / wall_aa, "p50_ms": 1e3 * pct(lat_aa, 50), "p99_ms": 1e3 * pct(lat_aa, 99),
-               "iters_mean": float(np.mean(it_aa)), "steps": st_aa["steps"], "pool_peak_gb": st_aa["pool_peak"] / 2**30},
+               "iters_mean": float(np.mean(it_aa)), "steps": st_aa["steps"], "pool_peak_gb": st_aa["pool_peak"] / 2**30,
+               "by_class": classes(by_aa)},
         "lloyd": {"solves_per_s": len(lat_ll) / wall_ll, "p50_ms": 1e3 * pct(lat_ll, 50), "p99_ms": 1e3 * pct(lat_ll, 99),
                   "iters_mean": float(np.mean(it_ll)), "steps": st_ll["steps"],
-                  "pool_peak_gb": st_ll["pool_peak"] / 2**30},
+                  "pool_peak_gb": st_ll["pool_peak"] / 2**30, "by_class": classes(by_ll)},
         "latency": "arrival (wall clock) to results in host memory, including the host-to-device copy of X",
         "rejected": len(rej_aa), "rejected_examples": [r for _, r in rej_aa[:3]],
         "e2e": {"value": len(lat_aa) / wall_aa, "unit": "solves/s",
@@ -645,11 +649,15 @@ def run_ours(args, rank, world, local_rank):
                    "passes_mean": float(np.mean([i["assign_passes"] for i in inf_aa])),
                    "converged_frac": float(np.mean([i["converged"] for i in inf_aa])),
                    "rescored_rows_mean": float(np.mean([i["rescored_rows"] for i in inf_aa])),
+                   "scanned_frac": float(np.mean([i["scanned_rows"] / max(1, i["assign_passes"] * N)
+                                                  for i in inf_aa])),
                    "E_mean": float(E_aa.mean())},
             "lloyd": {"solves_per_s": world * args.steps / tot_ll, "p50_ms": pct(ms_ll, 50),
                       "p99_ms": pct(ms_ll, 99),
                       "iters_mean": float(np.mean([i["iters"] for i in inf_ll])),
                       "passes_mean": float(np.mean([i["assign_passes"] for i in inf_ll])),
+                      "scanned_frac": float(np.mean([i["scanned_rows"] / max(1, i["assign_passes"] * N)
+                                                     for i in inf_ll])),
                       "converged_frac": float(np.mean([i["converged"] for i in inf_ll])),
                       "E_mean": float(E_ll.mean())},
             "aa_over_lloyd_speed": tot_ll / tot_aa,
@@ -686,6 +694,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-lanes", type=int, default=4)
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=0)

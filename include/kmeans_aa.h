@@ -93,7 +93,9 @@ typedef struct {
  *                  were rescored in FP32, summed over all passes
  *   device_ms      device time of the solve measured with CUDA events (batched solves: of the
  *                  whole batch)
- *   status         kmeans_status of this solve (KM_OK, KM_ENONFINITE, KM_ETIMEOUT) */
+ *   status         kmeans_status of this solve (KM_OK, KM_ENONFINITE, KM_ETIMEOUT)
+ *   scanned_rows   rows whose assignment took a scan over all K centroids, summed over the passes
+ *                  (the rest were settled by Hamerly bounds; 0 on the tensor-core path) */
 typedef struct {
     int32_t iters;
     int32_t accepted;
@@ -106,6 +108,7 @@ typedef struct {
     double device_ms;
     int32_t status;
     int32_t reserved;
+    int64_t scanned_rows;
 } kmeans_info;
 
 typedef struct kmeans_ctx kmeans_ctx;

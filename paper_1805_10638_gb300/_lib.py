@@ -47,7 +47,8 @@ class kmeans_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
                 ("assign_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("m_final", ctypes.c_int32), ("E", ctypes.c_double), ("rescored_rows", ctypes.c_int64),
-                ("device_ms", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device_ms", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("scanned_rows", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

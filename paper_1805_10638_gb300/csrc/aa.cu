@@ -86,6 +86,76 @@ __device__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double
     return rank;
 }
 
+// The same solve with the Gram rows in registers (lane r holds row r, MB >= mt columns), so that
+// the rank-1 updates of a column are independent FMAs instead of a chain through shared memory.
+// Every FP64 operation and its order match ls_warp, so the results are bitwise the same.
+template <int MB>
+__device__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
+                           double* sV)
+{
+    const int lane = threadIdx.x & 31;
+    const int sr = lane < mt ? (hnew - lane + m_max) % m_max : 0;
+    double m[MB];
+#pragma unroll
+    for (int c = 0; c < MB; ++c) {
+        const int sc = (hnew - c + m_max) % m_max;
+        m[c] = (lane < mt && c < mt) ? st->gram[sr * MMAX + sc] : 0.0;
+    }
+    double v = lane < mt ? st->bvec[sr] : 0.0;
+    double inv[MB];
+    int rank = 0;
+    double l00 = 0.0;
+    bool go = true;
+#pragma unroll
+    for (int k = 0; k < MB; ++k) {
+        inv[k] = 0.0;
+        if (go && k < mt) {
+            const double piv = __shfl_sync(FULL, m[k], k);
+            const double r = piv > 0.0 ? rsqrt(piv) : 0.0;
+            const double lkk = piv * r;
+            if (k == 0) l00 = lkk;
+            if (l00 == 0.0 || !(lkk > rank_tol * l00)) {
+                go = false;
+            } else {
+                if (lane > k && lane < mt) m[k] *= r;
+                if (lane == k) m[k] = lkk;
+                inv[k] = r;
+#pragma unroll
+                for (int j = k + 1; j < MB; ++j) {
+                    const double ljk = __shfl_sync(FULL, m[k], j);
+                    if (lane >= j && lane < mt) m[j] -= m[k] * ljk;
+                }
+                rank = k + 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MB; ++k) {             // L y = b
+        if (k < rank) {
+            const double yk = __shfl_sync(FULL, v, k) * inv[k];
+            if (lane == k) v = yk;
+            if (lane > k && lane < rank) v -= m[k] * yk;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < MB; ++c) sM[lane * MMAX + c] = m[c];
+    __syncwarp();
+    double colL[MB];                           // colL[k] = L[k][lane]
+#pragma unroll
+    for (int k = 0; k < MB; ++k) colL[k] = k < 32 ? sM[k * MMAX + lane] : 0.0;
+#pragma unroll
+    for (int k = MB - 1; k >= 0; --k) {        // L^T theta = y
+        if (k < rank) {
+            const double tk = __shfl_sync(FULL, v, k) * inv[k];
+            if (lane == k) v = tk;
+            if (lane < k) v -= colL[k] * tk;
+        }
+    }
+    sV[lane] = lane < rank ? v : 0.0;
+    __syncwarp();
+    return rank;
+}
+
 // C^{t+1}_j = G^t_j - sum_q theta_q dG_q,j for one centroid (one warp, lanes over d), written to
 // C64, and the FP32 packing of C^{t+1} (set 0) and G^t (set 1).  Reads go through L2 (__ldcg):
 // G^t and dG were written by other blocks of the same kernel when called from k_fin.
@@ -342,7 +412,10 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
         __syncthreads();
         if (warp == 0) {
             const int mt = min(min(st->m, st->t), st->ring_count);
-            const int rank = mt > 0 ? ls_warp(st, hnew, m_max, mt, a.rank_tol, s_M, s_inv, s_th) : 0;
+            int rank = 0;
+            if (mt > 0)
+                rank = m_max <= 16 ? ls_warp_reg<16>(st, hnew, m_max, mt, a.rank_tol, s_M, s_th)
+                                   : ls_warp(st, hnew, m_max, mt, a.rank_tol, s_M, s_inv, s_th);
             if (mt == 0) s_th[lane] = 0.0;
             st->theta[lane] = s_th[lane];
             s_sl[lane] = (hnew - lane + m_max) % m_max;
@@ -390,6 +463,7 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
     // element per thread, FP64), then ||c'||^2 per centroid from the packed FP32 values.
     if (a.fuse_mix && !stop) {
         const int rk = init ? 0 : rank;
+#pragma unroll 4
         for (size_t i = tid; i < n; i += blockDim.x) {
             const int j = (int)(i / d), k = (int)(i % d);
             const double g = __ldcg(a.CAU + i);
@@ -572,6 +646,7 @@ struct DevInfo {
     int iters, accepted, rejected, passes, converged, m_final, status, pad;
     double E;
     long long rescored;
+    long long scanned;
 };
 
 template <typename T>
@@ -596,6 +671,7 @@ __device__ __forceinline__ void epi_body(const SolveState* st, const double* C64
         f.pad = 0;
         f.E = st->E_final;
         f.rescored = st->rescored;
+        f.scanned = st->scanned;
         *info = f;
     }
 }

@@ -37,6 +37,8 @@ struct BInst {
 struct BGroup {
     int prec;        // KM_F64 or KM_F32
     int d;
+    int cls;         // shared-memory class (smem_class)
+    double ops;      // sum of N*K*(d+2) over its instances (ALU work of one pass, for reports)
     size_t smem;
     std::vector<int2> items;
     size_t items_off;
@@ -53,6 +55,7 @@ struct BLayout {
 struct Batch {
     int n = 0;
     int n_lowd = 0;
+    bool any_ham = false;
     std::vector<Launch> dense;       // d > 16 instances: their own solve chains in the same graph
     std::vector<BInst> inst;
     std::vector<BGroup> groups;
@@ -83,6 +86,16 @@ BatchPass pass_launch(const Batch& B, const BGroup& g, int mode, int flags, bool
 
 cudaError_t batch_passes(const Batch& B, int mode, int flags, cudaStream_t s)
 {
+    if (B.any_ham && (mode == MODE_INIT || mode == MODE_TRIAL)) {   // REVERT: from the TRIAL pass
+        BatchPass h;
+        h.args = bat<PassArgs>(B, B.L.t_pass);
+        h.items = bat<int2>(B, B.L.t_prep_items);
+        h.nitems = B.n_lowd;
+        h.mode = mode;
+        h.flags = 0;
+        cudaError_t e = launch_hprep_batch(h, std::min(B.n_lowd, 1024), s);
+        if (e != cudaSuccess) return e;
+    }
     for (const BGroup& g : B.groups) {
         cudaError_t e = launch_pass_lowd_batch(pass_launch(B, g, mode, flags, false), g.prec, g.d, g.grid, g.smem, s);
         if (e != cudaSuccess) return e;
@@ -180,7 +193,8 @@ kmeans_status tune_batch(kmeans_ctx* ctx, Batch& B, std::string& desc)
         cand.push_back(nit);
         std::sort(cand.begin(), cand.end());
         cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        snprintf(buf, sizeof(buf), "%s d=%d items=%d occ=%d", g.prec == KM_F64 ? "f64" : "f32", g.d, nit, occ);
+        snprintf(buf, sizeof(buf), "%s d=%d cls=%d ops=%.6g items=%d occ=%d", g.prec == KM_F64 ? "f64" : "f32", g.d,
+                 g.cls, g.ops, nit, occ);
         desc += buf;
         if (tune && cand.size() > 1) {
             const BatchPass b = pass_launch(B, g, MODE_STANDALONE, F_ASSIGN | F_BINS | F_ENERGY, true);
@@ -217,6 +231,7 @@ std::string batch_key(const kmeans_problem* pr, int n, const std::vector<kmeans_
     k.append(reinterpret_cast<const char*>(ps.data()), sizeof(kmeans_params) * (size_t)n);
     k.append(reinterpret_cast<const char*>(&ctx->arena), sizeof(ctx->arena));
     k.append(reinterpret_cast<const char*>(&ctx->arena_bytes), sizeof(ctx->arena_bytes));
+    k.push_back(hamerly_mode() ? 'H' : 'h');
     return k;
 }
 
@@ -243,7 +258,8 @@ kmeans_status batch_solve(kmeans_ctx* ctx, const kmeans_problem* pr, int n, cons
         BInst& bi = B.inst[i];
         bi.dense = q.X.d > 16;
         const int prec = bi.dense ? KM_BF16_F32 : (q.X.prec == KM_F64 ? KM_F64 : KM_F32);
-        if ((s = make_plan(ctx, q.X.N, q.X.d, q.K, prec, ps[i].lloyd_only ? 0 : ps[i].m_max, false, bi.P)) != KM_OK)
+        if ((s = make_plan(ctx, q.X.N, q.X.d, q.K, prec, ps[i].lloyd_only ? 0 : ps[i].m_max, false, bi.P, true,
+                           true)) != KM_OK)
             return s;
         bi.off = o;
         o += al256(bi.P.total);
@@ -251,13 +267,17 @@ kmeans_status batch_solve(kmeans_ctx* ctx, const kmeans_problem* pr, int n, cons
         bi.nepi = 0;
         if (bi.dense) continue;
         B.n_lowd += 1;
+        B.any_ham = B.any_ham || bi.P.ham;
         int gi = -1;
         for (size_t g = 0; g < B.groups.size(); ++g)
-            if (B.groups[g].prec == prec && B.groups[g].d == q.X.d) gi = (int)g;
+            if (B.groups[g].prec == prec && B.groups[g].d == q.X.d && B.groups[g].cls == smem_class(bi.P.smem))
+                gi = (int)g;
         if (gi < 0) {
             BGroup g;
             g.prec = prec;
             g.d = q.X.d;
+            g.cls = smem_class(bi.P.smem);
+            g.ops = 0.0;
             g.smem = 0;
             g.items_off = 0;
             g.grid = 1;
@@ -267,6 +287,7 @@ kmeans_status batch_solve(kmeans_ctx* ctx, const kmeans_problem* pr, int n, cons
         bi.group = gi;
         BGroup& g = B.groups[gi];
         g.smem = std::max(g.smem, bi.P.smem);
+        g.ops += (double)q.X.N * q.K * (q.X.d + 2);
         for (int b = 0; b < bi.P.nb; ++b) g.items.push_back(make_int2(i, b));
         for (int b = 0; b < bi.P.nfin; ++b) B.fin_items.push_back(make_int2(i, b));
         B.fin_smem_max = std::max(B.fin_smem_max, fin_smem(bi.P.KB, q.X.d));

@@ -13,9 +13,10 @@
 // Near ties: the BF16 scores carry a rigorous rounding-error bound (derived where the kernel
 // arguments are built)
 //   B ~= (4 u_b + 4 d u) |x| max|c| + 4 u max|c|^2     (u_b = 2^-9, u = 2^-24);
-// the epilogue keeps per row the two best (value, lowest index) and the third-best value.  If the
-// top-2 gap is within 2B but the third value is clear, only the two best can be the argmin and
-// they are compared in FP32 (direct form); otherwise the row is rescored over all K in FP32.
+// the epilogue keeps per row the three best (value, lowest index) and the fourth-best value.  If the
+// top-2 gap is within 2B, the candidates are the best two or three whose successor is clear of 2B;
+// they are compared in FP32 (direct form).  Only a row with four or more scores within 2B of the
+// best is rescored over all K in FP32.
 //
 // Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
@@ -39,6 +40,7 @@ constexpr int KBLK = 64;           // bf16 per 128-byte swizzle row
 constexpr int CST = 2;             // centroid-tile stages
 constexpr int DTHREADS = 576;      // 18 warps: TMA, MMA, 16 epilogue
 constexpr int SEG = 64;            // rows per segment-sum chunk
+constexpr int MREC = 7;            // floats per row and column quarter in the merge buffer
 constexpr unsigned SPIN_LIMIT = 1u << 28;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -159,7 +161,7 @@ __host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
     p.x = o;     o += 2u * nkb * TM * 128;
     p.c = o;     o += (uint32_t)CST * nkb * TN * 128;
     p.cn = o;    o += (uint32_t)Kpad * 4;
-    p.merge = o; o += 3 * TM * 5 * 4;
+    p.merge = o; o += 3 * TM * MREC * 4;
     p.bar = (o + 7) & ~7u; o = p.bar + 16 * 8;
     p.slot = o;  o += 8;
     p.abort = o; o += 16;
@@ -288,9 +290,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
         volatile int* s_go = reinterpret_cast<volatile int*>(smem + P.abort + 4);
         uint32_t ait = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            // per row and quarter: the two best (value, lowest index) and the third-best value
-            float v1 = __int_as_float(0x7f800000), v2 = v1, v3 = v1;
-            int i1 = 0, i2 = 0;
+            // per row and quarter: the three best (value, lowest index) and the fourth-best value
+            float v1 = __int_as_float(0x7f800000), v2 = v1, v3 = v1, v4 = v1;
+            int i1 = 0, i2 = 0, i3 = 0;
             bool ok = true;
             for (int ct = 0; ct < nct; ++ct, ++ait) {
                 const uint32_t ab = ait & 1;
@@ -309,8 +311,10 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                         for (int e = 0; e < 16; ++e) {
                             const float s = fmaf(-2.f, v[e], s_cn[j0 + e]);
                             const int j = j0 + e;
+                            const bool p1 = s < v1, p2 = s < v2, p3 = s < v3;
+                            v4 = fminf(v4, fmaxf(v3, s));
+                            i3 = p2 ? i2 : (p3 ? j : i3);
                             v3 = fminf(v3, fmaxf(v2, s));
-                            const bool p1 = s < v1, p2 = s < v2;
                             i2 = p1 ? i1 : (p2 ? j : i2);
                             v2 = fminf(v2, fmaxf(v1, s));
                             i1 = p1 ? j : i1;
@@ -325,35 +329,45 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             // merge the four column quarters of each row (lexicographic on (value, index))
             const int r = q * 32 + lane;
             if (h > 0) {
-                float* m = s_merge + ((h - 1) * TM + r) * 5;
+                float* m = s_merge + ((h - 1) * TM + r) * MREC;
                 m[0] = v1;
                 m[1] = v2;
                 m[2] = v3;
-                m[3] = __int_as_float(i1);
-                m[4] = __int_as_float(i2);
+                m[3] = v4;
+                m[4] = __int_as_float(i1);
+                m[5] = __int_as_float(i2);
+                m[6] = __int_as_float(i3);
             }
             named_bar(1, 512);
             if (h == 0 && ok) {
                 for (int hh = 0; hh < 3; ++hh) {
-                    const float* m = s_merge + (hh * TM + r) * 5;
-                    const float w[2] = {m[0], m[1]};
-                    const int wj[2] = {__float_as_int(m[3]), __float_as_int(m[4])};
-                    for (int u = 0; u < 2; ++u) {
-                        if (w[u] < v1 || (w[u] == v1 && wj[u] < i1)) {
-                            v3 = fminf(v3, v2);
+                    const float* m = s_merge + (hh * TM + r) * MREC;
+                    for (int u = 0; u < 3; ++u) {
+                        const float w = m[u];
+                        const int wj = __float_as_int(m[4 + u]);
+                        if (w < v1 || (w == v1 && wj < i1)) {
+                            v4 = fminf(v4, v3);
+                            v3 = v2;
+                            i3 = i2;
                             v2 = v1;
                             i2 = i1;
-                            v1 = w[u];
-                            i1 = wj[u];
-                        } else if (w[u] < v2 || (w[u] == v2 && wj[u] < i2)) {
-                            v3 = fminf(v3, v2);
-                            v2 = w[u];
-                            i2 = wj[u];
+                            v1 = w;
+                            i1 = wj;
+                        } else if (w < v2 || (w == v2 && wj < i2)) {
+                            v4 = fminf(v4, v3);
+                            v3 = v2;
+                            i3 = i2;
+                            v2 = w;
+                            i2 = wj;
+                        } else if (w < v3 || (w == v3 && wj < i3)) {
+                            v4 = fminf(v4, v3);
+                            v3 = w;
+                            i3 = wj;
                         } else {
-                            v3 = fminf(v3, w[u]);
+                            v4 = fminf(v4, w);
                         }
                     }
-                    v3 = fminf(v3, m[2]);
+                    v4 = fminf(v4, m[3]);
                 }
                 const float nb1 = v1, nb2 = v2;
                 const int ni1 = i1;
@@ -375,12 +389,13 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     const float bnd = a.bcoef_a * xn * cmax + a.bcoef_b * cmax2;
                     rho[row] = ni1;
                     if (!(nb2 - nb1 > 2.f * bnd)) {
-                        if (v3 - nb1 > 2.f * bnd) {
-                            // only the two best can be the argmin: compare them exactly later
+                        if (v3 - nb1 > 2.f * bnd || v4 - nb1 > 2.f * bnd) {
+                            // only the two (or three) best can be the argmin: compare them exactly later
                             const unsigned pos = atomicAdd(a.qcount + 1, 1u);
-                            a.cand[3 * pos] = (int)row;
-                            a.cand[3 * pos + 1] = ni1;
-                            a.cand[3 * pos + 2] = i2;
+                            a.cand[4 * pos] = (int)row;
+                            a.cand[4 * pos + 1] = ni1;
+                            a.cand[4 * pos + 2] = i2;
+                            a.cand[4 * pos + 3] = v3 - nb1 > 2.f * bnd ? -1 : i3;
                         } else {
                             const unsigned pos = atomicAdd(a.qcount, 1u);
                             a.queue[pos] = (int)row;
@@ -404,9 +419,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ near-tie rescoring
-// FP32 direct form sum_k (x_k - c_jk)^2 for the queued rows.  Pairs (row, i1, i2): one warp
-// compares the two candidates (lanes split d, fixed butterfly).  Full rows: one warp scans all K
-// (lanes split K, ascending j per lane) and a lexicographic (distance, index) butterfly.
+// FP32 direct form sum_k (x_k - c_jk)^2 for the queued rows.  Candidate sets (row, i1, i2, i3 or
+// -1): one warp compares the two or three candidates (lanes split d, fixed butterfly; lowest index
+// wins a tie).  Full rows: see k_rescore_full.
 __global__ void __launch_bounds__(256) k_rescore(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
@@ -419,21 +434,35 @@ __global__ void __launch_bounds__(256) k_rescore(DenseArgs a)
     const int d = a.d, K = a.K;
     int32_t* rho = pass_rho(a, a.st);
     for (unsigned q = blockIdx.x * 8 + w; q < npair; q += gridDim.x * 8) {
-        const int64_t row = a.cand[3 * q];
-        const int j1 = a.cand[3 * q + 1], j2 = a.cand[3 * q + 2];
-        float s1 = 0.f, s2 = 0.f;
+        const int64_t row = a.cand[4 * q];
+        const int j1 = a.cand[4 * q + 1], j2 = a.cand[4 * q + 2], j3 = a.cand[4 * q + 3];
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         for (int k = lane; k < d; k += 32) {
             const float x = X[row * d + k];
             const float t1 = x - C[(size_t)j1 * d + k], t2 = x - C[(size_t)j2 * d + k];
             s1 = fmaf(t1, t1, s1);
             s2 = fmaf(t2, t2, s2);
+            if (j3 >= 0) {
+                const float t3 = x - C[(size_t)j3 * d + k];
+                s3 = fmaf(t3, t3, s3);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(FULL, s1, o);
             s2 += __shfl_xor_sync(FULL, s2, o);
+            s3 += __shfl_xor_sync(FULL, s3, o);
         }
-        if (lane == 0) rho[row] = (s2 < s1 || (s2 == s1 && j2 < j1)) ? j2 : j1;
+        if (lane == 0) {
+            float bs = s1;
+            int bj = j1;
+            if (s2 < bs || (s2 == bs && j2 < bj)) {
+                bs = s2;
+                bj = j2;
+            }
+            if (j3 >= 0 && (s3 < bs || (s3 == bs && j3 < bj))) bj = j3;
+            rho[row] = bj;
+        }
     }
     (void)sx;
     (void)nfull;

@@ -27,7 +27,7 @@ struct DenseArgs {
     const int32_t* rho_prev;  // standalone previous assignment (optional)
     int32_t* rho_pair[2];     // solver ping-pong assignment
     int* queue;               // [N] rows to rescore over all K
-    int* cand;                // [N][3] (row, i1, i2): rows whose argmin is one of two candidates
+    int* cand;                // [N][4] (row, i1, i2, i3 or -1): rows whose argmin is one of two or three candidates
     unsigned int* qcount;     // [2]: full rows, candidate pairs
     int* err;
     // update chain

@@ -19,7 +19,7 @@
 namespace km {
 
 constexpr int MMAX = 32;            // largest supported m_max (history ring length)
-constexpr int CH = 8;               // centroids per argmin chunk in the low-d FP32 kernel
+constexpr int KPAD_ALIGN = 16;      // K padded to a multiple of this for the low-d FP32 scan (its chunk widths divide it)
 constexpr int LOWD_THREADS = 256;   // threads per block of the low-d pass kernel
 constexpr int FIN_THREADS = 256;    // threads per block of the update/finalize kernel
 constexpr int DOTS = 2 * MMAX;      // per-block dot partials: Gram row + right-hand side
@@ -65,6 +65,7 @@ struct SolveState {
     int final_src;    // 0: result is C^t (C64), 1: result is C_AU
     long long n_changed;
     long long rescored;
+    long long scanned;    // rows scanned over all K, summed over the assignment passes
     double E_prev;    // stored E^{t-1}
     double E_prev2;   // stored E^{t-2}
     double E_trial;   // E(P^t, C^t) of the proposed iterate
@@ -106,6 +107,7 @@ struct PassArgs {
     double* pE;
     long long* pNch;
     long long* pResc;
+    long long* pScan;        // rows that went through the full scan over K (may be NULL)
     int* pBad;
     unsigned int* counter;
     // finalize targets
@@ -122,6 +124,20 @@ struct PassArgs {
     double eps2;
     long long thr;
     int nblk;                // blocks of this instance's pass (batched launches only)
+    // Hamerly bounds (FP32 solver passes; ham = 0 turns them off): per sample an upper bound on the
+    // distance to its assigned centroid and a lower bound on the distance to every other centroid,
+    // relative to the centroids of the last pass (hlast, FP32 [K][D])
+    int ham;
+    int hq_cap;              // rows one block can queue for a full scan (shared memory)
+    int d;                   // dimension (the pass kernels also have it as a template argument)
+    float* hub;
+    float* hlb;
+    float* hlast;
+    // per-pass inputs of the bounds, written by k_hprep: drift [K], half distance to the nearest
+    // other centroid [K], and hm = (largest drift, second largest, index of the largest, eta)
+    float* hdr;
+    float* hs;
+    float* hm;
 };
 
 // Arguments of the update / Anderson-finalize kernel.
@@ -270,7 +286,7 @@ __host__ __device__ inline size_t pk_index(int j, int k, int DP)
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s);
-size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins);
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap = 0);
 int pass_lowd_dp(int d);
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s);
 int fin_blocks(int K, int d, int* KB);
@@ -287,6 +303,8 @@ size_t devinfo_bytes();
 cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s);
 int pass_lowd_batch_occupancy(int prec, int d, size_t smem);
 int pass_lowd_occupancy(int prec, int d, size_t smem);   // resident blocks per SM (CUDA occupancy API)
+cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_hprep_batch(const BatchPass& b, int grid, cudaStream_t s);
 cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s);
 size_t fin_smem(int KB, int d);
 cudaError_t launch_mix_batch(const BatchMix& b, int grid, cudaStream_t s);

@@ -11,7 +11,7 @@
 //
 // FP32 path: distances as ||c'||^2 - 2 x'.c' with x' = x - o, c' = c - o (o = an origin near
 // the data), D FMAs per (sample, centroid) pair on CUDA cores, packed two samples per
-// fma.rn.f32x2.  The argmin over K runs in chunks of 8 centroids: a 3-input min tree gives the
+// fma.rn.f32x2.  The argmin over K runs in chunks of 8 (or 16) centroids: a 3-input min tree gives the
 // chunk minimum, and only the best chunk index, the best value and the second-best chunk
 // minimum are tracked.  After the scan the best chunk is re-scored (bit-identical arithmetic)
 // to find the lowest index attaining the minimum and the second-best value.  If the top-2 gap
@@ -29,19 +29,51 @@
 
 namespace km {
 
+namespace {
+
+__global__ void __launch_bounds__(256) k_hprep(PassArgs a, int mode)
+{
+    __shared__ float s_r[3 * 32];
+    hprep_dispatch(a, mode, s_r);
+}
+
+__global__ void __launch_bounds__(256) k_hprep_batch(BatchPass b)
+{
+    __shared__ float s_r[3 * 32];
+    for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
+        const PassArgs& a = b.args[b.items[it].x];
+        if (a.ham) hprep_dispatch(a, b.mode, s_r);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s)
+{
+    k_hprep<<<1, 256, 0, s>>>(a, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hprep_batch(const BatchPass& b, int grid, cudaStream_t s)
+{
+    k_hprep_batch<<<grid, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
 int pass_lowd_dp(int d)
 {
     return ((2 * (d + 1) + 3) / 4 * 4) / 2;
 }
 
-size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins)
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap)
 {
-    return layout(prec != KM_F64, d, pass_lowd_dp(d), K, Kpad, bins).total;
+    return layout(prec != KM_F64, d, pass_lowd_dp(d), K, Kpad, bins, hq_cap).total;
 }
 
 cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s)
 {
-    const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0);
+    const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0, a.ham ? a.hq_cap : 0);
     return prec == KM_F64 ? lowd_launch_f64(a, d, nb, smem, s) : lowd_launch_f32(a, d, nb, smem, s);
 }
 

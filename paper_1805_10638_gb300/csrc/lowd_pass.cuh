@@ -5,6 +5,7 @@
 
 #include "controller.cuh"
 #include "km_internal.cuh"
+#include "lowd_inst.cuh"
 
 #include <type_traits>
 
@@ -22,10 +23,18 @@ __device__ __forceinline__ float fmin3f(float a, float b, float c)
     return d;
 }
 
+// Centroids per argmin chunk of the FP32 scan with few dimensions (8 or 16; both divide KPAD_ALIGN).
+#ifndef KM_LOWD_CHUNK_SMALL
+#define KM_LOWD_CHUNK_SMALL 8
+#endif
+
+__host__ __device__ constexpr int chunk_of(int D) { return D <= 8 ? KM_LOWD_CHUNK_SMALL : 8; }
+
 template <int D>
 struct Shape {
     static constexpr int DP = ((2 * (D + 1) + 3) / 4 * 4) / 2;   // packed floats per centroid
     static constexpr int R = (D <= 8) ? 4 : 2;             // samples per thread in the scan
+    static constexpr int CK = chunk_of(D);                 // centroids per argmin chunk
 };
 
 // Resident blocks per SM the compiler must allow (register budget): the FP32 scan with few
@@ -33,24 +42,31 @@ struct Shape {
 #ifndef KM_LOWD_MINB_SMALL
 #define KM_LOWD_MINB_SMALL 4
 #endif
+#ifndef KM_LOWD_MINB_LARGE
+#define KM_LOWD_MINB_LARGE 2
+#endif
 template <typename T, int D>
 struct MinBlocks {
-    static constexpr int value = (std::is_same<T, float>::value && D <= 8) ? KM_LOWD_MINB_SMALL : 1;
+    static constexpr int value =
+        std::is_same<T, float>::value ? (D <= 8 ? KM_LOWD_MINB_SMALL : KM_LOWD_MINB_LARGE) : 1;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Layout {
-    size_t red, org, cpk, rec, c, stage, bS, bC, total;
+    size_t red, org, cpk, rec, c, stage, bS, bC, hdr, hs, hm, hq, total;
 };
 
-// Skewed copy of the packed centroids for the per-row recovery reads: chunk b (8 centroids of
-// D+1 floats) starts at b * RS floats, RS = 8(D+1)+1 is odd, so lanes recovering different chunks
+// Skewed copy of the packed centroids for the per-row recovery reads: chunk b (CK centroids of
+// D+1 floats) starts at b * RS floats, RS = CK(D+1)+1 is odd, so lanes recovering different chunks
 // read different banks (the unskewed layout puts every chunk's element (q,k) in the same bank).
+__host__ __device__ constexpr int rec_stride_of(int D) { return chunk_of(D) * (D + 1) + 1; }
 template <int D>
-__host__ __device__ constexpr int rec_stride() { return 8 * (D + 1) + 1; }
+__host__ __device__ constexpr int rec_stride() { return rec_stride_of(D); }
 
-__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins)
+// hq_cap > 0 (FP32 passes with Hamerly bounds): centroid drifts, half distances to the nearest other
+// centroid, drift maxima and the queue of rows that need a full scan.
+__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins, int hq_cap = 0)
 {
     const size_t esz = f32 ? 4 : 8;
     Layout L;
@@ -59,7 +75,7 @@ __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpa
     L.org = o;   o += 64 * sizeof(float);
     if (f32) {
         L.cpk = o; o += al16((size_t)Kpad * DP * 4);
-        L.rec = o; o += al16((size_t)(Kpad / 8) * (8 * (D + 1) + 1) * 4);
+        L.rec = o; o += al16((size_t)(Kpad / chunk_of(D)) * rec_stride_of(D) * 4);
         L.c = o;   o += al16((size_t)K * D * 4);
     } else {
         L.cpk = 0;
@@ -72,6 +88,14 @@ __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpa
         L.bC = o; o += al16((size_t)W * K * 4);
     } else {
         L.bS = L.bC = 0;
+    }
+    if (f32 && hq_cap > 0) {
+        L.hdr = o; o += al16((size_t)Kpad * 4);
+        L.hs = o;  o += al16((size_t)Kpad * 4);
+        L.hm = o;  o += 16 * 4;
+        L.hq = o;  o += al16((size_t)hq_cap * 4);
+    } else {
+        L.hdr = L.hs = L.hm = L.hq = 0;
     }
     L.total = o;
     return L;
@@ -119,7 +143,20 @@ __device__ long long block_sum_ll(long long v, double* red)
     return s;
 }
 
-// Scan all centroids for R samples: per chunk of 8 centroids (4 interleaved pairs), each
+// Minimum of one chunk's scores (pairs of centroids), by 3-input min instructions.
+__device__ __forceinline__ float chunk_min(const float2 (&s)[4])
+{
+    return fmin3f(fmin3f(s[0].x, s[0].y, s[1].x), fmin3f(s[1].y, s[2].x, s[2].y), fminf(s[3].x, s[3].y));
+}
+__device__ __forceinline__ float chunk_min(const float2 (&s)[8])
+{
+    const float a = fmin3f(s[0].x, s[0].y, s[1].x), b = fmin3f(s[1].y, s[2].x, s[2].y);
+    const float c = fmin3f(s[3].x, s[3].y, s[4].x), d = fmin3f(s[4].y, s[5].x, s[5].y);
+    const float e = fmin3f(s[6].x, s[6].y, s[7].x);
+    return fminf(fmin3f(a, b, c), fmin3f(d, e, s[7].y));
+}
+
+// Scan all centroids for R samples: per chunk of CK centroids (CK/2 interleaved pairs), each
 // fma.rn.f32x2 scores one sample against two centroids; xd holds each sample coordinate twice.
 template <int D, int R>
 __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int Kpad,
@@ -127,6 +164,7 @@ __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int
                                             float (&sec)[R], int (&bc)[R])
 {
     constexpr int PP = 2 * Shape<D>::DP;        // floats per centroid pair
+    constexpr int CK = Shape<D>::CK;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         best[r] = __int_as_float(0x7f800000);
@@ -134,10 +172,10 @@ __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int
         bc[r] = 0;
     }
 #pragma unroll 1
-    for (int c0 = 0; c0 < Kpad; c0 += CH) {
-        float2 s[R][CH / 2];
+    for (int c0 = 0; c0 < Kpad; c0 += CK) {
+        float2 s[R][CK / 2];
 #pragma unroll
-        for (int p = 0; p < CH / 2; ++p) {
+        for (int p = 0; p < CK / 2; ++p) {
             float cv[PP];
             const float4* p4 = reinterpret_cast<const float4*>(s_cpk + (size_t)((c0 >> 1) + p) * PP);
 #pragma unroll
@@ -158,8 +196,7 @@ __device__ __forceinline__ void scan_chunks(const float* __restrict__ s_cpk, int
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float m = fmin3f(fmin3f(s[r][0].x, s[r][0].y, s[r][1].x), fmin3f(s[r][1].y, s[r][2].x, s[r][2].y),
-                                   fminf(s[r][3].x, s[r][3].y));
+            const float m = chunk_min(s[r]);
             sec[r] = fminf(sec[r], fmaxf(best[r], m));
             const bool p = m < best[r];
             best[r] = p ? m : best[r];
@@ -175,11 +212,12 @@ __device__ __forceinline__ int recover(const float* __restrict__ s_rec, const fl
                                        int bc, float& second_in)
 {
     constexpr int RS = rec_stride<D>();
-    const float* base = s_rec + (size_t)(bc >> 3) * RS;
+    constexpr int CK = Shape<D>::CK;
+    const float* base = s_rec + (size_t)(bc / CK) * RS;
     int jj = -1;
     float sv = __int_as_float(0x7f800000);
 #pragma unroll
-    for (int q = 0; q < CH; ++q) {
+    for (int q = 0; q < CK; ++q) {
         const float* cp = base + q * (D + 1);
         float acc = cp[D];
 #pragma unroll
@@ -244,6 +282,135 @@ __device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int
     return idx;
 }
 
+// Per-pass inputs of the Hamerly bounds of one solve, computed by one block: by k_hprep before the
+// INIT and TRIAL passes (on C^0, C^t), and by the TRIAL pass's last block for the REVERT pass (on
+// C_AU) when the safeguard fired.  All in FP32 with explicit margins so that they only loosen the
+// bounds:
+//   hdr[j] = ||c_j - c_j^last|| (1 + 1e-5) + eta      drift since the centroids of the last pass
+//   hs[j]  = (min_{j' != j} ||c_j - c_j'|| / 2)(1 - 1e-5) - eta, at least 0
+//   hm     = (largest drift, second largest, index of the largest, eta)
+// with eta = 4e-7 max(||c||, ||c^last||), the allowance for the rounding of the FP32 centroids.
+template <int D>
+__device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96 floats of block scratch
+{
+    const SolveState* st = a.st;
+    if (st->done) return;
+    int which = 0;
+    if (mode == MODE_REVERT) {
+        if (!st->revert) return;
+        which = 1;
+    }
+    constexpr int d = D;
+    const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const float* cs = a.c32[which];
+    const float* cl = a.hlast;
+    const bool have_last = mode != MODE_INIT;
+    __syncthreads();      // s_r may be in use by the caller's previous step
+    float cm = 0.f;
+    for (int j = tid; j < K; j += blockDim.x) {
+        float n1 = 0.f, n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            n1 = fmaf(cs[j * d + k], cs[j * d + k], n1);
+            if (have_last) n2 = fmaf(cl[j * d + k], cl[j * d + k], n2);
+        }
+        cm = fmaxf(cm, fmaxf(n1, n2));
+    }
+    for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
+    if (lane == 0) s_r[warp] = cm;
+    __syncthreads();
+    cm = 0.f;
+    for (int w = 0; w < nw; ++w) cm = fmaxf(cm, s_r[w]);
+    const float eta = 4e-7f * sqrtf(cm) + 1e-30f;
+    __syncthreads();
+    float m1 = 0.f, m2 = 0.f;
+    int i1 = -1;
+    for (int j = tid; j < K; j += blockDim.x) {
+        float dr = 0.f;
+        if (have_last) {
+            float dd = 0.f;
+            for (int k = 0; k < d; ++k) {
+                const float t = cs[j * d + k] - cl[j * d + k];
+                dd = fmaf(t, t, dd);
+            }
+            dr = sqrtf(dd) * (1.f + 1e-5f) + eta;
+        }
+        a.hdr[j] = dr;
+        if (dr > m1) {
+            m2 = m1;
+            m1 = dr;
+            i1 = j;
+        } else if (dr > m2) {
+            m2 = dr;
+        }
+        float cj[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) cj[k] = cs[j * d + k];
+        float mn = __int_as_float(0x7f800000);
+#pragma unroll 4
+        for (int j2 = 0; j2 < K; ++j2) {
+            float dd = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = cj[k] - __ldg(cs + j2 * d + k);
+                dd = fmaf(t, t, dd);
+            }
+            mn = j2 == j ? mn : fminf(mn, dd);
+        }
+        a.hs[j] = fmaxf(0.f, 0.5f * sqrtf(mn) * (1.f - 1e-5f) - eta);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const float om1 = __shfl_xor_sync(0xffffffffu, m1, off), om2 = __shfl_xor_sync(0xffffffffu, m2, off);
+        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, off);
+        if (om1 > m1) {
+            m2 = fmaxf(m1, om2);
+            m1 = om1;
+            i1 = oi1;
+        } else {
+            m2 = fmaxf(m2, om1);
+        }
+    }
+    if (lane == 0) {
+        s_r[3 * warp] = m1;
+        s_r[3 * warp + 1] = m2;
+        s_r[3 * warp + 2] = __int_as_float(i1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float b1 = 0.f, b2 = 0.f;
+        int bi = -1;
+        for (int w = 0; w < nw; ++w) {
+            const float w1 = s_r[3 * w], w2 = s_r[3 * w + 1];
+            if (w1 > b1) {
+                b2 = fmaxf(b1, w2);
+                b1 = w1;
+                bi = __float_as_int(s_r[3 * w + 2]);
+            } else {
+                b2 = fmaxf(b2, w1);
+            }
+        }
+        a.hm[0] = b1;
+        a.hm[1] = b2;
+        a.hm[2] = __int_as_float(bi);
+        a.hm[3] = eta;
+    }
+}
+
+
+#define KM_HPREP_CASE(DD) \
+    case DD:              \
+        hprep_body<DD>(a, mode, s_r); \
+        break;
+
+// k_hprep / k_hprep_batch: the block's instance has its dimension at run time.
+__device__ inline void hprep_dispatch(const PassArgs& a, int mode, float* s_r)
+{
+    switch (a.d) {
+        KM_FOR_EACH_D(KM_HPREP_CASE)
+        default:
+            break;
+    }
+}
+
 // The work of block `bid` of a pass launched with `nblk` blocks.  The standalone kernel calls it
 // with (blockIdx.x, gridDim.x); the batched kernel with a work item's (block, blocks of that
 // instance), so that every instance gets exactly the arithmetic of its own launch.
@@ -279,7 +446,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     const bool do_assign = flags & F_ASSIGN;
     const bool do_bins = flags & F_BINS;
     const int K = a.K;
-    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins);
+    // Hamerly bounds: FP32 solver passes that assign (INIT computes the bounds, TRIAL and REVERT use them)
+    const bool ham = F32 && a.ham && do_assign &&
+                     (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
+    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0);
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     T* s_stage = reinterpret_cast<T*>(smem + L.stage);
     T* s_bS = reinterpret_cast<T*>(smem + L.bS);
@@ -353,7 +523,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         float* sr = reinterpret_cast<float*>(smem + L.rec);
         for (int i = tid; i < a.Kpad * (D + 1); i += blockDim.x) {
             const int j = i / (D + 1), k = i % (D + 1);
-            sr[(size_t)(j >> 3) * RS + (j & 7) * (D + 1) + k] = s_cpk[pk_index(j, k, DP)];
+            sr[(size_t)(j / Shape<D>::CK) * RS + (j % Shape<D>::CK) * (D + 1) + k] = s_cpk[pk_index(j, k, DP)];
         }
         float mx = 0.f;
         for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, s_cpk[pk_index(j, D, DP)]);
@@ -370,6 +540,29 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         __syncthreads();
     }
 
+    // ---- Hamerly: the per-pass inputs k_hprep wrote (drifts, half distances, drift maxima, eta)
+    float h_eta = 0.f, h_dm1 = 0.f, h_dm2 = 0.f;
+    int h_am = -1;
+    float* s_hdr = reinterpret_cast<float*>(smem + L.hdr);
+    float* s_hs = reinterpret_cast<float*>(smem + L.hs);
+    float* s_hm = reinterpret_cast<float*>(smem + L.hm);
+    unsigned int* s_hqn = reinterpret_cast<unsigned int*>(s_hm + 8);
+    uint32_t* s_hq = reinterpret_cast<uint32_t*>(smem + L.hq);
+    if constexpr (F32) {
+        if (ham) {
+            for (int jj = tid; jj < K; jj += blockDim.x) {
+                s_hdr[jj] = a.hdr[jj];
+                s_hs[jj] = a.hs[jj];
+            }
+            if (tid == 0) *s_hqn = 0u;
+            __syncthreads();
+            h_dm1 = a.hm[0];
+            h_dm2 = a.hm[1];
+            h_am = __float_as_int(a.hm[2]);
+            h_eta = a.hm[3];
+        }
+    }
+
     const T* X = reinterpret_cast<const T*>(a.X);
     const int64_t N = a.N;
     const int64_t TT = (int64_t)nblk * blockDim.x;
@@ -379,7 +572,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     const int64_t n_max = __shfl_sync(FULL, n_g, 0);
 
     T eacc = T(0);
-    long long nch = 0, resc = 0;
+    long long nch = 0, resc = 0, nscan = 0;
     int bad = 0;
 
     // Everything after the label is known, for one sample (warp-uniform call).
@@ -446,7 +639,146 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     if (do_assign) {
         if constexpr (F32) {
             const float cA = a.bound_coef, cB = a.bound_coef2;
-            const int64_t main_iters = n_min / R;
+            if (ham) {
+                // Bounds of a row the full scan assigned: u from the exact FP32 distance to the chosen
+                // centroid, l from the second-best score minus its error bound (0 after a near-tie
+                // rescore, which is the conservative choice).
+                auto ham_store = [&](int64_t row, int idx, float second, float xn, float bnd, bool rescored) {
+                    const float* xr = X + row * D;
+                    const float* c = reinterpret_cast<const float*>(s_c) + (size_t)idx * D;
+                    float dd = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float t = xr[k] - c[k];
+                        dd = fmaf(t, t, dd);
+                    }
+                    const float u = sqrtf(dd) * (1.f + 1e-5f) + h_eta;
+                    float l = 0.f;
+                    if (!rescored)
+                        l = sqrtf(fmaxf(0.f, second - bnd + xn * (1.f - 2e-6f))) * (1.f - 1e-5f) - h_eta;
+                    rho_out[row] = idx;
+                    a.hub[row] = u;
+                    a.hlb[row] = fmaxf(l, 0.f);
+                };
+                // phase A: rows whose bounds show the assigned centroid is still the unique nearest by
+                // a relative margin of 1e-5 (far beyond the FP32 rounding of either score form, so a
+                // full scan would return the same label) keep it; the others are queued
+                const bool force = a.mode == MODE_INIT;
+                const int32_t* rho_last = a.mode == MODE_TRIAL ? rho_prev : rho_out;
+                for (int64_t q = 0; q < n_g; ++q) {
+                    const int64_t row = g + q * TT;
+                    const float* xr = X + row * D;
+                    check(xr);
+                    bool scan = force;
+                    if (!force) {
+                        const int al = rho_last[row];
+                        float u = (a.hub[row] + s_hdr[al]) * (1.f + 2e-7f);
+                        const float l = fmaxf(0.f, (a.hlb[row] - (al == h_am ? h_dm2 : h_dm1)) * (1.f - 2e-7f));
+                        const float m = fmaxf(l, s_hs[al]);
+                        if (!(u * (1.f + 1e-5f) < m)) {
+                            const float* c = reinterpret_cast<const float*>(s_c) + (size_t)al * D;
+                            float dd = 0.f;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                const float t = xr[k] - c[k];
+                                dd = fmaf(t, t, dd);
+                            }
+                            u = sqrtf(dd) * (1.f + 1e-5f) + h_eta;
+                            scan = !(u * (1.f + 1e-5f) < m);
+                        }
+                        if (!scan) {
+                            rho_out[row] = al;
+                            a.hub[row] = u;
+                            a.hlb[row] = l;
+                        }
+                    }
+                    if (scan) {
+                        s_hq[atomicAdd(s_hqn, 1u)] = (uint32_t)row;
+                        nscan += 1;
+                    }
+                }
+                __syncthreads();
+                // phase B: full scans of the queued rows, R per thread while whole rounds remain
+                const int nq = (int)*s_hqn;
+                const int round = (int)blockDim.x * R;
+                int qb = 0;
+                for (; qb + round <= nq; qb += round) {
+                    int64_t rows[R];
+                    float x[R][D];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        rows[r] = s_hq[qb + r * (int)blockDim.x + tid];
+                        const float* xr = X + rows[r] * D;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) x[r][k] = xr[k] - o[k];
+                    }
+                    float2 xd[R][D];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) xd[r][k] = make_float2(x[r][k], x[r][k]);
+                    float best[R], sec[R];
+                    int bc[R];
+                    scan_chunks<D, R>(s_cpk, a.Kpad, xd, best, sec, bc);
+                    int idxr[R];
+                    bool need[R];
+                    float sc2[R], xnr[R], bndr[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        float xn = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) xn = fmaf(x[r][k], x[r][k], xn);
+                        float sin_;
+                        idxr[r] = recover<D>(s_rec, x[r], best[r], bc[r], sin_);
+                        sc2[r] = fminf(sec[r], sin_);
+                        xnr[r] = xn;
+                        bndr[r] = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                        need[r] = sc2[r] - best[r] <= 2.f * bndr[r];
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        idxr[r] = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, rows[r], need[r], idxr[r],
+                                                  lane, resc);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) ham_store(rows[r], idxr[r], sc2[r], xnr[r], bndr[r], need[r]);
+                }
+                for (int e = qb + tid; e < qb + ((nq - qb + (int)blockDim.x - 1) / (int)blockDim.x) * (int)blockDim.x;
+                     e += blockDim.x) {
+                    const bool valid = e < nq;
+                    const int64_t row = valid ? (int64_t)s_hq[e] : 0;
+                    float x[1][D];
+                    const float* xr = X + row * D;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) x[0][k] = xr[k] - o[k];
+                    float2 xd[1][D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xd[0][k] = make_float2(x[0][k], x[0][k]);
+                    float best[1], sec[1];
+                    int bc[1];
+                    scan_chunks<D, 1>(s_cpk, a.Kpad, xd, best, sec, bc);
+                    float xn = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xn = fmaf(x[0][k], x[0][k], xn);
+                    float sin_;
+                    int idx = recover<D>(s_rec, x[0], best[0], bc[0], sin_);
+                    const float second = fminf(sec[0], sin_);
+                    const float bnd = cA * cmax * cmax + cB * sqrtf(xn) * cmax;
+                    const bool need = valid && second - best[0] <= 2.f * bnd;
+                    idx = warp_rescore<D>(reinterpret_cast<const float*>(s_c), K, X, row, need, idx, lane, resc);
+                    if (valid) ham_store(row, idx, second, xn, bnd, need);
+                }
+                __syncthreads();
+                // phase C: the rest of the pass in the same per-thread row order as without bounds,
+                // so the update's sums come out bitwise the same
+                for (int64_t q = 0; q < n_max; ++q) {
+                    const bool valid = q < n_g;
+                    const int64_t row = valid ? g + q * TT : 0;
+                    finish(row, valid, valid ? rho_out[row] : 0);
+                }
+                kk = n_max;
+            }
+            const int64_t main_iters = ham ? 0 : n_min / R;
+            if (!ham) nscan = n_g;
             for (int64_t it = 0; it < main_iters; ++it, kk += R) {
                 float x[R][D];
 #pragma unroll
@@ -551,11 +883,14 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     const double eb = block_sum_d((double)eacc, s_red);
     const long long nb_ch = block_sum_ll(nch, s_red);
     const long long nb_rs = block_sum_ll(resc, s_red);
+    if constexpr (!F32) nscan = do_assign ? n_g : 0;
+    const long long nb_sc = block_sum_ll(nscan, s_red);
     const long long nb_bad = block_sum_ll(bad, s_red);
     if (tid == 0) {
         a.pE[bid] = eb;
         a.pNch[bid] = nb_ch;
         a.pResc[bid] = nb_rs;
+        if (a.pScan) a.pScan[bid] = nb_sc;
         a.pBad[bid] = (int)(nb_bad != 0);
     }
     if (do_bins) {
@@ -586,17 +921,21 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     if (*sflag == 0u) return;
     __threadfence();
     double E = 0.0;
-    long long ch = 0, rs = 0, bd = 0;
+    long long ch = 0, rs = 0, bd = 0, sc = 0;
     for (int b = tid; b < nblk; b += blockDim.x) {
         E += __ldcg(a.pE + b);
         ch += __ldcg(a.pNch + b);
         rs += __ldcg(a.pResc + b);
+        if (a.pScan) sc += __ldcg(a.pScan + b);
         bd += __ldcg(a.pBad + b);
     }
     E = block_sum_d(E, s_red);
     ch = block_sum_ll(ch, s_red);
     rs = block_sum_ll(rs, s_red);
+    sc = block_sum_ll(sc, s_red);
     bd = block_sum_ll(bd, s_red);
+    if (ham)
+        for (int i = tid; i < K * D; i += blockDim.x) a.hlast[i] = reinterpret_cast<const float*>(s_c)[i];
     if (tid == 0) {
         *a.counter = 0u;
         if (a.mode == MODE_STANDALONE) {
@@ -604,6 +943,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
             if (a.out_E) *a.out_E = E;
         } else {
             st->rescored += rs;
+            st->scanned += sc;
             if (a.mode == MODE_EPI) {
                 st->E_final = E;
             } else if (a.mode == MODE_INIT) {
@@ -618,6 +958,14 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 // the kernel that ends the solve also ends the graph's while loop
                 if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
             }
+        }
+    }
+    // the safeguard fired: the REVERT pass's bound inputs (drift from C^t, just saved as the last
+    // centroids, to C_AU), computed here instead of by a launch of their own
+    if constexpr (F32) {
+        if (ham && a.mode == MODE_TRIAL) {
+            __syncthreads();
+            if (st->revert && !st->done) hprep_body<D>(a, MODE_REVERT, reinterpret_cast<float*>(s_red));
         }
     }
 }
@@ -648,13 +996,22 @@ __global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_l
     }
 }
 
+// Largest dynamic shared memory a kernel may request: the per-block limit minus its static part.
+template <typename F>
+int dyn_smem_limit(F kern)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return LOWD_SMEM_MAX;
+    return LOWD_SMEM_MAX - (int)fa.sharedSizeBytes;
+}
+
 template <typename T, int D>
 cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
 {
     auto kern = k_pass_lowd<T, D>;
     static bool attr_set = false;
     if (!attr_set || smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -668,7 +1025,7 @@ cudaError_t launch_batch_one(const BatchPass& b, int grid, size_t smem, cudaStre
     auto kern = k_pass_lowd_batch<T, D>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -681,7 +1038,7 @@ int pass_occ(size_t smem)
 {
     int n = 0;
     auto kern = k_pass_lowd<T, D>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX) != cudaSuccess) return 1;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern)) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
@@ -691,7 +1048,7 @@ int batch_occ(size_t smem)
 {
     int n = 0;
     auto kern = k_pass_lowd_batch<T, D>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LOWD_SMEM_MAX) != cudaSuccess) return 1;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern)) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

@@ -29,12 +29,13 @@ struct GraphKey {
     kmeans_params p;
     void* arena;
     size_t arena_bytes;
+    int ham;
 };
 
 struct Plan {
     // offsets into the arena
     size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
-    size_t pS, pCnt, pE, pNch, pResc, pBad, pDots, counter, info;
+    size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
     size_t cb0, cb1, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
@@ -44,6 +45,10 @@ struct Plan {
     bool dense;
     int dpad, nbk, rpb, max_chunks;
     size_t smem;
+    // Hamerly bounds of the FP32 solver passes
+    bool ham;
+    int hq_cap;
+    size_t hub, hlb, hlast, hprep;
 };
 
 constexpr int DENSE_RPB = 4096;   // rows per block of the dense update's histogram and scatter
@@ -166,7 +171,7 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.cn0 = take((size_t)P.Kpad * 4);
     P.cn1 = take((size_t)P.Kpad * 4);
     P.xnorm = take((size_t)N * 4);
-    P.queue = take((size_t)N * 4 * 4);   // full-rescore rows, then (row, i1, i2) candidate pairs
+    P.queue = take((size_t)N * 5 * 4);   // full-rescore rows, then (row, i1, i2, i3) candidate sets
     P.qcount = take(256);
     P.err = take(256);
     P.hist = take((size_t)K * P.nbk * 4);
@@ -184,7 +189,7 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.rown = take(4096 * 8);
     P.pS = P.S;
     P.pCnt = P.counts;
-    P.pE = P.pNch = P.pResc = P.pBad = 0;
+    P.pE = P.pNch = P.pResc = P.pScan = P.pBad = 0;
     P.pDots = take((size_t)P.nfin * DOTS * 8);
     P.info = take(256);
     if (host_copies) {
@@ -200,27 +205,57 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     return KM_OK;
 }
 
+// KM_HAMERLY=0 in the environment solves without Hamerly bounds (same results, every row scanned).
+bool hamerly_mode()
+{
+    const char* v = getenv("KM_HAMERLY");
+    return !(v && v[0] == '0');
+}
+
+// Solver plans (ham_ok) on the FP32 low-d path use Hamerly bounds when every block can afford to
+// recompute the centroids' pairwise half-distances (K*K*d <= 2^21) and the row queue fits in
+// shared memory.
 kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
-                        Plan& P, bool bins = true)
+                        Plan& P, bool bins = true, bool ham_ok = false)
 {
     P.dense = false;
+    P.ham = false;
+    P.hq_cap = 0;
+    P.hub = P.hlb = P.hlast = P.hprep = 0;
     P.dpad = P.nbk = P.rpb = P.max_chunks = 0;
     if (prec == KM_BF16_F32 && d > 16) return make_plan_dense(ctx, N, d, K, m_max, host_copies, P);
     if (d > 16) return fail(ctx, KM_EINVAL, "d > 16 needs KM_BF16_F32 (the tensor-core path)");
     const bool f32 = prec != KM_F64;
     const size_t esz = f32 ? 4 : 8;
     P.DP = pass_lowd_dp(d);
-    P.Kpad = (K + CH - 1) / CH * CH;
+    P.Kpad = (K + KPAD_ALIGN - 1) / KPAD_ALIGN * KPAD_ALIGN;
     P.smem = pass_lowd_smem(prec, d, K, P.Kpad, bins);
     if (P.smem > (size_t)LOWD_SMEM_MAX)
         return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
     P.nb = pass_blocks(ctx, N, P.smem, prec, d);
+    if (ham_ok && f32 && bins && hamerly_mode() && (int64_t)K * K * d <= (int64_t(1) << 21) &&
+        N < (int64_t(1) << 31)) {
+        const int64_t per = (int64_t)P.nb * LOWD_THREADS;
+        const int cap = (int)((N + per - 1) / per) * LOWD_THREADS;
+        const size_t sm = pass_lowd_smem(prec, d, K, P.Kpad, bins, cap);
+        if (sm <= (size_t)LOWD_SMEM_MAX) {
+            P.ham = true;
+            P.hq_cap = cap;
+            P.smem = sm;
+        }
+    }
     P.nfin = fin_blocks(K, d, &P.KB);
     const size_t n = (size_t)K * d;
     const int mm = m_max > 0 ? m_max : 1;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += al256(bytes); return r; };
     P.counter = take(256);          // fixed offset 0 for every plan; zeroed at the start of every call
+    if (P.ham) {
+        P.hub = take((size_t)N * 4);
+        P.hlb = take((size_t)N * 4);
+        P.hlast = take(n * 4);
+        P.hprep = take(((size_t)2 * P.Kpad + 8) * 4);
+    }
     P.st = take(sizeof(SolveState));
     P.rhoA = take((size_t)N * 4);
     P.rhoB = take((size_t)N * 4);
@@ -239,6 +274,7 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.pE = take((size_t)P.nb * 8);
     P.pNch = take((size_t)P.nb * 8);
     P.pResc = take((size_t)P.nb * 8);
+    P.pScan = take((size_t)P.nb * 8);
     P.pBad = take((size_t)P.nb * 4);
     P.pDots = take((size_t)P.nfin * DOTS * 8);
     P.info = take(256);
@@ -321,6 +357,7 @@ PassArgs base_pass(char* base, const Plan& P, const void* X, int64_t N, int K, i
     a.pE = at<double>(base, P.pE);
     a.pNch = at<long long>(base, P.pNch);
     a.pResc = at<long long>(base, P.pResc);
+    a.pScan = P.pScan ? at<long long>(base, P.pScan) : nullptr;
     a.pBad = at<int>(base, P.pBad);
     a.counter = at<unsigned int>(base, P.counter);
     a.st = at<SolveState>(base, P.st);
@@ -339,6 +376,15 @@ void set_bound(PassArgs& a, int d)
     a.bound_coef2 = (float)(1.01 * (2 * d + 4) * u);
 }
 
+
+// Shared-memory class of a low-d pass (resident blocks per SM its smem allows, at most 4): the
+// batched and serving launches group instances by (precision, d, class) so that a small instance is
+// not launched with a large instance's shared memory.
+inline int smem_class(size_t smem)
+{
+    const int c = (int)((SM_SMEM - 1024) / (smem + 1024));
+    return c < 1 ? 1 : (c > 4 ? 4 : c);
+}
 
 // The accelerated iterate is formed inside k_fin's last block when K*d is small (saves a launch).
 inline bool fuse_mix_rule(int K, int d) { return K <= 1024 && (size_t)K * d <= 16384; }
@@ -484,6 +530,15 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     pa.eps1 = p.eps1;
     pa.eps2 = p.eps2;
     pa.thr = thr;
+    pa.ham = P.ham ? 1 : 0;
+    pa.hq_cap = P.hq_cap;
+    pa.d = d;
+    pa.hub = P.ham ? at<float>(base, P.hub) : nullptr;
+    pa.hlb = P.ham ? at<float>(base, P.hlb) : nullptr;
+    pa.hlast = P.ham ? at<float>(base, P.hlast) : nullptr;
+    pa.hdr = P.ham ? at<float>(base, P.hprep) : nullptr;
+    pa.hs = P.ham ? pa.hdr + P.Kpad : nullptr;
+    pa.hm = P.ham ? pa.hdr + 2 * P.Kpad : nullptr;
 
     FinArgs& fa = L.fa;
     memset(&fa, 0, sizeof(fa));
@@ -601,6 +656,7 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
     PassArgs a = L.pa;
     a.mode = MODE_INIT;
     a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
+    if (e == cudaSuccess && a.ham) e = launch_hprep(a, MODE_INIT, s);
     if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
     FinArgs f = L.fa;
     f.mode = MODE_INIT;
@@ -637,8 +693,9 @@ cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraph
     a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
     a.use_cond = use_cond;
     a.cond = h;
-    cudaError_t e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
-    a.mode = MODE_REVERT;
+    cudaError_t e = a.ham ? launch_hprep(a, MODE_TRIAL, s) : cudaSuccess;
+    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    a.mode = MODE_REVERT;       // its bound inputs come from the TRIAL pass's last block
     if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
     FinArgs f = L.fa;
     f.mode = MODE_TRIAL;
@@ -683,6 +740,7 @@ struct DevInfoH {
     int iters, accepted, rejected, passes, converged, m_final, status, pad;
     double E;
     long long rescored;
+    long long scanned;
 };
 
 kmeans_status validate_params(kmeans_ctx* ctx, const kmeans_params& p)
@@ -759,6 +817,7 @@ void fill_info(kmeans_info* info, const DevInfoH* di, float ms)
     info->device_ms = ms;
     info->status = di->status;
     info->reserved = 0;
+    info->scanned_rows = di->scanned;
 }
 
 // Add  prologue -> while (cond) { body } -> epilogue  to graph g as an independent chain.  The

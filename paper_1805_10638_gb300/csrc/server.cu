@@ -290,11 +290,11 @@ void apply_flags(kmeans_server* srv, int b)
 
 struct ItemSet {
     std::vector<std::vector<int2>> pass;   // per group
-    std::vector<int2> fin, mix, prep, epi;
+    std::vector<int2> fin, mix, prep, epi, hp;   // hp: (slot, 0) of the instances passing, for k_hprep
 };
 
 struct GroupKey {
-    int prec, d;
+    int prec, d, cls;
     size_t smem;
 };
 
@@ -360,12 +360,13 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
     std::vector<GroupKey> groups;
     auto group_of = [&](const Req& r) {
         const int prec = r.Xh.prec == KM_F64 ? KM_F64 : KM_F32;
+        const int cls = smem_class(r.P.smem);
         for (size_t g = 0; g < groups.size(); ++g)
-            if (groups[g].prec == prec && groups[g].d == r.Xh.d) {
+            if (groups[g].prec == prec && groups[g].d == r.Xh.d && groups[g].cls == cls) {
                 groups[g].smem = std::max(groups[g].smem, r.P.smem);
                 return (int)g;
             }
-        groups.push_back(GroupKey{prec, r.Xh.d, r.P.smem});
+        groups.push_back(GroupKey{prec, r.Xh.d, cls, r.P.smem});
         return (int)groups.size() - 1;
     };
     // item lists: prologue (J), body (J + A), epilogue (F)
@@ -383,6 +384,7 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
             for (int b = 0; b < mix_blocks(r.K, r.Xh.d); ++b) is.mix.push_back(make_int2(s, b));
         }
         if (prep) is.prep.push_back(make_int2(s, 0));
+        if (pass && r.P.ham) is.hp.push_back(make_int2(s, 0));
         if (epil)
             for (int b = 0; b < epi_blocks(r.Xh.N, (size_t)r.K * r.Xh.d); ++b) is.epi.push_back(make_int2(s, b));
     };
@@ -401,6 +403,7 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
         lists.push_back(&is->mix);
         lists.push_back(&is->prep);
         lists.push_back(&is->epi);
+        lists.push_back(&is->hp);
     }
     size_t tot = 0;
     for (auto* v : lists) {
@@ -429,7 +432,32 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
     auto run = [&](ItemSet& is, int mode, int flags, bool with_fin, bool with_prep, bool with_epi) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         const size_t l0 = li;
-        li += groups.size() + 4;
+        li += groups.size() + 5;
+        auto hprep = [&](int m) -> cudaError_t {
+            if (is.hp.empty()) return cudaSuccess;
+            BatchPass h;
+            h.args = tb<PassArgs>(srv, srv->t_pass);
+            h.items = items + spans[l0 + groups.size() + 4].first;
+            h.nitems = (int)is.hp.size();
+            h.mode = m;
+            h.flags = 0;
+            return launch_hprep_batch(h, (int)std::min<size_t>(is.hp.size(), 1024), srv->s_small);
+        };
+        auto passes = [&](int m) -> cudaError_t {
+            cudaError_t r = (m == MODE_INIT || m == MODE_TRIAL) ? hprep(m) : cudaSuccess;
+            for (size_t g = 0; g < groups.size() && r == cudaSuccess; ++g) {
+                if (is.pass[g].empty()) continue;
+                BatchPass b;
+                b.args = tb<PassArgs>(srv, srv->t_pass);
+                b.items = items + spans[l0 + g].first;
+                b.nitems = (int)is.pass[g].size();
+                b.mode = m;
+                b.flags = flags;
+                const int grid = (int)std::min<size_t>(is.pass[g].size(), (size_t)nsm * 2);
+                r = launch_pass_lowd_batch(b, groups[g].prec, groups[g].d, grid, groups[g].smem, srv->s_small);
+            }
+            return r;
+        };
         if (with_prep && !is.prep.empty()) {
             BatchPrep p;
             p.args = tb<PrepArgs>(srv, srv->t_prep);
@@ -437,21 +465,8 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
             p.nitems = (int)is.prep.size();
             e = launch_prep_batch(p, srv->s_small);
         }
-        for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
-            if (is.pass[g].empty()) continue;
-            BatchPass b;
-            b.args = tb<PassArgs>(srv, srv->t_pass);
-            b.items = items + spans[l0 + g].first;
-            b.nitems = (int)is.pass[g].size();
-            b.mode = mode;
-            b.flags = flags;
-            const int grid = (int)std::min<size_t>(is.pass[g].size(), (size_t)nsm * 2);
-            e = launch_pass_lowd_batch(b, groups[g].prec, groups[g].d, grid, groups[g].smem, srv->s_small);
-            if (e == cudaSuccess && mode == MODE_TRIAL) {
-                b.mode = MODE_REVERT;
-                e = launch_pass_lowd_batch(b, groups[g].prec, groups[g].d, grid, groups[g].smem, srv->s_small);
-            }
-        }
+        if (e == cudaSuccess) e = passes(mode);
+        if (e == cudaSuccess && mode == MODE_TRIAL) e = passes(MODE_REVERT);
         if (e == cudaSuccess && with_fin && !is.fin.empty()) {
             BatchFin f;
             f.args = tb<FinArgs>(srv, srv->t_fin);
@@ -477,8 +492,7 @@ kmeans_status server_step(kmeans_server* srv, int32_t* done_now)
         }
         return e;
     };
-    // In the body, each group's TRIAL pass is followed by its REVERT pass: an instance's revert
-    // only has to follow its own trial, which the per-group order keeps.
+    // Every pass mode runs over all groups (after the bounds' prep) before the next mode starts.
     KS_CUDA(run(pro, MODE_INIT, F_ASSIGN | F_BINS | F_ENERGY | F_CHECK, true, true, false));
     KS_CUDA(run(body, MODE_TRIAL, F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED, true, false, false));
     if (!J.empty() || !A.empty()) {
@@ -630,7 +644,8 @@ kmeans_status kmeans_server_submit(kmeans_server* srv, const kmeans_data* Xh, in
         return sfail(srv, KM_EINVAL, "d > 16 needs KM_BF16_F32 and a large lane");
     if (cudaSetDevice(srv->ctx->device) != cudaSuccess) return sfail(srv, KM_ECUDA, "cudaSetDevice");
     const int prec = r.large ? KM_BF16_F32 : (Xh->prec == KM_F64 ? KM_F64 : KM_F32);
-    if ((s = make_plan(srv->ctx, Xh->N, Xh->d, K, prec, r.p.lloyd_only ? 0 : r.p.m_max, false, r.P)) != KM_OK)
+    if ((s = make_plan(srv->ctx, Xh->N, Xh->d, K, prec, r.p.lloyd_only ? 0 : r.p.m_max, false, r.P, true, true)) !=
+        KM_OK)
         return sfail(srv, s, srv->ctx->err);
     r.bytes = request_bytes(r);
     if (r.bytes > srv->alloc.cap()) return sfail(srv, KM_ENOMEM, "request larger than the server's HBM budget");

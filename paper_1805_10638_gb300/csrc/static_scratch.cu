@@ -59,7 +59,7 @@ extern "C" kmeans_status kmeans_update_static(const kmeans_data* X, const int32_
     if (X->prec != KM_F64 && X->prec != KM_F32 && X->prec != KM_BF16_F32) return KM_EINVAL;
     const int d = X->d, prec = X->prec == KM_F64 ? KM_F64 : KM_F32;
     const size_t esz = prec == KM_F64 ? 8 : 4;
-    const int Kpad = (K + CH - 1) / CH * CH;
+    const int Kpad = (K + KPAD_ALIGN - 1) / KPAD_ALIGN * KPAD_ALIGN;
     const size_t smem = pass_lowd_smem(prec, d, K, Kpad, true);
     if (smem > (size_t)LOWD_SMEM_MAX) return KM_EINVAL;   // K*d too large for the per-warp shared-memory bins
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);

@@ -122,6 +122,7 @@ __device__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, do
                 inv[k] = r;
 #pragma unroll
                 for (int j = k + 1; j < MB; ++j) {
+                    if (j >= mt) break;          // uniform: no FP64 issue for columns past the history
                     const double ljk = __shfl_sync(FULL, m[k], j);
                     if (lane >= j && lane < mt) m[j] -= m[k] * ljk;
                 }
@@ -226,12 +227,22 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
 
     // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
     // block size) each element goes straight to s_tot; s_part holds only 2*FIN_THREADS entries.
+    // FP32 solver passes after the first leave 64-bit fixed-point partials (scale 2^st->fx_s):
+    // their integer sums are exact, scaled to FP64 once.
+    const bool fxp = a.part_fx && solver && a.mode != MODE_INIT;
+    const int fxs = fxp ? st->fx_s : 0;
     if (split == 1) {
         for (int e = tid; e < E; e += blockDim.x) {
             double acc = 0.0;
             if (e < kb * d) {
                 const size_t off = (size_t)j0 * d + e;
-                if (a.part_f64) {
+                if (fxp) {
+                    const long long* pS = reinterpret_cast<const long long*>(a.pS);
+                    long long is = 0;
+#pragma unroll 8
+                    for (int b = 0; b < nb; ++b) is += pS[(size_t)b * K * d + off];
+                    acc = ldexp((double)is, -fxs);
+                } else if (a.part_f64) {
                     const double* pS = reinterpret_cast<const double*>(a.pS);
 #pragma unroll 8
                     for (int b = 0; b < nb; ++b) acc += pS[(size_t)b * K * d + off];
@@ -255,7 +266,13 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
         double acc = 0.0;
         if (e < kb * d) {
             const size_t off = (size_t)j0 * d + e;
-            if (a.part_f64) {
+            if (fxp) {
+                const long long* pS = reinterpret_cast<const long long*>(a.pS);
+                long long is = 0;
+#pragma unroll 8
+                for (int b = sp; b < nb; b += split) is += pS[(size_t)b * K * d + off];
+                acc = ldexp((double)is, -fxs);
+            } else if (a.part_f64) {
                 const double* pS = reinterpret_cast<const double*>(a.pS);
 #pragma unroll 8
                 for (int b = sp; b < nb; b += split) acc += pS[(size_t)b * K * d + off];
@@ -355,21 +372,26 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
                 bv[s] += col[s] * Fe;
             }
         }
+        // only the warps that hold elements reduce (FP64 is slow on this part: every warp-wide
+        // FP64 instruction counts, whatever its active lanes)
+        const int nwa = min(nw, (kb * d + 31) / 32);
+        if (warp < nwa) {
 #pragma unroll
-        for (int s = 0; s < MMAX; ++s) {
-            if (s < nage) {
-                const double g = warp_sum(gv[s]);
-                const double b = warp_sum(bv[s]);
-                if (lane == 0) {
-                    s_red[(2 * s) * 8 + warp] = g;
-                    s_red[(2 * s + 1) * 8 + warp] = b;
+            for (int s = 0; s < MMAX; ++s) {
+                if (s < nage) {
+                    const double g = warp_sum(gv[s]);
+                    const double b = warp_sum(bv[s]);
+                    if (lane == 0) {
+                        s_red[(2 * s) * 8 + warp] = g;
+                        s_red[(2 * s + 1) * 8 + warp] = b;
+                    }
                 }
             }
         }
         __syncthreads();
         for (int v = tid; v < 2 * nage; v += blockDim.x) {
             double acc = 0.0;
-            for (int w = 0; w < nw; ++w) acc += s_red[v * 8 + w];
+            for (int w = 0; w < nwa; ++w) acc += s_red[v * 8 + w];
             a.pDots[(size_t)bid * DOTS + v] = acc;
         }
     }

@@ -23,6 +23,10 @@ constexpr int KPAD_ALIGN = 16;      // K padded to a multiple of this for the lo
 constexpr int LOWD_THREADS = 256;   // threads per block of the low-d pass kernel
 constexpr int FIN_THREADS = 256;    // threads per block of the update/finalize kernel
 constexpr int DOTS = 2 * MMAX;      // per-block dot partials: Gram row + right-hand side
+// FP32 solver passes with d <= FX_MAX_D sum the update in per-block 64-bit fixed point: an exact,
+// order-independent add that beats per-warp bins there; with more dimensions the d conversions and
+// 64-bit shared-memory adds per sample cost more than the per-warp bins.
+constexpr int FX_MAX_D = 4;
 constexpr int LOWD_SMEM_MAX = 227 * 1024;   // opt-in dynamic shared memory per block on sm_103a
 constexpr int SM_SMEM = 228 * 1024;         // shared memory per SM
 
@@ -66,6 +70,8 @@ struct SolveState {
     long long n_changed;
     long long rescored;
     long long scanned;    // rows scanned over all K, summed over the assignment passes
+    float xmax;           // max |x_ik| over the samples (FP32 path, set by the INIT pass)
+    int fx_s;             // scale 2^fx_s of the last pass's fixed-point residual sums (FP32 path)
     double E_prev;    // stored E^{t-1}
     double E_prev2;   // stored E^{t-2}
     double E_trial;   // E(P^t, C^t) of the proposed iterate
@@ -150,6 +156,7 @@ struct FinArgs {
     const void* pS;       // [nb][K][d]
     const int32_t* pCnt;  // [nb][K]
     int KB;               // centroids per block
+    int part_fx;          // FP32 solver: TRIAL / REVERT partials are int64 fixed point (scale st->fx_s)
     // standalone update
     const void* C_ref;    // reference centroids of the residuals (C_prev), element type T
     void* C_out;          // [K][d] element type T

@@ -31,13 +31,13 @@ namespace km {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_hprep(PassArgs a, int mode)
+__global__ void __launch_bounds__(1024) k_hprep(PassArgs a, int mode)
 {
     __shared__ float s_r[3 * 32];
     hprep_dispatch(a, mode, s_r);
 }
 
-__global__ void __launch_bounds__(256) k_hprep_batch(BatchPass b)
+__global__ void __launch_bounds__(1024) k_hprep_batch(BatchPass b)
 {
     __shared__ float s_r[3 * 32];
     for (int it = blockIdx.x; it < b.nitems; it += gridDim.x) {
@@ -51,13 +51,13 @@ __global__ void __launch_bounds__(256) k_hprep_batch(BatchPass b)
 
 cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s)
 {
-    k_hprep<<<1, 256, 0, s>>>(a, mode);
+    k_hprep<<<1, 1024, 0, s>>>(a, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hprep_batch(const BatchPass& b, int grid, cudaStream_t s)
 {
-    k_hprep_batch<<<grid, 256, 0, s>>>(b);
+    k_hprep_batch<<<grid, 1024, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -38,9 +38,10 @@ struct Shape {
 };
 
 // Resident blocks per SM the compiler must allow (register budget): the FP32 scan with few
-// dimensions is latency-bound at 2 blocks per SM (16 warps), so it is compiled for more.
+// dimensions is latency-bound at 2 blocks per SM (16 warps), so it is compiled for 3 (85 registers,
+// no spills up to d = 3; at 4 blocks the 64-register cap spills the bounds and bins code).
 #ifndef KM_LOWD_MINB_SMALL
-#define KM_LOWD_MINB_SMALL 4
+#define KM_LOWD_MINB_SMALL 3
 #endif
 #ifndef KM_LOWD_MINB_LARGE
 #define KM_LOWD_MINB_LARGE 2
@@ -66,7 +67,10 @@ __host__ __device__ constexpr int rec_stride() { return rec_stride_of(D); }
 
 // hq_cap > 0 (FP32 passes with Hamerly bounds): centroid drifts, half distances to the nearest other
 // centroid, drift maxima and the queue of rows that need a full scan.
-__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins, int hq_cap = 0)
+// bins: the per-cluster residual sums of the update.  Per warp in the element type (sums combined in
+// a fixed order), or with fx, once per block as 64-bit fixed point (exact, order-independent adds).
+__host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins, int hq_cap = 0,
+                                         bool fx = false)
 {
     const size_t esz = f32 ? 4 : 8;
     Layout L;
@@ -83,7 +87,10 @@ __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpa
         L.c = o;   o += al16((size_t)K * D * 8);
     }
     L.stage = o; o += al16((size_t)W * 32 * D * esz);
-    if (bins) {
+    if (bins && fx) {
+        L.bS = o; o += al16((size_t)K * D * 8);
+        L.bC = o; o += al16((size_t)K * 4);
+    } else if (bins) {
         L.bS = o; o += al16((size_t)W * K * D * esz);
         L.bC = o; o += al16((size_t)W * K * 4);
     } else {
@@ -324,39 +331,51 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
     __syncthreads();
     float m1 = 0.f, m2 = 0.f;
     int i1 = -1;
-    for (int j = tid; j < K; j += blockDim.x) {
+    // tpj consecutive lanes share a centroid j and split the j2 range (1, 2 or 4 of them).  The trip
+    // count of the loop is the same for every thread (lanes past K compute nothing) because the
+    // lanes of a centroid combine their minima with warp shuffles.
+    const int tpj = blockDim.x >= 4 * K ? 4 : (blockDim.x >= 2 * K ? 2 : 1);
+    const int sub = tid % tpj, per = blockDim.x / tpj;
+    for (int jb = 0; jb < K; jb += per) {
+        const int j = jb + tid / tpj;
+        const bool valid = j < K;
+        const int jc = valid ? j : 0;
         float dr = 0.f;
         if (have_last) {
             float dd = 0.f;
             for (int k = 0; k < d; ++k) {
-                const float t = cs[j * d + k] - cl[j * d + k];
+                const float t = cs[jc * d + k] - cl[jc * d + k];
                 dd = fmaf(t, t, dd);
             }
             dr = sqrtf(dd) * (1.f + 1e-5f) + eta;
         }
-        a.hdr[j] = dr;
-        if (dr > m1) {
-            m2 = m1;
-            m1 = dr;
-            i1 = j;
-        } else if (dr > m2) {
-            m2 = dr;
+        if (valid && sub == 0) {
+            a.hdr[j] = dr;
+            if (dr > m1) {
+                m2 = m1;
+                m1 = dr;
+                i1 = j;
+            } else if (dr > m2) {
+                m2 = dr;
+            }
         }
         float cj[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) cj[k] = cs[j * d + k];
+        for (int k = 0; k < D; ++k) cj[k] = cs[jc * d + k];
         float mn = __int_as_float(0x7f800000);
 #pragma unroll 4
-        for (int j2 = 0; j2 < K; ++j2) {
+        for (int j2 = sub; j2 < K; j2 += tpj) {
             float dd = 0.f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const float t = cj[k] - __ldg(cs + j2 * d + k);
                 dd = fmaf(t, t, dd);
             }
-            mn = j2 == j ? mn : fminf(mn, dd);
+            mn = j2 == jc ? mn : fminf(mn, dd);
         }
-        a.hs[j] = fmaxf(0.f, 0.5f * sqrtf(mn) * (1.f - 1e-5f) - eta);
+        if (tpj >= 2) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
+        if (tpj >= 4) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));
+        if (valid && sub == 0) a.hs[j] = fmaxf(0.f, 0.5f * sqrtf(mn) * (1.f - 1e-5f) - eta);
     }
     for (int off = 16; off > 0; off >>= 1) {
         const float om1 = __shfl_xor_sync(0xffffffffu, m1, off), om2 = __shfl_xor_sync(0xffffffffu, m2, off);
@@ -449,7 +468,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     // Hamerly bounds: FP32 solver passes that assign (INIT computes the bounds, TRIAL and REVERT use them)
     const bool ham = F32 && a.ham && do_assign &&
                      (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
-    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0);
+    // the solver's TRIAL / REVERT update sums in 64-bit fixed point (see layout)
+    const bool fx = F32 && D <= FX_MAX_D && do_bins && (a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
+    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0, fx);
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     T* s_stage = reinterpret_cast<T*>(smem + L.stage);
     T* s_bS = reinterpret_cast<T*>(smem + L.bS);
@@ -509,7 +530,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         double* dc = reinterpret_cast<double*>(smem + L.c);
         for (int i = tid; i < K * D; i += blockDim.x) dc[i] = c64[i];
     }
-    if (do_bins) {
+    if (do_bins && fx) {
+        unsigned long long* fb = reinterpret_cast<unsigned long long*>(smem + L.bS);
+        for (int i = tid; i < K * D; i += blockDim.x) fb[i] = 0ull;
+        for (int i = tid; i < K; i += blockDim.x) s_bC[i] = 0;
+    } else if (do_bins) {
         for (int i = tid; i < W * K * D; i += blockDim.x) s_bS[i] = T(0);
         for (int i = tid; i < W * K; i += blockDim.x) s_bC[i] = 0;
     }
@@ -563,6 +588,29 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         }
     }
 
+    // fixed-point scale 2^fx_s: every residual |r_k| <= max|x| + max|c|, so N of them stay below 2^61
+    float fx_f = 0.f;
+    int fx_s = 0;
+    if constexpr (F32) {
+        if (fx) {
+            float cm = 0.f;
+            for (int i = tid; i < K * D; i += blockDim.x) cm = fmaxf(cm, fabsf(reinterpret_cast<const float*>(s_c)[i]));
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(FULL, cm, off));
+            float* fr = reinterpret_cast<float*>(s_red);
+            __syncthreads();
+            if (lane == 0) fr[warp] = cm;
+            __syncthreads();
+            cm = 0.f;
+            for (int w = 0; w < W; ++w) cm = fmaxf(cm, fr[w]);
+            __syncthreads();
+            const double rb = ((double)st->xmax + (double)cm) * (double)a.N;
+            fx_s = rb > 0.0 ? 60 - ilogb(rb) : 0;
+            fx_s = fx_s > 100 ? 100 : (fx_s < -100 ? -100 : fx_s);
+            fx_f = ldexpf(1.f, fx_s);
+        }
+    }
+
     const T* X = reinterpret_cast<const T*>(a.X);
     const int64_t N = a.N;
     const int64_t TT = (int64_t)nblk * blockDim.x;
@@ -576,12 +624,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     int bad = 0;
 
     // Everything after the label is known, for one sample (warp-uniform call).
-    auto finish = [&](int64_t row, bool valid, int idx) {
+    // xr: the sample (global memory or preloaded registers); prev: its previous label, or -2 to
+    // read it here.
+    auto finish_x = [&](int64_t row, bool valid, int idx, const T* xr, int prev) {
         idx = idx < K ? idx : K - 1;           // only reachable with non-finite data
         T res[D];
         T e = T(0);
         if (valid) {
-            const T* xr = X + row * D;
             const T* c = s_c + (size_t)idx * D;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -594,14 +643,22 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 }
             }
             if (do_assign) rho_out[row] = idx;
-            if ((flags & F_CHANGED) && rho_prev) nch += (rho_prev[row] != idx);
+            if ((flags & F_CHANGED) && rho_prev) nch += ((prev == -2 ? rho_prev[row] : prev) != idx);
             if (flags & F_DMIN) reinterpret_cast<T*>(a.dmin)[row] = e;
             eacc += e;
         } else {
 #pragma unroll
             for (int k = 0; k < D; ++k) res[k] = T(0);
         }
-        if (do_bins) {
+        if (do_bins && fx) {
+            if (valid) {
+                unsigned long long* fb = reinterpret_cast<unsigned long long*>(s_bS) + (size_t)idx * D;
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    atomicAdd(fb + k, (unsigned long long)__float2ll_rn((float)res[k] * fx_f));
+                atomicAdd(s_bC + idx, 1);
+            }
+        } else if (do_bins) {
             const int lab = valid ? idx : -1;
             const unsigned mm = __match_any_sync(FULL, lab);
             T* stg = s_stage + (size_t)warp * 32 * D;
@@ -628,10 +685,16 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         }
     };
 
+    auto finish = [&](int64_t row, bool valid, int idx) { finish_x(row, valid, idx, X + row * D, -2); };
+
+    float xabs = 0.f;   // INIT pass (FP32 solver): max |x_ik| seen by this thread
     auto check = [&](const T* xr) {
         if (flags & F_CHECK) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) bad |= !isfinite(xr[k]);
+            for (int k = 0; k < D; ++k) {
+                bad |= !isfinite(xr[k]);
+                if constexpr (F32) xabs = fmaxf(xabs, fabsf((float)xr[k]));
+            }
         }
     };
 
@@ -665,36 +728,52 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 // full scan would return the same label) keep it; the others are queued
                 const bool force = a.mode == MODE_INIT;
                 const int32_t* rho_last = a.mode == MODE_TRIAL ? rho_prev : rho_out;
-                for (int64_t q = 0; q < n_g; ++q) {
-                    const int64_t row = g + q * TT;
-                    const float* xr = X + row * D;
-                    check(xr);
-                    bool scan = force;
-                    if (!force) {
-                        const int al = rho_last[row];
-                        float u = (a.hub[row] + s_hdr[al]) * (1.f + 2e-7f);
-                        const float l = fmaxf(0.f, (a.hlb[row] - (al == h_am ? h_dm2 : h_dm1)) * (1.f - 2e-7f));
-                        const float m = fmaxf(l, s_hs[al]);
-                        if (!(u * (1.f + 1e-5f) < m)) {
-                            const float* c = reinterpret_cast<const float*>(s_c) + (size_t)al * D;
-                            float dd = 0.f;
+                constexpr int HB = 4;             // rows per thread whose loads are issued together
+                for (int64_t q0 = 0; q0 < n_g; q0 += HB) {
+                    int al[HB];
+                    float ub[HB], lb[HB], xv[HB][D];
 #pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                const float t = xr[k] - c[k];
-                                dd = fmaf(t, t, dd);
-                            }
-                            u = sqrtf(dd) * (1.f + 1e-5f) + h_eta;
-                            scan = !(u * (1.f + 1e-5f) < m);
-                        }
-                        if (!scan) {
-                            rho_out[row] = al;
-                            a.hub[row] = u;
-                            a.hlb[row] = l;
-                        }
+                    for (int r = 0; r < HB; ++r) {
+                        const bool v = q0 + r < n_g;
+                        const int64_t row = g + (v ? q0 + r : q0) * TT;
+                        al[r] = force ? 0 : rho_last[row];
+                        ub[r] = force ? 0.f : a.hub[row];
+                        lb[r] = force ? 0.f : a.hlb[row];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) xv[r][k] = X[row * D + k];
                     }
-                    if (scan) {
-                        s_hq[atomicAdd(s_hqn, 1u)] = (uint32_t)row;
-                        nscan += 1;
+#pragma unroll
+                    for (int r = 0; r < HB; ++r) {
+                        if (q0 + r >= n_g) break;
+                        const int64_t row = g + (q0 + r) * TT;
+                        check(xv[r]);
+                        bool scan = force;
+                        if (!force) {
+                            const int a_ = al[r];
+                            float u = (ub[r] + s_hdr[a_]) * (1.f + 2e-7f);
+                            const float l = fmaxf(0.f, (lb[r] - (a_ == h_am ? h_dm2 : h_dm1)) * (1.f - 2e-7f));
+                            const float m = fmaxf(l, s_hs[a_]);
+                            if (!(u * (1.f + 1e-5f) < m)) {
+                                const float* c = reinterpret_cast<const float*>(s_c) + (size_t)a_ * D;
+                                float dd = 0.f;
+#pragma unroll
+                                for (int k = 0; k < D; ++k) {
+                                    const float t = xv[r][k] - c[k];
+                                    dd = fmaf(t, t, dd);
+                                }
+                                u = sqrtf(dd) * (1.f + 1e-5f) + h_eta;
+                                scan = !(u * (1.f + 1e-5f) < m);
+                            }
+                            if (!scan) {
+                                rho_out[row] = a_;
+                                a.hub[row] = u;
+                                a.hlb[row] = l;
+                            }
+                        }
+                        if (scan) {
+                            s_hq[atomicAdd(s_hqn, 1u)] = (uint32_t)row;
+                            nscan += 1;
+                        }
                     }
                 }
                 __syncthreads();
@@ -770,10 +849,24 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 __syncthreads();
                 // phase C: the rest of the pass in the same per-thread row order as without bounds,
                 // so the update's sums come out bitwise the same
-                for (int64_t q = 0; q < n_max; ++q) {
-                    const bool valid = q < n_g;
-                    const int64_t row = valid ? g + q * TT : 0;
-                    finish(row, valid, valid ? rho_out[row] : 0);
+                for (int64_t q0 = 0; q0 < n_max; q0 += HB) {
+                    int lab[HB], prv[HB];
+                    float xv[HB][D];
+#pragma unroll
+                    for (int r = 0; r < HB; ++r) {
+                        const bool v = q0 + r < n_g;
+                        const int64_t row = v ? g + (q0 + r) * TT : 0;
+                        lab[r] = v ? rho_out[row] : 0;
+                        prv[r] = (v && (flags & F_CHANGED) && rho_prev) ? rho_prev[row] : -1;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) xv[r][k] = X[row * D + k];
+                    }
+#pragma unroll
+                    for (int r = 0; r < HB; ++r) {
+                        if (q0 + r >= n_max) break;
+                        const bool v = q0 + r < n_g;
+                        finish_x(v ? g + (q0 + r) * TT : 0, v, lab[r], xv[r], prv[r]);
+                    }
                 }
                 kk = n_max;
             }
@@ -893,7 +986,21 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         if (a.pScan) a.pScan[bid] = nb_sc;
         a.pBad[bid] = (int)(nb_bad != 0);
     }
-    if (do_bins) {
+    if constexpr (F32) {
+        if ((flags & F_CHECK) && a.mode == MODE_INIT) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) xabs = fmaxf(xabs, __shfl_xor_sync(FULL, xabs, off));
+            if (lane == 0 && isfinite(xabs)) atomicMax(reinterpret_cast<int*>(&st->xmax), __float_as_int(xabs));
+        }
+    }
+    if (do_bins && fx) {
+        __syncthreads();
+        const long long* fb = reinterpret_cast<const long long*>(s_bS);
+        long long* pS = reinterpret_cast<long long*>(a.pS) + (size_t)bid * K * D;
+        for (int e = tid; e < K * D; e += blockDim.x) pS[e] = fb[e];
+        int32_t* pC = a.pCnt + (size_t)bid * K;
+        for (int j = tid; j < K; j += blockDim.x) pC[j] = s_bC[j];
+    } else if (do_bins) {
         __syncthreads();
         T* pS = reinterpret_cast<T*>(a.pS) + (size_t)bid * K * D;
         for (int e = tid; e < K * D; e += blockDim.x) {
@@ -944,6 +1051,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         } else {
             st->rescored += rs;
             st->scanned += sc;
+            if (fx) st->fx_s = fx_s;
             if (a.mode == MODE_EPI) {
                 st->E_final = E;
             } else if (a.mode == MODE_INIT) {

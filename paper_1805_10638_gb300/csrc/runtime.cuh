@@ -269,7 +269,7 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.c32_0 = take(n * 4);
     P.c32_1 = take(n * 4);
     P.origin = take(64 * 4);
-    P.pS = take((size_t)P.nb * n * esz);
+    P.pS = take((size_t)P.nb * n * 8);       // FP64 bins, or FP32 bins / 64-bit fixed point (FP32 path)
     P.pCnt = take((size_t)P.nb * K * 4);
     P.pE = take((size_t)P.nb * 8);
     P.pNch = take((size_t)P.nb * 8);
@@ -386,8 +386,10 @@ inline int smem_class(size_t smem)
     return c < 1 ? 1 : (c > 4 ? 4 : c);
 }
 
-// The accelerated iterate is formed inside k_fin's last block when K*d is small (saves a launch).
-inline bool fuse_mix_rule(int K, int d) { return K <= 1024 && (size_t)K * d <= 16384; }
+// The accelerated iterate could be formed inside k_fin's last block (saving a launch), but FP64 is
+// slow on this part (a few FP64 lanes per SM per cycle), so one block's mix over all K*d elements
+// costs more than a launch of k_mix, which spreads it over K/8 blocks: only tiny problems fuse.
+inline bool fuse_mix_rule(int K, int d) { return (size_t)K * d <= 64; }
 
 // Everything one solve launches, resolved to device pointers once.
 struct Launch {
@@ -561,6 +563,7 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     fa.lloyd_only = p.lloyd_only;
     fa.rank_tol = p.rank_tol;
     fa.fuse_mix = fuse_mix_rule(K, d) ? 1 : 0;
+    fa.part_fx = (!L.f64 && d <= FX_MAX_D) ? 1 : 0;
     fa.DP = P.DP;
     fa.fp32_path = !L.f64;
     fa.origin = at<float>(base, P.origin);
@@ -591,6 +594,7 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     L.X32 = reinterpret_cast<const float*>(X->X);
     if (P.dense) {
         fa.part_f64 = 1;                 // S: FP64 residual sums per cluster, one "partial block"
+        fa.part_fx = 0;
         fa.fuse_mix = 0;
         fa.fp32_path = 0;
         ma.fp32_path = 0;                // the mix only writes C; the BF16 packing is separate

@@ -34,7 +34,7 @@ __device__ __forceinline__ double warp_sum(double v)
 // owning row r, with 1/L_kk from rsqrt (no divisions); columns from the first with
 // L_kk <= rank_tol * L_00 on are dropped.  Forward and back substitution give theta.
 // Returns the rank (in every lane); theta[0..MMAX) in shared memory.
-__device__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
+__device__ __forceinline__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
                        double* sInv, double* sV)
 {
     const int lane = threadIdx.x & 31;
@@ -90,15 +90,15 @@ __device__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double
 // the rank-1 updates of a column are independent FMAs instead of a chain through shared memory.
 // Every FP64 operation and its order match ls_warp, so the results are bitwise the same.
 template <int MB>
-__device__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
+__device__ __forceinline__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
                            double* sV)
 {
     const int lane = threadIdx.x & 31;
-    const int sr = lane < mt ? (hnew - lane + m_max) % m_max : 0;
+    const int sr = lane < mt ? (hnew >= lane ? hnew - lane : hnew - lane + m_max) : 0;   // mt <= m_max
     double m[MB];
 #pragma unroll
     for (int c = 0; c < MB; ++c) {
-        const int sc = (hnew - c + m_max) % m_max;
+        const int sc = hnew >= c ? hnew - c : hnew - c + m_max;
         m[c] = (lane < mt && c < mt) ? st->gram[sr * MMAX + sc] : 0.0;
     }
     double v = lane < mt ? st->bvec[sr] : 0.0;
@@ -127,15 +127,11 @@ __device__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, do
                     if (lane >= j && lane < mt) m[j] -= m[k] * ljk;
                 }
                 rank = k + 1;
+                // L y = b, step k, as soon as column k is final (off the pivot chain)
+                const double yk = __shfl_sync(FULL, v, k) * inv[k];
+                if (lane == k) v = yk;
+                if (lane > k && lane < mt) v -= m[k] * yk;
             }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < MB; ++k) {             // L y = b
-        if (k < rank) {
-            const double yk = __shfl_sync(FULL, v, k) * inv[k];
-            if (lane == k) v = yk;
-            if (lane > k && lane < rank) v -= m[k] * yk;
         }
     }
 #pragma unroll
@@ -199,6 +195,25 @@ __device__ void mix_pack_centroid(int j, int K, int d, int DP, int fp32_path, do
     }
 }
 
+// sum_{b = b0, b0 + step, ... < nb} p[b * stride] in that order, 16 loads in flight (predicated,
+// so a short tail costs no serial round trips).
+template <typename V, typename Acc>
+__device__ __forceinline__ Acc strided_sum(const V* p, size_t stride, int b0, int nb, int step)
+{
+    Acc acc = Acc(0);
+    for (int b = b0; b < nb; b += 16 * step) {
+        V v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int bb = b + u * step;
+            v[u] = bb < nb ? p[(size_t)bb * stride] : V(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc += (Acc)v[u];
+    }
+    return acc;
+}
+
 // The work of block `bid` of a finalize launch with `nblk` blocks (see k_fin / k_fin_batch).
 __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const int nblk, unsigned char* smem)
 {
@@ -227,74 +242,45 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
 
     // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
     // block size) each element goes straight to s_tot; s_part holds only 2*FIN_THREADS entries.
-    // FP32 solver passes after the first leave 64-bit fixed-point partials (scale 2^st->fx_s):
-    // their integer sums are exact, scaled to FP64 once.
+    // FP32 solver passes after the first (d <= FX_MAX_D) leave 64-bit fixed-point partials (scale
+    // 2^st->fx_s): they and the counts are summed as integers at both levels (exact, so the split
+    // does not matter) and converted to FP64 once.
     const bool fxp = a.part_fx && solver && a.mode != MODE_INIT;
     const int fxs = fxp ? st->fx_s : 0;
-    if (split == 1) {
-        for (int e = tid; e < E; e += blockDim.x) {
-            double acc = 0.0;
-            if (e < kb * d) {
-                const size_t off = (size_t)j0 * d + e;
-                if (fxp) {
-                    const long long* pS = reinterpret_cast<const long long*>(a.pS);
-                    long long is = 0;
-#pragma unroll 8
-                    for (int b = 0; b < nb; ++b) is += pS[(size_t)b * K * d + off];
-                    acc = ldexp((double)is, -fxs);
-                } else if (a.part_f64) {
-                    const double* pS = reinterpret_cast<const double*>(a.pS);
-#pragma unroll 8
-                    for (int b = 0; b < nb; ++b) acc += pS[(size_t)b * K * d + off];
-                } else {
-                    const float* pS = reinterpret_cast<const float*>(a.pS);
-#pragma unroll 8
-                    for (int b = 0; b < nb; ++b) acc += (double)pS[(size_t)b * K * d + off];
-                }
-            } else {
-                const int j = j0 + (e - kb * d);
-                long long c = 0;
-#pragma unroll 8
-                for (int b = 0; b < nb; ++b) c += a.pCnt[(size_t)b * K + j];
-                acc = (double)c;
-            }
-            s_tot[e] = acc;
-        }
-    }
-    for (int p = tid; split > 1 && p < E * split; p += blockDim.x) {
-        const int e = p / split, sp = p % split;
+    long long* s_ipart = reinterpret_cast<long long*>(s_part);
+    const size_t Kd = (size_t)K * d;
+    // (e, sp): element e, blocks sp, sp + split, ...; split == 1 writes s_tot directly
+    for (int p = tid; p < E * split; p += blockDim.x) {
+        const int e = p / split, sp = p - e * split;
+        const bool isum = e >= kb * d || fxp;          // integer sum
+        long long is = 0;
         double acc = 0.0;
         if (e < kb * d) {
             const size_t off = (size_t)j0 * d + e;
-            if (fxp) {
-                const long long* pS = reinterpret_cast<const long long*>(a.pS);
-                long long is = 0;
-#pragma unroll 8
-                for (int b = sp; b < nb; b += split) is += pS[(size_t)b * K * d + off];
-                acc = ldexp((double)is, -fxs);
-            } else if (a.part_f64) {
-                const double* pS = reinterpret_cast<const double*>(a.pS);
-#pragma unroll 8
-                for (int b = sp; b < nb; b += split) acc += pS[(size_t)b * K * d + off];
-            } else {
-                const float* pS = reinterpret_cast<const float*>(a.pS);
-#pragma unroll 8
-                for (int b = sp; b < nb; b += split) acc += (double)pS[(size_t)b * K * d + off];
-            }
+            if (fxp) is = strided_sum<long long, long long>(reinterpret_cast<const long long*>(a.pS) + off, Kd, sp, nb, split);
+            else if (a.part_f64) acc = strided_sum<double, double>(reinterpret_cast<const double*>(a.pS) + off, Kd, sp, nb, split);
+            else acc = strided_sum<float, double>(reinterpret_cast<const float*>(a.pS) + off, Kd, sp, nb, split);
         } else {
-            const int j = j0 + (e - kb * d);
-            long long c = 0;
-#pragma unroll 8
-            for (int b = sp; b < nb; b += split) c += a.pCnt[(size_t)b * K + j];
-            acc = (double)c;
+            is = strided_sum<int32_t, long long>(a.pCnt + j0 + (e - kb * d), (size_t)K, sp, nb, split);
         }
-        s_part[p] = acc;
+        if (split == 1)
+            s_tot[e] = !isum ? acc : (e >= kb * d ? (double)is : ldexp((double)is, -fxs));
+        else if (isum)
+            s_ipart[p] = is;
+        else
+            s_part[p] = acc;
     }
     __syncthreads();
     for (int e = tid; split > 1 && e < E; e += blockDim.x) {
-        double v = 0.0;
-        for (int sp = 0; sp < split; ++sp) v += s_part[e * split + sp];
-        s_tot[e] = v;
+        if (e >= kb * d || fxp) {
+            long long v = 0;
+            for (int sp = 0; sp < split; ++sp) v += s_ipart[e * split + sp];
+            s_tot[e] = e >= kb * d ? (double)v : ldexp((double)v, -fxs);
+        } else {
+            double v = 0.0;
+            for (int sp = 0; sp < split; ++sp) v += s_part[e * split + sp];
+            s_tot[e] = v;
+        }
     }
     __syncthreads();
     // 1/N_j once per centroid
@@ -348,51 +334,52 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
     }
     __syncthreads();
 
-    // ---- dot partials: age 0 = the new column, age s >= 1 = slot (head - s + 1)
-    const int nw = blockDim.x >> 5;
+    // ---- dot partials of this block's elements: age 0 = the new column, age s >= 1 = ring slot
+    // (head - s + 1).  Each age gets a group of G = FIN_THREADS / A threads (A = nage rounded up to
+    // a power of two); a group's threads take the elements r, r + G, ... and the group is reduced
+    // by shuffles within its warp and, when it spans several warps, through shared memory in warp
+    // order.  Every product is formed once, and every FP64 instruction does useful work in most
+    // lanes: FP64 issue is scarce on this part.
     const int nage = ring ? nold + 1 : 0;
     if (ring) {
-        double gv[MMAX], bv[MMAX];
-#pragma unroll
-        for (int s = 0; s < MMAX; ++s) gv[s] = bv[s] = 0.0;
-        for (int e = tid; e < kb * d; e += blockDim.x) {
-            const size_t i = (size_t)j0 * d + e;
-            const double dfn = s_dfn[e], Fe = s_F[e];
-            double col[MMAX];
-#pragma unroll
-            for (int s = 1; s < MMAX; ++s) {
-                const int q = (head - (s - 1) + m_max) % m_max;
-                col[s] = s < nage ? a.dF[(size_t)q * n + i] : 0.0;
-            }
-            gv[0] += dfn * dfn;
-            bv[0] += dfn * Fe;
-#pragma unroll
-            for (int s = 1; s < MMAX; ++s) {
-                gv[s] += dfn * col[s];
-                bv[s] += col[s] * Fe;
+        int A = 1;
+        while (A < nage) A <<= 1;
+        const int G = FIN_THREADS / A;
+        const int s = tid / G, r = tid - s * G;
+        double g = 0.0, bb = 0.0;
+        if (s < nage) {
+            const double* col = s == 0 ? s_dfn
+                                       : a.dF + (size_t)((head - (s - 1) + m_max) % m_max) * n + (size_t)j0 * d;
+#pragma unroll 4
+            for (int e = r; e < kb * d; e += G) {
+                const double c = col[e];
+                g = fma(s_dfn[e], c, g);
+                bb = fma(c, s_F[e], bb);
             }
         }
-        // only the warps that hold elements reduce (FP64 is slow on this part: every warp-wide
-        // FP64 instruction counts, whatever its active lanes)
-        const int nwa = min(nw, (kb * d + 31) / 32);
-        if (warp < nwa) {
-#pragma unroll
-            for (int s = 0; s < MMAX; ++s) {
-                if (s < nage) {
-                    const double g = warp_sum(gv[s]);
-                    const double b = warp_sum(bv[s]);
-                    if (lane == 0) {
-                        s_red[(2 * s) * 8 + warp] = g;
-                        s_red[(2 * s + 1) * 8 + warp] = b;
-                    }
-                }
-            }
+        const int Wg = G < 32 ? G : 32;
+        for (int off = Wg >> 1; off > 0; off >>= 1) {
+            g += __shfl_xor_sync(FULL, g, off);
+            bb += __shfl_xor_sync(FULL, bb, off);
         }
-        __syncthreads();
-        for (int v = tid; v < 2 * nage; v += blockDim.x) {
-            double acc = 0.0;
-            for (int w = 0; w < nwa; ++w) acc += s_red[v * 8 + w];
-            a.pDots[(size_t)bid * DOTS + v] = acc;
+        if (G <= 32) {
+            if (r == 0 && s < nage) {
+                a.pDots[(size_t)bid * DOTS + 2 * s] = g;
+                a.pDots[(size_t)bid * DOTS + 2 * s + 1] = bb;
+            }
+        } else {
+            if (lane == 0) {
+                s_red[2 * warp] = g;
+                s_red[2 * warp + 1] = bb;
+            }
+            __syncthreads();
+            const int wpa = G / 32;
+            if (tid < 2 * nage) {
+                const int s2 = tid >> 1, which = tid & 1;
+                double acc = 0.0;
+                for (int w = 0; w < wpa; ++w) acc += s_red[2 * (s2 * wpa + w) + which];
+                a.pDots[(size_t)bid * DOTS + tid] = acc;
+            }
         }
     }
 

@@ -242,35 +242,41 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
 
     // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
     // block size) each element goes straight to s_tot; s_part holds only 2*FIN_THREADS entries.
-    // FP32 solver passes after the first (d <= FX_MAX_D) leave 64-bit fixed-point partials (scale
-    // 2^st->fx_s): they and the counts are summed as integers at both levels (exact, so the split
-    // does not matter) and converted to FP64 once.
-    const bool fxp = a.part_fx && solver && a.mode != MODE_INIT;
+    // FP32 solver passes after the first (d <= FX_MAX_D) sum in 64-bit fixed point (scale
+    // 2^st->fx_s) straight into the totals acc / accC: read once, converted to FP64 once, and
+    // cleared for the next pass.  Counts of the other passes are summed as integers.
+    const bool fxp = a.part_fx && a.acc && solver && a.mode != MODE_INIT;
     const int fxs = fxp ? st->fx_s : 0;
     long long* s_ipart = reinterpret_cast<long long*>(s_part);
     const size_t Kd = (size_t)K * d;
-    // (e, sp): element e, blocks sp, sp + split, ...; split == 1 writes s_tot directly
+    // (e, sp): element e, blocks sp, sp + split, ...; split == 1 writes s_tot directly.  Consecutive
+    // threads take consecutive elements of the same partial block (coalesced loads).
     for (int p = tid; p < E * split; p += blockDim.x) {
-        const int e = p / split, sp = p - e * split;
+        const int sp = p / E, e = p - sp * E;
         const bool isum = e >= kb * d || fxp;          // integer sum
         long long is = 0;
         double acc = 0.0;
         if (e < kb * d) {
             const size_t off = (size_t)j0 * d + e;
-            if (fxp) is = strided_sum<long long, long long>(reinterpret_cast<const long long*>(a.pS) + off, Kd, sp, nb, split);
+            if (fxp) is = sp == 0 ? a.acc[off] : 0;       // the pass's exact total
             else if (a.part_f64) acc = strided_sum<double, double>(reinterpret_cast<const double*>(a.pS) + off, Kd, sp, nb, split);
             else acc = strided_sum<float, double>(reinterpret_cast<const float*>(a.pS) + off, Kd, sp, nb, split);
         } else {
-            is = strided_sum<int32_t, long long>(a.pCnt + j0 + (e - kb * d), (size_t)K, sp, nb, split);
+            const int j = j0 + (e - kb * d);
+            is = fxp ? (sp == 0 ? (long long)a.accC[j] : 0) : strided_sum<int32_t, long long>(a.pCnt + j, (size_t)K, sp, nb, split);
         }
         if (split == 1)
             s_tot[e] = !isum ? acc : (e >= kb * d ? (double)is : ldexp((double)is, -fxs));
         else if (isum)
-            s_ipart[p] = is;
+            s_ipart[e * split + sp] = is;
         else
-            s_part[p] = acc;
+            s_part[e * split + sp] = acc;
     }
     __syncthreads();
+    if (fxp) {                                   // read by this block only: clear for the next pass
+        for (int e = tid; e < kb * d; e += blockDim.x) a.acc[(size_t)j0 * d + e] = 0;
+        for (int e = tid; e < kb; e += blockDim.x) a.accC[j0 + e] = 0;
+    }
     for (int e = tid; split > 1 && e < E; e += blockDim.x) {
         if (e >= kb * d || fxp) {
             long long v = 0;

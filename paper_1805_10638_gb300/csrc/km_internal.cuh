@@ -116,6 +116,12 @@ struct PassArgs {
     long long* pScan;        // rows that went through the full scan over K (may be NULL)
     int* pBad;
     unsigned int* counter;
+    // FP32 solver passes with fixed-point bins (d <= FX_MAX_D): every block adds its int64 bins and
+    // counts into these totals (exact, order-independent) instead of writing block partials.  Zero
+    // between uses: the INIT pass clears them, k_fin clears what it read, and a TRIAL pass whose
+    // safeguard fired clears them for the REVERT pass.  NULL: block partials as usual.
+    long long* acc;          // [K][D]
+    int32_t* accC;           // [K]
     // finalize targets
     SolveState* st;
     long long* out_nch;
@@ -156,7 +162,9 @@ struct FinArgs {
     const void* pS;       // [nb][K][d]
     const int32_t* pCnt;  // [nb][K]
     int KB;               // centroids per block
-    int part_fx;          // FP32 solver: TRIAL / REVERT partials are int64 fixed point (scale st->fx_s)
+    int part_fx;          // FP32 solver: TRIAL / REVERT sums are int64 fixed point (scale st->fx_s)
+    long long* acc;       //   ... accumulated by the pass in acc [K][d] and accC [K] (read, then zeroed)
+    int32_t* accC;
     // standalone update
     const void* C_ref;    // reference centroids of the residuals (C_prev), element type T
     void* C_out;          // [K][d] element type T

@@ -469,7 +469,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     const bool ham = F32 && a.ham && do_assign &&
                      (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
     // the solver's TRIAL / REVERT update sums in 64-bit fixed point (see layout)
-    const bool fx = F32 && D <= FX_MAX_D && do_bins && (a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
+    const bool fx = F32 && D <= FX_MAX_D && do_bins && a.acc != nullptr &&
+                    (a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
     const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0, fx);
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     T* s_stage = reinterpret_cast<T*>(smem + L.stage);
@@ -994,12 +995,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         }
     }
     if (do_bins && fx) {
+        // integer adds into the pass totals: exact, so their order does not matter
         __syncthreads();
         const long long* fb = reinterpret_cast<const long long*>(s_bS);
-        long long* pS = reinterpret_cast<long long*>(a.pS) + (size_t)bid * K * D;
-        for (int e = tid; e < K * D; e += blockDim.x) pS[e] = fb[e];
-        int32_t* pC = a.pCnt + (size_t)bid * K;
-        for (int j = tid; j < K; j += blockDim.x) pC[j] = s_bC[j];
+        unsigned long long* acc = reinterpret_cast<unsigned long long*>(a.acc);
+        for (int e = tid; e < K * D; e += blockDim.x) {
+            const long long v = fb[e];
+            if (v != 0) atomicAdd(acc + e, (unsigned long long)v);
+        }
+        for (int j = tid; j < K; j += blockDim.x) {
+            const int c = s_bC[j];
+            if (c != 0) atomicAdd(a.accC + j, c);
+        }
     } else if (do_bins) {
         __syncthreads();
         T* pS = reinterpret_cast<T*>(a.pS) + (size_t)bid * K * D;
@@ -1027,6 +1034,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     __syncthreads();
     if (*sflag == 0u) return;
     __threadfence();
+    if (a.acc && a.mode == MODE_INIT) {       // the solve's first pass: clear the fixed-point totals
+        for (int i = tid; i < K * D; i += blockDim.x) a.acc[i] = 0;
+        for (int j = tid; j < K; j += blockDim.x) a.accC[j] = 0;
+    }
     double E = 0.0;
     long long ch = 0, rs = 0, bd = 0, sc = 0;
     for (int b = tid; b < nblk; b += blockDim.x) {
@@ -1066,6 +1077,14 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 // the kernel that ends the solve also ends the graph's while loop
                 if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
             }
+        }
+    }
+    // the safeguard fired: the REVERT pass sums into cleared totals
+    if (fx && a.mode == MODE_TRIAL) {
+        __syncthreads();
+        if (st->revert && !st->done) {
+            for (int i = tid; i < K * D; i += blockDim.x) a.acc[i] = 0;
+            for (int j = tid; j < K; j += blockDim.x) a.accC[j] = 0;
         }
     }
     // the safeguard fired: the REVERT pass's bound inputs (drift from C^t, just saved as the last

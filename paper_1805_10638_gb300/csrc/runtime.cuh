@@ -35,7 +35,7 @@ struct GraphKey {
 struct Plan {
     // offsets into the arena
     size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
-    size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info;
+    size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info, acc;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
     size_t cb0, cb1, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
@@ -190,6 +190,7 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.pS = P.S;
     P.pCnt = P.counts;
     P.pE = P.pNch = P.pResc = P.pScan = P.pBad = 0;
+    P.acc = 0;
     P.pDots = take((size_t)P.nfin * DOTS * 8);
     P.info = take(256);
     if (host_copies) {
@@ -276,6 +277,7 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.pResc = take((size_t)P.nb * 8);
     P.pScan = take((size_t)P.nb * 8);
     P.pBad = take((size_t)P.nb * 4);
+    P.acc = (f32 && d <= FX_MAX_D) ? take(n * 8 + (size_t)K * 4) : 0;   // fixed-point totals + counts
     P.pDots = take((size_t)P.nfin * DOTS * 8);
     P.info = take(256);
     if (host_copies) {
@@ -541,6 +543,8 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     pa.hdr = P.ham ? at<float>(base, P.hprep) : nullptr;
     pa.hs = P.ham ? pa.hdr + P.Kpad : nullptr;
     pa.hm = P.ham ? pa.hdr + 2 * P.Kpad : nullptr;
+    pa.acc = P.acc ? at<long long>(base, P.acc) : nullptr;
+    pa.accC = P.acc ? reinterpret_cast<int32_t*>(pa.acc + (size_t)K * d) : nullptr;
 
     FinArgs& fa = L.fa;
     memset(&fa, 0, sizeof(fa));
@@ -563,7 +567,9 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     fa.lloyd_only = p.lloyd_only;
     fa.rank_tol = p.rank_tol;
     fa.fuse_mix = fuse_mix_rule(K, d) ? 1 : 0;
-    fa.part_fx = (!L.f64 && d <= FX_MAX_D) ? 1 : 0;
+    fa.part_fx = pa.acc ? 1 : 0;
+    fa.acc = pa.acc;
+    fa.accC = pa.accC;
     fa.DP = P.DP;
     fa.fp32_path = !L.f64;
     fa.origin = at<float>(base, P.origin);

@@ -31,10 +31,11 @@ namespace km {
 
 namespace {
 
+// Block b of `gridDim.x` takes the half distances of its share of the centroids (hprep_body).
 __global__ void __launch_bounds__(1024) k_hprep(PassArgs a, int mode)
 {
     __shared__ float s_r[3 * 32];
-    hprep_dispatch(a, mode, s_r);
+    hprep_dispatch(a, mode, s_r, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(1024) k_hprep_batch(BatchPass b)
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(1024) k_hprep_batch(BatchPass b)
 
 cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s)
 {
-    k_hprep<<<1, 1024, 0, s>>>(a, mode);
+    const int parts = a.K / 32 < 1 ? 1 : (a.K / 32 > 16 ? 16 : a.K / 32);   // >= 32 centroids per block
+    k_hprep<<<parts, 1024, 0, s>>>(a, mode);
     return cudaGetLastError();
 }
 

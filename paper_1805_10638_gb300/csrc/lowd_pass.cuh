@@ -297,9 +297,12 @@ __device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int
 //   hs[j]  = (min_{j' != j} ||c_j - c_j'|| / 2)(1 - 1e-5) - eta, at least 0
 //   hm     = (largest drift, second largest, index of the largest, eta)
 // with eta = 4e-7 max(||c||, ||c^last||), the allowance for the rounding of the FP32 centroids.
+// Block `part` of `nparts`: every block computes eta, all drifts and their top two (O(K d), so no
+// block waits for another); the half distances, O(K^2 d), are split: block `part` takes the
+// centroids [part*K/nparts, (part+1)*K/nparts).  Block 0 writes hdr and hm.
 template <int D>
-__device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96 floats of block scratch
-{
+__device__ void hprep_body(const PassArgs& a, int mode, float* s_r, int part = 0, int nparts = 1)
+{                                                                     // s_r: 96 floats of block scratch
     const SolveState* st = a.st;
     if (st->done) return;
     int which = 0;
@@ -312,6 +315,7 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
     const float* cs = a.c32[which];
     const float* cl = a.hlast;
     const bool have_last = mode != MODE_INIT;
+    const bool writer = part == 0;
     __syncthreads();      // s_r may be in use by the caller's previous step
     float cm = 0.f;
     for (int j = tid; j < K; j += blockDim.x) {
@@ -325,32 +329,26 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
     for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
     if (lane == 0) s_r[warp] = cm;
     __syncthreads();
-    cm = 0.f;
-    for (int w = 0; w < nw; ++w) cm = fmaxf(cm, s_r[w]);
-    const float eta = 4e-7f * sqrtf(cm) + 1e-30f;
+    if (warp == 0) {
+        cm = lane < nw ? s_r[lane] : 0.f;
+        for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
+        if (lane == 0) s_r[32] = cm;
+    }
     __syncthreads();
+    const float eta = 4e-7f * sqrtf(s_r[32]) + 1e-30f;
+    __syncthreads();
+    // drifts of all centroids and their top two (every block; block 0 writes them)
     float m1 = 0.f, m2 = 0.f;
     int i1 = -1;
-    // tpj consecutive lanes share a centroid j and split the j2 range (1, 2 or 4 of them).  The trip
-    // count of the loop is the same for every thread (lanes past K compute nothing) because the
-    // lanes of a centroid combine their minima with warp shuffles.
-    const int tpj = blockDim.x >= 4 * K ? 4 : (blockDim.x >= 2 * K ? 2 : 1);
-    const int sub = tid % tpj, per = blockDim.x / tpj;
-    for (int jb = 0; jb < K; jb += per) {
-        const int j = jb + tid / tpj;
-        const bool valid = j < K;
-        const int jc = valid ? j : 0;
-        float dr = 0.f;
-        if (have_last) {
+    if (have_last) {
+        for (int j = tid; j < K; j += blockDim.x) {
             float dd = 0.f;
             for (int k = 0; k < d; ++k) {
-                const float t = cs[jc * d + k] - cl[jc * d + k];
+                const float t = cs[j * d + k] - cl[j * d + k];
                 dd = fmaf(t, t, dd);
             }
-            dr = sqrtf(dd) * (1.f + 1e-5f) + eta;
-        }
-        if (valid && sub == 0) {
-            a.hdr[j] = dr;
+            const float dr = sqrtf(dd) * (1.f + 1e-5f) + eta;
+            if (writer) a.hdr[j] = dr;
             if (dr > m1) {
                 m2 = m1;
                 m1 = dr;
@@ -359,6 +357,21 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
                 m2 = dr;
             }
         }
+    } else if (writer) {
+        for (int j = tid; j < K; j += blockDim.x) a.hdr[j] = 0.f;
+    }
+    // half distances of this block's centroids: tpj consecutive lanes share a centroid j and split
+    // the j2 range.  The outer trip count is the same for every thread (lanes past the range compute
+    // nothing) because the lanes of a centroid combine their minima with warp shuffles.
+    const int jlo = (int)((long long)K * part / nparts), jhi = (int)((long long)K * (part + 1) / nparts);
+    const int nj = jhi - jlo;
+    int tpj = 1;
+    while (tpj < 32 && 2 * tpj * nj <= (int)blockDim.x) tpj <<= 1;
+    const int sub = tid % tpj, per = blockDim.x / tpj;
+    for (int jb = 0; jb < nj; jb += per) {
+        const int j = jlo + jb + tid / tpj;
+        const bool valid = j < jhi;
+        const int jc = valid ? j : jlo;
         float cj[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) cj[k] = cs[jc * d + k];
@@ -373,10 +386,10 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
             }
             mn = j2 == jc ? mn : fminf(mn, dd);
         }
-        if (tpj >= 2) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
-        if (tpj >= 4) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));
+        for (int off = 1; off < tpj; off <<= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
         if (valid && sub == 0) a.hs[j] = fmaxf(0.f, 0.5f * sqrtf(mn) * (1.f - 1e-5f) - eta);
     }
+    if (!writer) return;
     for (int off = 16; off > 0; off >>= 1) {
         const float om1 = __shfl_xor_sync(0xffffffffu, m1, off), om2 = __shfl_xor_sync(0xffffffffu, m2, off);
         const int oi1 = __shfl_xor_sync(0xffffffffu, i1, off);
@@ -394,34 +407,38 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r)   // s_r: 96
         s_r[3 * warp + 2] = __int_as_float(i1);
     }
     __syncthreads();
-    if (tid == 0) {
-        float b1 = 0.f, b2 = 0.f;
-        int bi = -1;
-        for (int w = 0; w < nw; ++w) {
-            const float w1 = s_r[3 * w], w2 = s_r[3 * w + 1];
-            if (w1 > b1) {
-                b2 = fmaxf(b1, w2);
-                b1 = w1;
-                bi = __float_as_int(s_r[3 * w + 2]);
+    if (warp == 0) {                 // the warps' top two, merged the same way
+        m1 = lane < nw ? s_r[3 * lane] : 0.f;
+        m2 = lane < nw ? s_r[3 * lane + 1] : 0.f;
+        i1 = lane < nw ? __float_as_int(s_r[3 * lane + 2]) : -1;
+        for (int off = 16; off > 0; off >>= 1) {
+            const float om1 = __shfl_xor_sync(0xffffffffu, m1, off), om2 = __shfl_xor_sync(0xffffffffu, m2, off);
+            const int oi1 = __shfl_xor_sync(0xffffffffu, i1, off);
+            if (om1 > m1) {
+                m2 = fmaxf(m1, om2);
+                m1 = om1;
+                i1 = oi1;
             } else {
-                b2 = fmaxf(b2, w1);
+                m2 = fmaxf(m2, om1);
             }
         }
-        a.hm[0] = b1;
-        a.hm[1] = b2;
-        a.hm[2] = __int_as_float(bi);
-        a.hm[3] = eta;
+        if (lane == 0) {
+            a.hm[0] = m1;
+            a.hm[1] = m2;
+            a.hm[2] = __int_as_float(i1);
+            a.hm[3] = eta;
+        }
     }
 }
 
 
 #define KM_HPREP_CASE(DD) \
     case DD:              \
-        hprep_body<DD>(a, mode, s_r); \
+        hprep_body<DD>(a, mode, s_r, part, nparts); \
         break;
 
 // k_hprep / k_hprep_batch: the block's instance has its dimension at run time.
-__device__ inline void hprep_dispatch(const PassArgs& a, int mode, float* s_r)
+__device__ inline void hprep_dispatch(const PassArgs& a, int mode, float* s_r, int part = 0, int nparts = 1)
 {
     switch (a.d) {
         KM_FOR_EACH_D(KM_HPREP_CASE)

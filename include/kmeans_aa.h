@@ -69,7 +69,9 @@ typedef struct {
  *   eps1, eps2 thresholds of the dynamic-m rule (0.02, 0.5)
  *   tol       0 = stop when the assignment no longer changes (the paper's criterion);
  *             > 0 = stop when at most floor(tol*N) samples change cluster
- *   rank_tol  least-squares columns from the first with R_kk <= rank_tol*R_00 on are dropped */
+ *   rank_tol  least-squares columns from the first with R_kk <= rank_tol*R_00 on are dropped
+ *   fixed_m   1 = keep m at m_init for the whole solve (the fixed-m strategy that Section 3's
+ *             "Settings of m" and Tab. 2 compare with the dynamic rule); 0 = dynamic m (default) */
 typedef struct {
     int32_t m_max;
     int32_t m_init;
@@ -79,6 +81,7 @@ typedef struct {
     double eps2;
     double tol;
     double rank_tol;
+    int32_t fixed_m;
 } kmeans_params;
 
 /* Result summary (host struct).

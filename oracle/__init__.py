@@ -39,7 +39,7 @@ _lp = ctypes.POINTER(ctypes.c_int64)
 class _Params(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int), ("m_init", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("lloyd_only", ctypes.c_int), ("eps1", ctypes.c_double), ("eps2", ctypes.c_double),
-                ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double), ("fixed_m", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -180,7 +180,7 @@ def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-10):
 
 
 DEFAULT_PARAMS = dict(m_max=10, m_init=2, max_iter=1000, lloyd_only=0, eps1=0.02, eps2=0.5,
-                      tol=0.0, rank_tol=1e-6)
+                      tol=0.0, rank_tol=1e-6, fixed_m=0)
 
 
 def solve(X, C0, lloyd: bool = False, trace: bool = False, **kw):

@@ -315,6 +315,7 @@ void orc_aa_affine(const double* A, const double* b, int n, int m, int iters, do
 typedef struct {
     int m_max, m_init, max_iter, lloyd_only;
     double eps1, eps2, tol, rank_tol;
+    int fixed_m;         /* 1: m stays at m_init (the fixed-m strategy of Section 3, Tab. 2) */
 } orc_params;
 
 typedef struct {
@@ -412,12 +413,12 @@ int orc_solve(const double* X, int64_t N, int d, int K, const double* C0, const 
         /* Adjust the value of m */
         double Et = orc_energy(X, N, d, C, P);
         rec.E_trial = Et;
-        if (!p->lloyd_only && t >= 3) {
+        if (!p->lloyd_only && !p->fixed_m && t >= 3) {
             double num = E_prev - Et, den = E_prev2 - E_prev;
             rec.margin_lo = num - p->eps1 * den;
             rec.margin_hi = num - p->eps2 * den;
         }
-        if (!p->lloyd_only) m = orc_m_rule(m, m_max, t, Et, E_prev, E_prev2, p->eps1, p->eps2);
+        if (!p->lloyd_only && !p->fixed_m) m = orc_m_rule(m, m_max, t, Et, E_prev, E_prev2, p->eps1, p->eps2);
         rec.m = m;
         rec.margin_safe = Et - E_prev;
         /* Make sure C^t decreases the energy */

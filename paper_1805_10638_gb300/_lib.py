@@ -35,7 +35,7 @@ class kmeans_data(ctypes.Structure):
 class kmeans_params(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int32), ("m_init", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("lloyd_only", ctypes.c_int32), ("eps1", ctypes.c_double), ("eps2", ctypes.c_double),
-                ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("rank_tol", ctypes.c_double), ("fixed_m", ctypes.c_int32)]
 
 
 class kmeans_problem(ctypes.Structure):

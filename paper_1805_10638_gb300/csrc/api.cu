@@ -187,6 +187,7 @@ void kmeans_default_params(kmeans_params* p)
     p->eps2 = 0.5;
     p->tol = 0.0;
     p->rank_tol = 1e-6;
+    p->fixed_m = 0;
 }
 
 const char* kmeans_status_string(kmeans_status s)

@@ -11,9 +11,10 @@ namespace km {
 //   Reading R5: the ratio test is written without the division.
 //   Reading R6: equality reverts.  Reading R8: a converged accelerated point is confirmed by
 //   reverting to C_AU.  Also the hard iteration guard and the non-finite input status.
+//   fixed_m: the fixed-m strategy of Section 3 (Tab. 2), m never changes.
 __device__ __forceinline__ void controller_trial(SolveState* st, double E, long long nch, long long thr,
-                                                 int lloyd_only, double eps1, double eps2, int m_max,
-                                                 int max_iter)
+                                                 int lloyd_only, int fixed_m, double eps1, double eps2,
+                                                 int m_max, int max_iter)
 {
     st->body_runs += 1;
     if (st->status != KM_OK || st->body_runs > (unsigned)max_iter + 2u) {
@@ -33,7 +34,7 @@ __device__ __forceinline__ void controller_trial(SolveState* st, double E, long 
         st->final_src = 0;
         return;
     }
-    if (!lloyd_only && st->t >= 3) {
+    if (!lloyd_only && !fixed_m && st->t >= 3) {
         const double num = st->E_prev - E, den = st->E_prev2 - st->E_prev;
         if (num < eps1 * den)
             st->m = st->m - 1 > 0 ? st->m - 1 : 0;

@@ -829,7 +829,7 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
         st->E_trial = E;
     } else {
         if (a.mode == MODE_TRIAL)
-            controller_trial(st, E, ch, a.thr, a.lloyd_only, a.eps1, a.eps2, a.m_max, a.max_iter);
+            controller_trial(st, E, ch, a.thr, a.lloyd_only, a.fixed_m, a.eps1, a.eps2, a.m_max, a.max_iter);
         else
             controller_revert(st, E, ch, a.thr);
         if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);

@@ -50,6 +50,7 @@ struct DenseArgs {
     SolveState* st;
     long long thr;
     int lloyd_only;
+    int fixed_m;
     double eps1;
     double eps2;
     int m_max;

@@ -132,6 +132,7 @@ struct PassArgs {
     int m_max;
     int max_iter;
     int lloyd_only;
+    int fixed_m;             // 1 = m stays at its initial value (no dynamic-m rule)
     double eps1;
     double eps2;
     long long thr;

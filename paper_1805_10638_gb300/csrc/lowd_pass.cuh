@@ -1088,7 +1088,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 if (bd) st->status = KM_ENONFINITE;       // the first loop pass stops the solve
             } else {
                 if (a.mode == MODE_TRIAL)
-                    controller_trial(st, E, ch, a.thr, a.lloyd_only, a.eps1, a.eps2, a.m_max, a.max_iter);
+                    controller_trial(st, E, ch, a.thr, a.lloyd_only, a.fixed_m, a.eps1, a.eps2, a.m_max, a.max_iter);
                 else
                     controller_revert(st, E, ch, a.thr);
                 // the kernel that ends the solve also ends the graph's while loop

@@ -531,6 +531,7 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     pa.m_max = L.m_max;
     pa.max_iter = p.max_iter;
     pa.lloyd_only = p.lloyd_only;
+    pa.fixed_m = p.fixed_m ? 1 : 0;
     pa.eps1 = p.eps1;
     pa.eps2 = p.eps2;
     pa.thr = thr;
@@ -609,6 +610,7 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
         da.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
         da.thr = thr;
         da.lloyd_only = p.lloyd_only;
+        da.fixed_m = p.fixed_m ? 1 : 0;
         da.eps1 = p.eps1;
         da.eps2 = p.eps2;
         da.m_max = L.m_max;

@@ -299,3 +299,50 @@ def test_m_rule_scripted():
     assert oracle.m_rule(3, 10, 5, 9.0, 10.0, 10.0) == 4
     assert oracle.m_rule(3, 10, 5, 11.0, 10.0, 10.0) == 2
     assert oracle.m_rule(3, 10, 5, 10.0, 10.0, 10.0) == 3
+
+
+# --------------------------------------------- fixed m (Section 3, "Settings of m"; Tab. 2)
+@pytest.mark.parametrize("seed", range(3))
+def test_fixed_m0_is_exactly_lloyd(seed):
+    # m held at 0 never mixes: the Lloyd map, pass for pass (while the dynamic rule started at
+    # m = 0 does raise m on these data, so the flag is what keeps it at 0)
+    X, C0 = datagen.small_2d(seed=seed)
+    Cl, rl, il = oracle.solve(X, C0, lloyd=True)
+    Cf, rf, jf = oracle.solve(X, C0, m_init=0, fixed_m=1)
+    np.testing.assert_array_equal(Cl, Cf)
+    np.testing.assert_array_equal(rl, rf)
+    for f in ("iters", "assign_passes", "converged", "E"):
+        assert il[f] == jf[f]
+    assert jf["accepted"] == 0 and jf["rejected"] == 0
+    _, _, _, tr = oracle.solve(X, C0, m_init=0, trace=True)
+    assert max(r["m"] for r in tr) > 0
+
+
+@pytest.mark.parametrize("m", [2, 5])
+@pytest.mark.parametrize("seed", range(3))
+def test_fixed_m_keeps_m_and_invariants(seed, m):
+    X, C0 = datagen.small_2d(seed=seed)
+    C, rho, info, tr = oracle.solve(X, C0, m_init=m, m_max=10, fixed_m=1, trace=True)
+    assert info["converged"] == 1 and info["m_final"] == m
+    assert all(r["m"] == m for r in tr)
+    assert all(math.isnan(r["margin_lo"]) and math.isnan(r["margin_hi"]) for r in tr)
+    assert all(r["m_t"] <= min(m, r["t"]) for r in tr)
+    Es = [r["E"] for r in tr]
+    assert all(b <= a for a, b in zip(Es, Es[1:]))              # stored E non-increasing
+    prev = math.inf
+    for r in tr:
+        if r["accelerated"] and not r["rejected"]:
+            assert r["E_trial"] < prev                          # accepted iterates decrease E
+        prev = r["E"]
+    assert info["assign_passes"] == 1 + info["iters"] + info["rejected"]
+    C_means, _ = oracle.update(X, rho, C.shape[0], C)           # Reading R8: fixed point
+    np.testing.assert_array_equal(C, C_means)
+    np.testing.assert_array_equal(oracle.assign(X, C)[0], rho)
+
+
+def test_fixed_m_is_clamped_to_m_max():
+    X, C0 = datagen.small_2d(seed=0)
+    Ca, ra, ia = oracle.solve(X, C0, m_init=7, m_max=3, fixed_m=1)
+    Cb, rb, ib = oracle.solve(X, C0, m_init=3, m_max=3, fixed_m=1)
+    np.testing.assert_array_equal(Ca, Cb)
+    assert ia["iters"] == ib["iters"] and ia["m_final"] == 3

@@ -1,0 +1,65 @@
+"""bench.py on the CPU: the reference arm's JSON line (the FP64 oracle on host cores) and the
+helpers the GPU arm uses for its roofline and rank timing."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+KEYS = ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+        "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e")
+
+
+def _run(*args):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    return json.loads(lines[0])
+
+
+def _check_line(j, unit):
+    for k in KEYS:
+        assert k in j, k
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == unit
+    assert j["value"] > 0 and j["higher_is_better"] is True and j["vs_baseline"] is None
+    assert j["steps"] == 1 and j["warmup"] == 0 and j["n_gpus"] == 1
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == j["value"] and cb["sample"]
+    e = j["e2e"]
+    assert e["value"] == j["value"] and e["unit"] == unit
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert "workload" in j["config"]
+
+
+def test_reference_arm_lowd_line():
+    j = _run("--steps", "1", "--warmup", "0", "--ref-sample-rows", "4000")
+    _check_line(j, "solves/s")
+    assert j["config"]["workload"] == "lowd_2m" and j["config"]["N"] == 2_000_000
+    assert "4000 of 2000000 rows" in j["cpu_baseline"]["sample"]
+    assert j["p50_ms"] > 0 and j["ms_per_step"] == pytest.approx(1e3 / j["value"])
+
+
+def test_reference_arm_batched_line():
+    j = _run("--workload", "batched_512", "--steps", "1", "--warmup", "0")
+    _check_line(j, "instance solves/s")
+    assert j["config"]["workload"] == "batched_512"
+
+
+def test_profiled_traffic_reads_the_committed_summary():
+    t = bench.profiled_traffic("k_pass_lowd_lowd_2m.md")
+    assert isinstance(t, int) and 20_000_000 < t < 60_000_000
+    assert bench.profiled_traffic("no_such_profile.md") is None
+
+
+def test_rank_helpers():
+    assert bench.max_over_ranks([1, 2.5], None, None) == [1.0, 2.5]
+    assert bench.pct([3, 1, 2], 50) == 2 and bench.pct([], 50) is None
+    assert bench.pct(list(range(101)), 99) == 99

@@ -93,6 +93,8 @@ def _load():
                               ctypes.POINTER(_Params), _dp, _ip, ctypes.POINTER(_Info),
                               ctypes.POINTER(_Trace)]
     lib.orc_solve.restype = ctypes.c_int
+    lib.orc_kmeanspp.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp, _ip, _dp]
+    lib.orc_kmeanspp.restype = None
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -181,6 +183,18 @@ def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-10):
 
 DEFAULT_PARAMS = dict(m_max=10, m_init=2, max_iter=1000, lloyd_only=0, eps1=0.02, eps2=0.5,
                       tol=0.0, rank_tol=1e-6, fixed_m=0)
+
+
+def kmeanspp(X, K: int, u):
+    """K-Means++ seeding with the given uniforms u[0..K-1]; returns (row indices, C)."""
+    X = _f64(X)
+    u = _f64(u)
+    N, d = X.shape
+    assert u.shape == (K,) and 1 <= K and N >= 1
+    idx = np.empty(K, np.int32)
+    C = np.empty((K, d), np.float64)
+    _load().orc_kmeanspp(_ptr(X, _dp), N, d, K, _ptr(u, _dp), _ptr(idx, _ip), _ptr(C, _dp))
+    return idx, C
 
 
 def solve(X, C0, lloyd: bool = False, trace: bool = False, **kw):

@@ -488,6 +488,64 @@ int orc_solve(const double* X, int64_t N, int d, int K, const double* C0, const 
     return 0;
 }
 
+/* ---------------------------------------------------------------------------------------
+ * K-Means++ seeding (the D^2 weighting of Arthur and Vassilvitskii, the initialiser the paper
+ * names beside random seeding in Sections 1 and 3).  The random numbers are inputs:
+ * u[0..K-1], uniform in [0, 1).
+ *   i_1 = min(floor(u_0 N), N - 1).
+ *   For k >= 2: w_i = min_{j<k} ||x_i - c_j||^2 (direct form), W = sum_i w_i in index order,
+ *   S_i = w_0 + ... + w_i; i_k = the smallest i with S_i > u_k W (inverse-CDF sampling), so
+ *   sample i is drawn with probability w_i / W and a chosen sample (w = 0) is never drawn again.
+ * Reading R22: if W = 0 (fewer than K distinct samples) i_k = min(floor(u_k N), N - 1); if
+ *   rounding leaves no S_i above u_k W, the last sample with w_i > 0 is taken.
+ * idx (K) gets the chosen rows, C (K*d) their coordinates.
+ * ------------------------------------------------------------------------------------- */
+void orc_kmeanspp(const double* X, int64_t N, int d, int K, const double* u, int32_t* idx, double* C)
+{
+    double* w = (double*)malloc(sizeof(double) * (size_t)N);
+    int64_t i0 = (int64_t)floor(u[0] * (double)N);
+    if (i0 > N - 1) i0 = N - 1;
+    if (i0 < 0) i0 = 0;
+    idx[0] = (int32_t)i0;
+    for (int k = 0; k < d; ++k) C[k] = X[i0 * d + k];
+    for (int64_t i = 0; i < N; ++i) w[i] = INFINITY;
+    for (int c = 1; c < K; ++c) {
+        const double* cp = C + (int64_t)(c - 1) * d;
+        double W = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) {
+                const double t = X[i * d + k] - cp[k];
+                s += t * t;
+            }
+            if (s < w[i]) w[i] = s;
+            W += w[i];
+        }
+        int64_t pick = -1;
+        if (W > 0.0) {
+            const double target = u[c] * W;
+            double S = 0.0;
+            int64_t last_pos = -1;
+            for (int64_t i = 0; i < N; ++i) {
+                if (w[i] > 0.0) last_pos = i;
+                S += w[i];
+                if (S > target && w[i] > 0.0) {
+                    pick = i;
+                    break;
+                }
+            }
+            if (pick < 0) pick = last_pos;
+        } else {
+            pick = (int64_t)floor(u[c] * (double)N);
+            if (pick > N - 1) pick = N - 1;
+            if (pick < 0) pick = 0;
+        }
+        idx[c] = (int32_t)pick;
+        for (int k = 0; k < d; ++k) C[(int64_t)c * d + k] = X[pick * d + k];
+    }
+    free(w);
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -346,3 +346,55 @@ def test_fixed_m_is_clamped_to_m_max():
     Cb, rb, ib = oracle.solve(X, C0, m_init=3, m_max=3, fixed_m=1)
     np.testing.assert_array_equal(Ca, Cb)
     assert ia["iters"] == ib["iters"] and ia["m_final"] == 3
+
+
+# --------------------------------------------------------------- K-Means++ seeding (D^2 sampling)
+def test_kmeanspp_first_pick_is_uniform_index():
+    X = np.arange(10, dtype=np.float64).reshape(10, 1)
+    for u0, want in ((0.0, 0), (0.05, 0), (0.1, 1), (0.55, 5), (0.999, 9)):
+        idx, C = oracle.kmeanspp(X, 1, [u0])
+        assert idx[0] == want and C[0, 0] == want
+
+
+def test_kmeanspp_inverse_cdf_by_hand():
+    # points 0, 1, 3, 6 on a line; first centre x = 0 -> weights 0, 1, 9, 36 (W = 46):
+    # u W in (0, 1] -> x = 1, (1, 10] -> x = 3, (10, 46) -> x = 6
+    X = np.array([[0.0], [1.0], [3.0], [6.0]])
+    for uW, want in ((0.5, 1), (0.99, 1), (1.5, 2), (5.0, 2), (9.9, 2), (10.5, 3), (20.0, 3), (45.9, 3)):
+        idx, _ = oracle.kmeanspp(X, 2, [0.0, uW / 46.0])
+        assert idx[1] == want, (uW, idx)
+    # third pick with centres {0, 6}: weights 0, min(1, 25) = 1, min(9, 9) = 9, 0 (W = 10)
+    for uW, want in ((0.5, 1), (2.0, 2), (9.9, 2)):
+        idx, _ = oracle.kmeanspp(X, 3, [0.0, 20.0 / 46.0, uW / 10.0])
+        assert list(idx) == [0, 3, want], (uW, idx)
+
+
+def test_kmeanspp_never_repeats_and_n_equals_k_is_a_permutation():
+    r = np.random.default_rng(3)
+    X = r.normal(size=(12, 2))
+    for s in range(5):
+        idx, C = oracle.kmeanspp(X, 12, np.random.default_rng(s).random(12))
+        assert sorted(idx) == list(range(12))
+        np.testing.assert_array_equal(C, X[idx])
+    # duplicates of a chosen point have weight 0 and are never drawn
+    Xd = np.vstack([X[:4], X[:4], X[:4]])
+    idx, _ = oracle.kmeanspp(Xd, 4, [0.0, 0.3, 0.6, 0.9])
+    assert len({tuple(Xd[i]) for i in idx}) == 4
+
+
+def test_kmeanspp_all_identical_falls_back_to_uniform():
+    X = np.ones((8, 3))
+    idx, _ = oracle.kmeanspp(X, 3, [0.0, 0.5, 0.99])
+    assert list(idx) == [0, 4, 7]
+
+
+def test_kmeanspp_one_pick_per_separated_cluster():
+    # 10 tight clusters 100 apart: after a pick, the other clusters carry all but ~1e-8 of the
+    # weight, so D^2 sampling picks one sample from each
+    r = np.random.default_rng(5)
+    centres = 100.0 * np.arange(10)[:, None] * np.array([[1.0, 0.5]])
+    lab = r.integers(0, 10, size=5000)
+    X = centres[lab] + 0.01 * r.normal(size=(5000, 2))
+    for s in range(5):
+        idx, _ = oracle.kmeanspp(X, 10, np.random.default_rng(100 + s).random(10))
+        assert sorted(lab[idx]) == list(range(10))

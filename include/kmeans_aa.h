@@ -167,6 +167,22 @@ kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t
 kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K,
                             const int32_t* rho, double* E);
 
+/* K-Means++ seeding (D^2 sampling; the paper names K-Means++ as an initialiser in Sections 1
+ * and 3 without specifying it): C_out[k] = x_{idx[k]}, k = 0..K-1.  idx[0] = floor(u[0] N); then
+ * row i is drawn with probability w_i / W, w_i the squared distance from x_i to its nearest row
+ * chosen so far (FP64, direct form, separately rounded operations) and W = sum_i w_i, by
+ * inverse-CDF sampling in index order with u[k]: the first i whose running sum exceeds u[k] W.
+ * If W = 0 (fewer distinct rows than K) idx[k] = floor(u[k] N).
+ *   X        [N, d] device (the FP32 copy for KM_BF16_F32; X_bf16 is not used)
+ *   u_host   K uniforms in [0, 1), host memory (the caller's random numbers)
+ *   C_out    [K, d] device output, element type of X
+ *   idx_out  [K] int32 device output, may be NULL
+ * Asynchronous on the context's stream; u_host may be reused when the call returns.  Errors:
+ * KM_EINVAL (NULL pointers, bad shapes, K > N, a u outside [0, 1)), KM_ENOMEM (workspace of
+ * 8 N bytes and more past the budget). */
+kmeans_status kmeans_seed_pp(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const double* u_host,
+                             void* C_out, int32_t* idx_out);
+
 /* Full solve from C0: Lloyd (params->lloyd_only = 1) or Algorithm 1 (Anderson acceleration
  * with the energy safeguard and dynamic m).  All iterations run on the device inside one CUDA
  * graph with a conditional while node; the host only waits for the end.

@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmeans_assign.argtypes = [vp, pd, vp, i32, vp, vp, vp, vp]
     L.kmeans_update.argtypes = [vp, pd, vp, i32, vp, vp, vp]
     L.kmeans_energy.argtypes = [vp, pd, vp, i32, vp, dp]
+    L.kmeans_seed_pp.argtypes = [vp, pd, i32, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.kmeans_solve.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
                                ctypes.POINTER(kmeans_info)]
     L.kmeans_solve_host.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
@@ -240,6 +241,22 @@ def kmeans_energy(ctx: Context, X, C, rho, E=None):
     data = make_data(X)
     _check(ctx, load().kmeans_energy(ctx.handle, ctypes.byref(data), _ptr(C), C.shape[0], _ptr(rho), _ptr(E)))
     return E
+
+
+def kmeans_seed_pp(ctx: Context, X, K: int, u, C_out=None, idx_out=None):
+    """K-Means++ seeding on the device with the uniforms u[0..K-1]; returns (C [K, d], idx [K])."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    if u.shape != (K,):
+        raise ValueError("u must hold K uniforms")
+    if C_out is None:
+        C_out = torch.empty((K, X.shape[1]), dtype=X.dtype, device=X.device)
+    if idx_out is None:
+        idx_out = torch.empty(K, dtype=torch.int32, device=X.device)
+    data = make_data(X)
+    _check(ctx, load().kmeans_seed_pp(ctx.handle, ctypes.byref(data), K,
+                                      u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(C_out),
+                                      _ptr(idx_out)))
+    return C_out, idx_out
 
 
 def kmeans_solve(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, **params):

@@ -60,6 +60,37 @@ def profiled_traffic(name: str):
     return None
 
 
+def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool) -> int:
+    """Kernels one solve launches.  Low-d: the prologue (k_prep, [k_hprep], INIT pass, k_fin,
+    [k_mix]), per loop pass the same with the TRIAL and REVERT passes in place of the INIT pass,
+    and the epilogue (EPI pass, k_epi); k_hprep with Hamerly bounds, k_mix unless the mix is fused
+    into k_fin.  Dense: 14 in the prologue, 19 per loop pass (two 8-kernel assignment and update
+    chains, k_fin, k_mix, the BF16 packing), 4 in the epilogue."""
+    if dense:
+        return 18 + 19 * iters
+    per = 3 + int(ham) + int(not fused_mix)
+    return per * (iters + 1) + 2
+
+
+def batched_launches(loops: int, ngrp: int, ham: bool, mix: bool, dense_iters) -> int:
+    """Kernels of one batched solve.  Low-d chain: prologue (k_prep_batch, [k_hprep_batch], one
+    INIT pass per group, k_fin_batch, [k_mix_batch]), per loop step ([k_hprep_batch], TRIAL and
+    REVERT passes per group, k_fin_batch, [k_mix_batch], k_batch_done), epilogue (EPI pass per
+    group, k_epi_batch); plus one tensor-core chain per dense instance."""
+    h, m = int(ham), int(mix)
+    lowd = (2 + h + ngrp + m) + loops * (h + 2 * ngrp + 2 + m) + ngrp + 1 if ngrp else 0
+    return lowd + sum(solve_launches(it, True, False, False) for it in dense_iters)
+
+
+def same_energy_speed(ms_aa, ms_ll, E_aa, E_ll, rtol: float = 1e-6):
+    """Lloyd's time over Algorithm 1's on the initialisations where both end at the same energy
+    (within rtol), and how many there were; (None, 0) when there are none."""
+    same = [i for i in range(len(ms_aa)) if abs(E_aa[i] - E_ll[i]) <= rtol * abs(E_ll[i])]
+    if not same:
+        return None, 0
+    return sum(ms_ll[i] for i in same) / sum(ms_aa[i] for i in same), len(same)
+
+
 def max_over_ranks(values, dist, device):
     """Element-wise maximum of per-rank timings (the slowest replica sets the job time); `dist`
     is torch.distributed or None for a single process."""
@@ -351,9 +382,11 @@ def run_batched(args, rank, world, local_rank):
 
     lowd = [i for i, (X, _, _, _) in enumerate(data) if X.shape[1] <= 16]
     dense = [i for i in range(n) if i not in set(lowd)]
-    loops = [max(inf[i]["iters"] for i in lowd) for inf in inf_aa]
+    loops = [max((inf[i]["iters"] for i in lowd), default=0) for inf in inf_aa]
     ngrp = len(groups)
-    launches = sum(1 + ngrp + 1 + L * (2 * ngrp + 2) + ngrp + 1 + sum(19 + 17 * inf[i]["iters"] for i in dense)
+    ham = any(inf[i]["scanned_rows"] < inf[i]["assign_passes"] * data[i][0].shape[0] for inf in inf_aa for i in lowd)
+    mix = any(data[i][2] * data[i][0].shape[1] > 64 for i in lowd)
+    launches = sum(batched_launches(L, ngrp, ham, mix, [inf[i]["iters"] for i in dense])
                    for inf, L in zip(inf_aa, loops))
     E_aa = np.array([[inf[i]["E"] for i in range(n)] for inf in inf_aa])
     E_ll = np.array([[inf[i]["E"] for i in range(n)] for inf in inf_ll])
@@ -617,13 +650,14 @@ def run_ours(args, rank, world, local_rank):
     e2e_tot = sum(e2e_t)
     (e2e_tot,) = max_over_ranks([e2e_tot], dist, "cuda")
 
-    # our kernels per solve: dense 13 (prologue) + 17 per loop pass + 6 (epilogue);
-    # low-d with the accelerated iterate fused into the update kernel 3 + 3 per pass + 2
-    launches = sum((19 + 17 * i["iters"]) if dense else (5 + 3 * i["iters"]) for i in inf_aa)
+    # our kernels in the timed Algorithm 1 solves (Hamerly bounds are on when a pass skipped rows)
+    ham = (not dense) and any(i["scanned_rows"] < i["assign_passes"] * N for i in inf_aa)
+    launches = sum(solve_launches(i["iters"], dense, ham, K * d <= 64) for i in inf_aa)
     if rank == 0:
         E_aa = np.array([i["E"] for i in inf_aa])
         E_ll = np.array([i["E"] for i in inf_ll])
         same_E = float(np.mean(np.abs(E_aa - E_ll) / E_ll <= 1e-6))
+        speed_same, n_same = same_energy_speed(ms_aa, ms_ll, E_aa, E_ll)
         h2d = int(X.nbytes + (Xb.nbytes if dense else 0) + C0s[0].nbytes)
         line = {
             "metric": METRIC,
@@ -662,6 +696,8 @@ def run_ours(args, rank, world, local_rank):
                       "E_mean": float(E_ll.mean())},
             "aa_over_lloyd_speed": tot_ll / tot_aa,
             "aa_lloyd_same_energy_frac": same_E,
+            "aa_over_lloyd_speed_same_energy": speed_same,
+            "same_energy_solves": n_same,
             "roofline": roof,
             "e2e": {"value": world * args.steps / e2e_tot, "unit": "solves/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(K * d * 4 + N * 4)},

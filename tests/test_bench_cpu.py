@@ -63,3 +63,25 @@ def test_rank_helpers():
     assert bench.max_over_ranks([1, 2.5], None, None) == [1.0, 2.5]
     assert bench.pct([3, 1, 2], 50) == 2 and bench.pct([], 50) is None
     assert bench.pct(list(range(101)), 99) == 99
+
+
+def test_solve_launch_count():
+    # lowd_2m: Hamerly bounds, separate mix -> 5 kernels in the prologue and per loop pass, 2 after
+    assert bench.solve_launches(152, dense=False, ham=True, fused_mix=False) == 5 * 153 + 2
+    assert bench.solve_launches(10, dense=False, ham=False, fused_mix=True) == 3 * 11 + 2
+    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False) == 18 + 19 * 160
+
+
+def test_same_energy_speed():
+    r, n = bench.same_energy_speed([10.0, 20.0, 30.0], [15.0, 25.0, 60.0], [1.0, 2.0, 3.0],
+                                   [1.0 + 1e-9, 2.5, 3.0])
+    assert n == 2 and r == pytest.approx((15.0 + 60.0) / (10.0 + 30.0))
+    assert bench.same_energy_speed([1.0], [2.0], [1.0], [2.0]) == (None, 0)
+
+
+def test_batched_launch_count():
+    # 3 groups, bounds and a separate mix: 2 + 1 + 3 + 1 in the prologue, 1 + 6 + 2 + 1 per step, 3 + 1 after
+    assert bench.batched_launches(10, 3, True, True, []) == 7 + 10 * 10 + 4
+    assert bench.batched_launches(10, 3, False, False, []) == 5 + 10 * 8 + 4
+    assert bench.batched_launches(5, 2, True, True, [7, 9]) == (6 + 5 * 8 + 3) + (18 + 19 * 7) + (18 + 19 * 9)
+    assert bench.batched_launches(0, 0, False, False, [4]) == 18 + 19 * 4

@@ -7,7 +7,10 @@
 //     with c' = fl32(c - o), o an origin near the data, pad rows (a = 0, ||c'||^2 = +inf)
 //   uncentred FP32 centroids [K][D] for the direct-form residual and rescoring
 //   per-block partials of one assignment pass: residual sums [nb][K][D], counts [nb][K],
-//     energy [nb] f64, changed [nb], rescored [nb]
+//     energy [nb] f64, changed [nb], rescored [nb]; FP32 solver passes with d <= FX_MAX_D add
+//     int64 fixed-point sums into one total [K][D] + counts [K] instead of the per-block sums
+//   Hamerly bounds (FP32 low-d solver): upper / lower bound [N] f32 each, the centroids of the
+//     last pass [K][D] f32, per-pass drifts / half distances [Kpad] f32 and the drift maxima
 //   SolveState: controller scalars, the FP64 Gram matrix of the dF ring, theta.
 #pragma once
 

@@ -23,7 +23,9 @@
 //
 // Determinism: per-cluster sums go to per-warp shared-memory bins; within a warp, lanes with the
 // same label are combined by the lowest such lane in lane order (__match_any_sync); warps are
-// combined in warp order and blocks in block order.  No floating-point atomics.
+// combined in warp order and blocks in block order.  FP32 solver passes with d <= FX_MAX_D sum in
+// 64-bit fixed point instead (shared-memory, then global integer atomics into per-solve totals),
+// which is exact and so independent of the order.  No floating-point atomics.
 #include "lowd_pass.cuh"
 #include "lowd_inst.cuh"
 

@@ -289,9 +289,9 @@ __device__ __forceinline__ int warp_rescore(const float* __restrict__ s_c32, int
     return idx;
 }
 
-// Per-pass inputs of the Hamerly bounds of one solve, computed by one block: by k_hprep before the
-// INIT and TRIAL passes (on C^0, C^t), and by the TRIAL pass's last block for the REVERT pass (on
-// C_AU) when the safeguard fired.  All in FP32 with explicit margins so that they only loosen the
+// Per-pass inputs of the Hamerly bounds of one solve: computed by k_hprep before the INIT and
+// TRIAL passes (on C^0, C^t; the half distances split over its blocks), and by the TRIAL pass's
+// last block alone for the REVERT pass (on C_AU) when the safeguard fired.  All in FP32 with explicit margins so that they only loosen the
 // bounds:
 //   hdr[j] = ||c_j - c_j^last|| (1 + 1e-5) + eta      drift since the centroids of the last pass
 //   hs[j]  = (min_{j' != j} ||c_j - c_j'|| / 2)(1 - 1e-5) - eta, at least 0

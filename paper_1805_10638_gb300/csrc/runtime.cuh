@@ -213,9 +213,9 @@ bool hamerly_mode()
     return !(v && v[0] == '0');
 }
 
-// Solver plans (ham_ok) on the FP32 low-d path use Hamerly bounds when every block can afford to
-// recompute the centroids' pairwise half-distances (K*K*d <= 2^21) and the row queue fits in
-// shared memory.
+// Solver plans (ham_ok) on the FP32 low-d path use Hamerly bounds when the centroids' pairwise
+// half-distances stay cheap (K*K*d <= 2^21: the TRIAL pass's last block recomputes them alone when
+// a REVERT pass follows) and the row queue fits in shared memory.
 kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
                         Plan& P, bool bins = true, bool ham_ok = false)
 {

@@ -23,8 +23,22 @@ def test_library_exports_every_declared_symbol():
 
 def test_defaults_and_status_strings_without_gpu():
     p = km.default_params()
-    assert (p.m_max, p.m_init, p.max_iter, p.lloyd_only) == (10, 2, 1000, 0)
+    assert (p.m_max, p.m_init, p.max_iter, p.lloyd_only, p.fixed_m) == (10, 2, 1000, 0, 0)
     assert (p.eps1, p.eps2, p.tol, p.rank_tol) == (0.02, 0.5, 0.0, 1e-6)
+    assert km.default_params(fixed_m=1, m_init=5).fixed_m == 1
+    with pytest.raises(KeyError):
+        km.default_params(no_such_field=1)
+    # the structs the Python side uses have the header's fields in the header's order
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(_lib._build.PKG), "include", "kmeans_aa.h")).read()
+    for name, cls in (("kmeans_params", _lib.kmeans_params), ("kmeans_info", _lib.kmeans_info),
+                      ("kmeans_data", _lib.kmeans_data), ("kmeans_problem", _lib.kmeans_problem),
+                      ("kmeans_server_stats", _lib.kmeans_server_stats)):
+        body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"(\w+)\s*;", body)
+        assert [f for f, _ in cls._fields_] == fields, name
     L = km.load()
     assert L.kmeans_status_string(1) == b"KM_EINVAL"
     assert L.kmeans_status_string(5) == b"KM_ENONFINITE"
@@ -37,3 +51,6 @@ def test_null_arguments_rejected_before_any_cuda_call():
     assert L.kmeans_destroy(None) == _lib.KM_OK
     data = _lib.kmeans_data(None, None, 10, 2, 0)
     assert L.kmeans_assign(None, ctypes.byref(data), None, 1, None, None, None, None) == _lib.KM_EINVAL
+
+    u = (ctypes.c_double * 2)(0.1, 0.2)
+    assert L.kmeans_seed_pp(None, ctypes.byref(data), 2, u, None, None) == _lib.KM_EINVAL

@@ -180,9 +180,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ CPU oracle
-def oracle_sample_solves(X, C0s, sample_rows: int, n: int, m_max: int, lloyd: bool = False):
-    """Time the FP64 oracle on a row sample; returns (seconds per solve list, cores, rows)."""
+def oracle_sample_solves(X, C0s, sample_rows: int, n: int, m_max: int, lloyd: bool = False, threads: int = 0):
+    """Time the FP64 oracle on a row sample; returns (seconds per solve list, cores, rows).
+    threads > 0 runs it on that many threads (then back to the previous count)."""
     import oracle
+    prev = oracle.num_threads()
+    if threads > 0:
+        oracle.set_num_threads(threads)
+    try:
+        return _oracle_sample_solves(oracle, X, C0s, sample_rows, n, m_max, lloyd)
+    finally:
+        oracle.set_num_threads(prev)
+
+
+def _oracle_sample_solves(oracle, X, C0s, sample_rows, n, m_max, lloyd):
     N = X.shape[0]
     r = np.random.default_rng(12345)
     idx = np.sort(r.choice(N, size=min(sample_rows, N), replace=False))
@@ -712,6 +723,11 @@ def run_ours(args, rank, world, local_rank):
                                     "kind": "oracle",
                                     "sample": f"{len(times)} AA solves on {rows} of {X.shape[0]} rows "
                                               f"(same d, K, inits), time scaled by {X.shape[0]}/{rows}"}
+            # the same oracle on one thread (its only parallel loop is the assignment's)
+            t1, _, rows1 = oracle_sample_solves(X, C0s, max(1, rows // 2), 1, wl["m_max"], threads=1)
+            line["cpu_baseline"]["value_1_thread"] = rows1 / (t1[0] * X.shape[0])
+            line["cpu_baseline"]["sample_1_thread"] = (f"1 AA solve on {rows1} of {X.shape[0]} rows on one thread, "
+                                                       f"time scaled by {X.shape[0]}/{rows1}")
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

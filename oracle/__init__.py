@@ -97,6 +97,8 @@ def _load():
     lib.orc_kmeanspp.restype = None
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+    lib.orc_set_num_threads.restype = None
     _lib = lib
     return lib
 
@@ -112,6 +114,11 @@ def _ptr(a: np.ndarray, typ):
 def num_threads() -> int:
     """OpenMP threads the oracle's assignment loop uses (OMP_NUM_THREADS, else all cores)."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the assignment loop from now on (results do not depend on it)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def assign(X, C):

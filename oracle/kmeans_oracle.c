@@ -554,3 +554,13 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the assignment loop for the calls that follow (results do not depend on it). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

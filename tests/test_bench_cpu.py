@@ -85,3 +85,21 @@ def test_batched_launch_count():
     assert bench.batched_launches(10, 3, False, False, []) == 5 + 10 * 8 + 4
     assert bench.batched_launches(5, 2, True, True, [7, 9]) == (6 + 5 * 8 + 3) + (18 + 19 * 7) + (18 + 19 * 9)
     assert bench.batched_launches(0, 0, False, False, [4]) == 18 + 19 * 4
+
+
+def test_oracle_thread_count_is_restored():
+    import numpy as np
+    import oracle
+    import datagen
+    X, C0 = datagen.small_2d(0)
+    before = oracle.num_threads()
+    t, cores, rows = bench.oracle_sample_solves(X, [C0], 2000, 1, 10, threads=1)
+    assert cores == 1 and rows == 2000 and len(t) == 1 and t[0] > 0
+    assert oracle.num_threads() == before
+    # the thread count does not change the result
+    a = oracle.solve(X[:3000], C0)
+    oracle.set_num_threads(1)
+    b = oracle.solve(X[:3000], C0)
+    oracle.set_num_threads(before)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[2]["iters"] == b[2]["iters"]

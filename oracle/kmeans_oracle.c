@@ -17,7 +17,8 @@
  *
  * Parity pins: every function here is pinned by tests that do not reuse this code
  * (brute force on tiny inputs, library least squares, closed forms, invariants of the
- * method, Anderson acceleration on an affine map).  The dynamic-m trajectory on real data
+ * method, Anderson acceleration on an affine map, fixed m = 0 against Lloyd, hand-computed
+ * inverse-CDF intervals for K-Means++ seeding).  The dynamic-m trajectory on real data
  * is the one part with no external pin (the paper's tables need datasets that are not
  * available); it is checked for the invariants of Algorithm 1 only.
  */

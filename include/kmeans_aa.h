@@ -178,8 +178,8 @@ kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C
  *   C_out    [K, d] device output, element type of X
  *   idx_out  [K] int32 device output, may be NULL
  * Asynchronous on the context's stream; u_host may be reused when the call returns.  Errors:
- * KM_EINVAL (NULL pointers, bad shapes, K > N, a u outside [0, 1)), KM_ENOMEM (workspace of
- * 8 N bytes and more past the budget). */
+ * KM_EINVAL (NULL pointers, bad shapes, K > N, N >= 2^31, a u outside [0, 1)), KM_ENOMEM
+ * (workspace of 8 N bytes and more past the budget). */
 kmeans_status kmeans_seed_pp(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const double* u_host,
                              void* C_out, int32_t* idx_out);
 

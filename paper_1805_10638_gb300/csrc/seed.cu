@@ -191,6 +191,7 @@ extern "C" kmeans_status kmeans_seed_pp(kmeans_ctx* ctx, const kmeans_data* X, i
     kmeans_status s = check_data(ctx, X, K, false);
     if (s != KM_OK) return s;
     if (!u_host || !C_out) return fail(ctx, KM_EINVAL, "u_host and C_out must not be NULL");
+    if (X->N > (int64_t)INT32_MAX) return fail(ctx, KM_EINVAL, "row indices are int32: N must be below 2^31");
     for (int k = 0; k < K; ++k)
         if (!(u_host[k] >= 0.0 && u_host[k] < 1.0)) return fail(ctx, KM_EINVAL, "every u must lie in [0, 1)");
     KM_CUDA(cudaSetDevice(ctx->device));

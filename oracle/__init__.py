@@ -155,7 +155,7 @@ def update(X, rho, K: int, C_prev):
     return C, counts
 
 
-def ls_qr(dF, f, rank_tol: float = 1e-10):
+def ls_qr(dF, f, rank_tol: float = 1e-12):
     """Eq. 7 by Householder QR.  dF is [n, m] (column 0 = newest difference).
 
     Returns (theta f64[m], rank); columns from the first with |R_kk| <= rank_tol*|R_00| on are
@@ -177,7 +177,7 @@ def m_rule(m: int, m_max: int, t: int, E_cur: float, E_prev: float, E_prev2: flo
     return int(_load().orc_m_rule(m, m_max, t, E_cur, E_prev, E_prev2, eps1, eps2))
 
 
-def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-10):
+def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-12):
     """Classical Anderson (Eq. 7-8, no safeguard) on g(x) = A x + b; returns [iters+1, n]."""
     A, b = _f64(A), _f64(b)
     n = b.shape[0]
@@ -189,7 +189,7 @@ def aa_affine(A, b, x0, m: int, iters: int, rank_tol: float = 1e-10):
 
 
 DEFAULT_PARAMS = dict(m_max=10, m_init=2, max_iter=1000, lloyd_only=0, eps1=0.02, eps2=0.5,
-                      tol=0.0, rank_tol=1e-6, fixed_m=0)
+                      tol=0.0, rank_tol=1e-12, fixed_m=0)
 
 
 def kmeanspp(X, K: int, u):

@@ -217,6 +217,45 @@ def test_ls_qr_truncates_dependent_columns():
     assert rank0 == 0 and (theta0 == 0).all()
 
 
+def _with_singular_values(n, sv, seed):
+    r = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(r.normal(size=(n, len(sv))))
+    V, _ = np.linalg.qr(r.normal(size=(len(sv), len(sv))))
+    return (U * np.asarray(sv)) @ V.T
+
+
+@pytest.mark.parametrize("cond", [1e6, 1e9, 1e11])
+def test_ls_qr_keeps_columns_up_to_cond_1e12(cond):
+    """Reading R11's cut is |R_kk| <= 1e-12 |R_00|: a history whose condition number lies between
+    1e6 and 1e12 keeps every column (min |R_kk| >= sigma_min), and the QR's theta is the
+    least-squares solution to the accuracy u * cond that a backward-stable solve guarantees."""
+    m = 6
+    A = _with_singular_values(300, np.geomspace(1.0, 1.0 / cond, m), seed=int(np.log10(cond)))
+    theta_true = np.linspace(1.0, -2.0, m)
+    f = A @ theta_true                               # consistent system: the exact minimiser is theta_true
+    theta, rank = oracle.ls_qr(A, f)
+    assert rank == m
+    np.testing.assert_allclose(theta, theta_true, rtol=0, atol=1e-16 * cond * 50 * np.abs(theta_true).max())
+    ref = np.linalg.lstsq(A, f, rcond=1e-14)[0]
+    np.testing.assert_allclose(theta, ref, rtol=0, atol=1e-16 * cond * 50 * np.abs(theta_true).max())
+
+
+def test_ls_qr_drops_a_column_dependent_to_1e_13():
+    """A newest-first history whose oldest column equals a combination of the others up to 1e-13
+    (relative) has |R_kk| / |R_00| far below 1e-12: that column is dropped, the rest solved."""
+    r = np.random.default_rng(11)
+    A = r.normal(size=(100, 4))
+    A[:, 3] = A[:, 0] - 0.5 * A[:, 2] + 1e-13 * r.normal(size=100)
+    f = r.normal(size=100)
+    theta, rank = oracle.ls_qr(A, f)
+    assert rank == 3 and theta[3] == 0.0
+    np.testing.assert_allclose(theta[:3], np.linalg.lstsq(A[:, :3], f, rcond=None)[0], rtol=1e-10)
+    # the same column 1e-8 away from dependence is kept at the default cut
+    A[:, 3] = A[:, 0] - 0.5 * A[:, 2] + 1e-8 * r.normal(size=100)
+    theta, rank = oracle.ls_qr(A, f)
+    assert rank == 4
+
+
 def test_ls_qr_equals_normal_equations_when_well_conditioned():
     """The LS solution through the Gram matrix and its Cholesky factor (the R of the QR)."""
     r = np.random.default_rng(8)

@@ -15,6 +15,7 @@ follows:
 * ``m_rule``  - Section 2.2 / Algorithm 1, dynamic m
 * ``aa_affine`` - Eq. 7-8 on an affine map (classical Anderson, used as a textbook pin)
 * ``solve``   - Lloyd (Section 1) and Algorithm 1
+* ``step``    - one loop pass of Algorithm 1 from an explicit state (the body of ``solve``)
 """
 from __future__ import annotations
 
@@ -56,6 +57,14 @@ class _Trace(ctypes.Structure):
                 ("margin_hi", ctypes.c_double), ("margin_safe", ctypes.c_double)]
 
 
+class _State(ctypes.Structure):
+    _fields_ = [("C", _dp), ("CAU", _dp), ("F", _dp), ("dF", _dp), ("dG", _dp), ("Pprev", _ip),
+                ("count", ctypes.c_int), ("t", ctypes.c_int), ("m", ctypes.c_int), ("from_lloyd", ctypes.c_int),
+                ("E_prev", ctypes.c_double), ("E_prev2", ctypes.c_double), ("done", ctypes.c_int),
+                ("E", ctypes.c_double), ("accepted", ctypes.c_int), ("rejected", ctypes.c_int),
+                ("assign_passes", ctypes.c_int), ("theta", ctypes.c_double * 64)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off, OpenMP on); returns the .so path."""
     with _lock:
@@ -93,6 +102,9 @@ def _load():
                               ctypes.POINTER(_Params), _dp, _ip, ctypes.POINTER(_Info),
                               ctypes.POINTER(_Trace)]
     lib.orc_solve.restype = ctypes.c_int
+    lib.orc_step.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Params),
+                             ctypes.POINTER(_State), ctypes.POINTER(_Trace), _ip, _dp, _dp, _dp]
+    lib.orc_step.restype = ctypes.c_int
     lib.orc_kmeanspp.argtypes = [_dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _dp, _ip, _dp]
     lib.orc_kmeanspp.restype = None
     lib.orc_num_threads.argtypes = []
@@ -228,3 +240,54 @@ def solve(X, C0, lloyd: bool = False, trace: bool = False, **kw):
     recs = [{f: getattr(tr[i], f) for f, _ in _Trace._fields_ if f != "pad"}
             for i in range(out["iters"])]
     return C, rho, out, recs
+
+
+def step(X, state: dict, **kw):
+    """One loop pass t of Algorithm 1 from an explicit state (the same routine ``solve`` loops over).
+
+    state: C (C^t, the iterate to assign), CAU (G^{t-1}), F (F^{t-1}), dF and dG ([count, K*d]
+    differences, newest first), Pprev (P^{t-1}), t, m, from_lloyd (1 if C^t is a plain Lloyd
+    iterate), E_prev (E^{t-1}), E_prev2 (E^{t-2}); kw are solver parameters as for ``solve``.
+    Returns (new_state, record): new_state holds the same keys after the pass (C = C^{t+1},
+    CAU = G^t, F = F^t, Pprev = P^t, t + 1, ...) plus done, E (terminal energy), theta (the last
+    least-squares solution, zeros past its rank) and the pass counters; record is the pass's trace
+    record (n_changed, m, m_t, rank, rejected, E_trial, E)."""
+    X = _f64(X)
+    N, d = X.shape
+    C = _f64(state["C"]).copy()
+    K = C.shape[0]
+    n = K * d
+    prm = dict(DEFAULT_PARAMS)
+    prm.update(kw)
+    m_max = 0 if prm["lloyd_only"] else prm["m_max"]
+    mm = max(m_max, 1)
+    dF = np.zeros((mm, n), np.float64)
+    dG = np.zeros((mm, n), np.float64)
+    cnt = int(state.get("count", len(state.get("dF", []))))
+    if cnt:
+        dF[:cnt] = np.asarray(state["dF"], np.float64).reshape(cnt, n)
+        dG[:cnt] = np.asarray(state["dG"], np.float64).reshape(cnt, n)
+    CAU = _f64(state["CAU"]).reshape(K, d).copy()
+    F = _f64(state["F"]).reshape(K, d).copy()
+    Pprev = np.ascontiguousarray(state["Pprev"], dtype=np.int32).copy()
+    st = _State()
+    st.C, st.CAU, st.F = _ptr(C, _dp), _ptr(CAU, _dp), _ptr(F, _dp)
+    st.dF, st.dG, st.Pprev = _ptr(dF, _dp), _ptr(dG, _dp), _ptr(Pprev, _ip)
+    st.count, st.t, st.m, st.from_lloyd = cnt, int(state["t"]), int(state["m"]), int(state["from_lloyd"])
+    st.E_prev, st.E_prev2 = float(state["E_prev"]), float(state["E_prev2"])
+    st.accepted = int(state.get("accepted", 0))
+    st.rejected = int(state.get("rejected", 0))
+    st.assign_passes = int(state.get("assign_passes", 0))
+    p = _Params(**prm)
+    rec = _Trace()
+    P = np.empty(N, np.int32)
+    G = np.empty(n, np.float64)
+    Fn = np.empty(n, np.float64)
+    Cn = np.empty(n, np.float64)
+    _load().orc_step(_ptr(X, _dp), N, d, K, ctypes.byref(p), ctypes.byref(st), ctypes.byref(rec),
+                     _ptr(P, _ip), _ptr(G, _dp), _ptr(Fn, _dp), _ptr(Cn, _dp))
+    out = dict(C=C, CAU=CAU, F=F, dF=dF[:st.count].copy(), dG=dG[:st.count].copy(), Pprev=Pprev,
+               count=st.count, t=st.t, m=st.m, from_lloyd=st.from_lloyd, E_prev=st.E_prev,
+               E_prev2=st.E_prev2, done=st.done, E=st.E, accepted=st.accepted, rejected=st.rejected,
+               assign_passes=st.assign_passes, theta=np.array(st.theta[:], np.float64))
+    return out, {f: getattr(rec, f) for f, _ in _Trace._fields_ if f != "pad"}

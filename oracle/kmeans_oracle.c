@@ -200,80 +200,41 @@ int orc_m_rule(int m, int m_max, int t, double E_cur, double E_prev, double E_pr
 
 /* ---------------------------------------------------------------------------------------
  * Anderson history and accelerated iterate (Eq. 7 and Eq. 8, Algorithm 1 last lines).
- * The history keeps the newest (m_max + 1) pairs (G^s, F^s) in a ring.  aa_mix forms
- *   dF_j = F^{t-j+1} - F^{t-j},  dG_j = G^{t-j+1} - G^{t-j},  j = 1..m_t,
- * solves Eq. 7 and returns C^{t+1} = G^t - sum_j theta_j dG_j.
+ * The history holds the differences
+ *   dF_j = F^{t-j+1} - F^{t-j},  dG_j = G^{t-j+1} - G^{t-j},  j = 1..count  (count <= m_max),
+ * newest first: dF_1 at dF[0].  Each new pair (G^t, F^t) pushes dF_1 = F^t - F^{t-1} and
+ * dG_1 = G^t - G^{t-1} in front and drops the oldest difference once m_max are kept.
+ * aa_mix solves Eq. 7 over the newest m_t differences and returns C^{t+1} = G^t - sum_j theta_j dG_j.
  * Reading R1: the sign is minus (Algorithm 1; Eq. 8's '+' and 'theta_i' are typos: the
  * minimiser of Eq. 7 makes F^t - dF theta small, whose G-counterpart is G^t - dG theta).
  * ------------------------------------------------------------------------------------- */
-typedef struct {
-    int cap;          /* ring capacity = m_max + 1 */
-    int count;        /* number of valid pairs */
-    int head;         /* slot of the newest pair */
-    int64_t n;        /* vector length (K*d) */
-    double* G;        /* cap x n */
-    double* F;        /* cap x n */
-} orc_hist;
-
-static void hist_init(orc_hist* h, int m_max, int64_t n)
+static void hist_push(double* dF, double* dG, int* count, int m_max, int64_t n, const double* G_new,
+                      const double* G_old, const double* F_new, const double* F_old)
 {
-    h->cap = m_max + 1;
-    h->count = 0;
-    h->head = -1;
-    h->n = n;
-    h->G = (double*)calloc((size_t)h->cap * n, sizeof(double));
-    h->F = (double*)calloc((size_t)h->cap * n, sizeof(double));
-}
-
-static void hist_free(orc_hist* h)
-{
-    free(h->G);
-    free(h->F);
-}
-
-static void hist_push(orc_hist* h, const double* G, const double* F)
-{
-    h->head = (h->head + 1) % h->cap;
-    memcpy(h->G + (int64_t)h->head * h->n, G, sizeof(double) * (size_t)h->n);
-    memcpy(h->F + (int64_t)h->head * h->n, F, sizeof(double) * (size_t)h->n);
-    if (h->count < h->cap) h->count++;
-}
-
-/* pointer to pair s steps back from the newest (s = 0 is the newest) */
-static const double* hist_G(const orc_hist* h, int s)
-{
-    return h->G + (int64_t)((h->head - s + h->cap) % h->cap) * h->n;
-}
-static const double* hist_F(const orc_hist* h, int s)
-{
-    return h->F + (int64_t)((h->head - s + h->cap) % h->cap) * h->n;
+    if (m_max <= 0) return;
+    int keep = *count < m_max ? *count : m_max - 1;
+    memmove(dF + n, dF, sizeof(double) * (size_t)n * keep);
+    memmove(dG + n, dG, sizeof(double) * (size_t)n * keep);
+    for (int64_t i = 0; i < n; ++i) {
+        dF[i] = F_new[i] - F_old[i];
+        dG[i] = G_new[i] - G_old[i];
+    }
+    *count = keep + 1;
 }
 
 /* Returns the number of LS columns kept (0 means C_next = G^t, a plain Lloyd iterate). */
-static int aa_mix(const orc_hist* h, int m_t, double rank_tol, double* C_next, double* theta_out)
+static int aa_mix(const double* dF, const double* dG, int count, int64_t n, int m_t, const double* Gt,
+                  const double* Ft, double rank_tol, double* C_next, double* theta_out)
 {
-    int64_t n = h->n;
-    const double* Gt = hist_G(h, 0);
-    const double* Ft = hist_F(h, 0);
-    if (m_t > h->count - 1) m_t = h->count - 1;
+    double theta[64];
+    if (m_t > count) m_t = count;
     memcpy(C_next, Gt, sizeof(double) * (size_t)n);
     if (m_t <= 0) return 0;
-    double* dF = (double*)malloc(sizeof(double) * (size_t)n * m_t);
-    double theta[64];
-    for (int j = 1; j <= m_t; ++j) {
-        const double* Fa = hist_F(h, j - 1);   /* F^{t-j+1} */
-        const double* Fb = hist_F(h, j);       /* F^{t-j}   */
-        for (int64_t i = 0; i < n; ++i) dF[(int64_t)(j - 1) * n + i] = Fa[i] - Fb[i];
-    }
     int rank = orc_ls_qr(dF, n, m_t, Ft, rank_tol, theta);
-    for (int j = 1; j <= rank; ++j) {
-        const double* Ga = hist_G(h, j - 1);
-        const double* Gb = hist_G(h, j);
-        for (int64_t i = 0; i < n; ++i) C_next[i] -= theta[j - 1] * (Ga[i] - Gb[i]);
-    }
+    for (int j = 0; j < rank; ++j)
+        for (int64_t i = 0; i < n; ++i) C_next[i] -= theta[j] * dG[(int64_t)j * n + i];
     if (theta_out)
         for (int j = 0; j < m_t; ++j) theta_out[j] = theta[j];
-    free(dF);
     return rank;
 }
 
@@ -288,10 +249,13 @@ static int aa_mix(const orc_hist* h, int m_t, double rank_tol, double* C_next, d
 void orc_aa_affine(const double* A, const double* b, int n, int m, int iters, double rank_tol,
                    double* x, double* traj)
 {
-    orc_hist h;
-    hist_init(&h, m, n);
+    double* dF = (double*)calloc((size_t)(m > 0 ? m : 1) * n, sizeof(double));
+    double* dG = (double*)calloc((size_t)(m > 0 ? m : 1) * n, sizeof(double));
     double* g = (double*)malloc(sizeof(double) * n);
     double* f = (double*)malloc(sizeof(double) * n);
+    double* g_old = (double*)malloc(sizeof(double) * n);
+    double* f_old = (double*)malloc(sizeof(double) * n);
+    int count = 0;
     if (traj) memcpy(traj, x, sizeof(double) * n);
     for (int t = 0; t < iters; ++t) {
         for (int r = 0; r < n; ++r) {
@@ -300,14 +264,19 @@ void orc_aa_affine(const double* A, const double* b, int n, int m, int iters, do
             g[r] = s;
         }
         for (int r = 0; r < n; ++r) f[r] = g[r] - x[r];
-        hist_push(&h, g, f);
+        if (t > 0) hist_push(dF, dG, &count, m, n, g, g_old, f, f_old);
+        memcpy(g_old, g, sizeof(double) * n);
+        memcpy(f_old, f, sizeof(double) * n);
         int m_t = m < t ? m : t;
-        aa_mix(&h, m_t, rank_tol, x, NULL);
+        aa_mix(dF, dG, count, n, m_t, g, f, rank_tol, x, NULL);
         if (traj) memcpy(traj + (int64_t)(t + 1) * n, x, sizeof(double) * n);
     }
+    free(dF);
+    free(dG);
     free(g);
     free(f);
-    hist_free(&h);
+    free(g_old);
+    free(f_old);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -334,6 +303,29 @@ typedef struct {
     double margin_safe;  /* E_trial - E^{t-1}: the safeguard reverts when this is >= 0 */
 } orc_trace;
 
+/* The state of Algorithm 1 between two loop passes: everything a pass reads, and what it leaves
+ * for the next one.  On entry to pass t: C = C^t (the iterate to assign), CAU = C_AU = G^{t-1},
+ * F = F^{t-1}, dF / dG the differences (newest first, `count` of them), Pprev = P^{t-1},
+ * E_prev = E^{t-1} and E_prev2 = E^{t-2} (stored energies), m, from_lloyd = whether C^t is a
+ * plain Lloyd iterate.  After the pass (unless it terminated): C = C^{t+1}, CAU = G^t, F = F^t,
+ * Pprev = P^t, t incremented.  If it terminated, done = 1, C and Pprev hold the result and E
+ * its energy. */
+typedef struct {
+    double* C;
+    double* CAU;
+    double* F;
+    double* dF;           /* m_max x K*d */
+    double* dG;
+    int32_t* Pprev;       /* N */
+    int count;
+    int t, m, from_lloyd;
+    double E_prev, E_prev2;
+    int done;
+    double E;             /* energy of the terminal pair */
+    int accepted, rejected, assign_passes;
+    double theta[64];     /* theta of the last least-squares solve (0 past its rank) */
+} orc_state;
+
 static int64_t count_changed(const int32_t* a, const int32_t* b, int64_t N)
 {
     int64_t c = 0;
@@ -342,7 +334,7 @@ static int64_t count_changed(const int32_t* a, const int32_t* b, int64_t N)
 }
 
 /*
- * Algorithm 1 with the readings:
+ * One loop pass t of Algorithm 1, with the readings:
  *   R3  the revert target C_AU is G^{t-1}, the Lloyd image of the previous stored iterate;
  *   R4, R5  m rule as in orc_m_rule;
  *   R6  the safeguard reverts on E^t >= E^{t-1} (as written);
@@ -350,10 +342,105 @@ static int64_t count_changed(const int32_t* a, const int32_t* b, int64_t N)
  *   R8  convergence is only accepted at a Lloyd iterate: if C^t was an accelerated point and
  *       its assignment equals P^{t-1}, the solver reverts to C_AU (= means of P^{t-1}) and
  *       tests again, so the returned C is always the mean of its clusters;
- *   R13 iters = t at termination; Lloyd runs the same loop, so m_max = 0 reproduces Lloyd;
  *   R14 tol > 0 stops when n_changed <= floor(tol * N); tol = 0 is exact equality;
  *   R18 the safeguard is skipped when C^t is itself a Lloyd iterate (reverting would
  *       re-assign the same point; Lloyd's step never increases E).
+ * P, G, Fn and Cnext are scratch buffers (N, K*d, K*d, K*d).  rec (optional) gets the pass's
+ * trace record.
+ */
+int orc_step(const double* X, int64_t N, int d, int K, const orc_params* p, orc_state* s, orc_trace* rec_out,
+             int32_t* P, double* G, double* Fn, double* Cnext)
+{
+    const int64_t n = (int64_t)K * d;
+    const int64_t thr = p->tol > 0 ? (int64_t)floor(p->tol * (double)N) : 0;
+    const int m_max = p->lloyd_only ? 0 : p->m_max;
+    const int t = s->t;
+    orc_trace rec;
+    memset(&rec, 0, sizeof(rec));
+    rec.t = t;
+    rec.accelerated = !s->from_lloyd;
+    rec.margin_lo = rec.margin_hi = NAN;
+    /* Check for convergence */
+    orc_assign(X, N, d, s->C, K, P, NULL, NULL);
+    s->assign_passes++;
+    int64_t nch = count_changed(P, s->Pprev, N);
+    rec.n_changed = (int)nch;
+    int conv = nch <= thr;
+    if (conv && s->from_lloyd) {
+        double E = orc_energy(X, N, d, s->C, P);
+        rec.E_trial = rec.E = E;
+        rec.margin_safe = NAN;
+        rec.m = s->m;
+        if (rec_out) *rec_out = rec;
+        s->E = E;
+        s->done = 1;
+        memcpy(s->Pprev, P, sizeof(int32_t) * (size_t)N);
+        return 1;
+    }
+    /* Adjust the value of m */
+    double Et = orc_energy(X, N, d, s->C, P);
+    rec.E_trial = Et;
+    if (!p->lloyd_only && !p->fixed_m && t >= 3) {
+        double num = s->E_prev - Et, den = s->E_prev2 - s->E_prev;
+        rec.margin_lo = num - p->eps1 * den;
+        rec.margin_hi = num - p->eps2 * den;
+    }
+    if (!p->lloyd_only && !p->fixed_m)
+        s->m = orc_m_rule(s->m, m_max, t, Et, s->E_prev, s->E_prev2, p->eps1, p->eps2);
+    rec.m = s->m;
+    rec.margin_safe = Et - s->E_prev;
+    /* Make sure C^t decreases the energy */
+    int reject = !s->from_lloyd && (conv || Et >= s->E_prev);
+    if (reject) {
+        memcpy(s->C, s->CAU, sizeof(double) * (size_t)n);
+        orc_assign(X, N, d, s->C, K, P, NULL, NULL);
+        s->assign_passes++;
+        s->rejected++;
+        rec.rejected = 1;
+        Et = orc_energy(X, N, d, s->C, P);
+        nch = count_changed(P, s->Pprev, N);
+        if (nch <= thr) {
+            rec.E = Et;
+            if (rec_out) *rec_out = rec;
+            s->E = Et;
+            s->done = 1;
+            memcpy(s->Pprev, P, sizeof(int32_t) * (size_t)N);
+            return 1;
+        }
+    } else if (!s->from_lloyd) {
+        s->accepted++;
+    }
+    rec.E = Et;
+    /* Anderson acceleration */
+    orc_update(X, N, d, P, K, s->C, G, NULL);
+    for (int64_t i = 0; i < n; ++i) Fn[i] = G[i] - s->C[i];
+    hist_push(s->dF, s->dG, &s->count, m_max, n, G, s->CAU, Fn, s->F);
+    memcpy(s->CAU, G, sizeof(double) * (size_t)n);
+    memcpy(s->F, Fn, sizeof(double) * (size_t)n);
+    int m_t = s->m < t ? s->m : t;
+    rec.m_t = m_t;
+    for (int j = 0; j < 64; ++j) s->theta[j] = 0.0;
+    int rank = 0;
+    if (m_t > 0) {
+        rank = aa_mix(s->dF, s->dG, s->count, n, m_t, G, Fn, p->rank_tol, Cnext, s->theta);
+    } else {
+        memcpy(Cnext, G, sizeof(double) * (size_t)n);
+    }
+    rec.rank = rank;
+    s->from_lloyd = rank == 0;
+    s->E_prev2 = s->E_prev;
+    s->E_prev = Et;
+    memcpy(s->Pprev, P, sizeof(int32_t) * (size_t)N);
+    memcpy(s->C, Cnext, sizeof(double) * (size_t)n);
+    s->t = t + 1;
+    if (rec_out) *rec_out = rec;
+    return 0;
+}
+
+/*
+ * Algorithm 1 (R13: iters = t at termination; Lloyd runs the same loop, so m_max = 0
+ * reproduces Lloyd): C^1 = C_AU^1 = G(C^0); F^0 = C^1 - C^0; E^0 = +inf; P^0 = Assign(C^0);
+ * then orc_step for t = 1, 2, ... until it terminates or t = max_iter.
  * At max_iter without convergence the returned pair is (P^t, G^t) of the last pass.
  * rho_out (N) and C_out (K*d) are written; trace (optional) gets one record per pass.
  */
@@ -361,131 +448,67 @@ int orc_solve(const double* X, int64_t N, int d, int K, const double* C0, const 
               double* C_out, int32_t* rho_out, orc_info* info, orc_trace* trace)
 {
     const int64_t n = (int64_t)K * d;
-    const int64_t thr = p->tol > 0 ? (int64_t)floor(p->tol * (double)N) : 0;
     const int m_max = p->lloyd_only ? 0 : p->m_max;
+    const int mm = m_max > 0 ? m_max : 1;
+    orc_state s;
+    memset(&s, 0, sizeof(s));
+    s.C = (double*)malloc(sizeof(double) * (size_t)n);
+    s.CAU = (double*)malloc(sizeof(double) * (size_t)n);
+    s.F = (double*)malloc(sizeof(double) * (size_t)n);
+    s.dF = (double*)calloc((size_t)mm * n, sizeof(double));
+    s.dG = (double*)calloc((size_t)mm * n, sizeof(double));
+    s.Pprev = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
     int32_t* P = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
-    int32_t* Pprev = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
-    double* C = (double*)malloc(sizeof(double) * (size_t)n);
-    double* Cnext = (double*)malloc(sizeof(double) * (size_t)n);
-    double* CAU = (double*)malloc(sizeof(double) * (size_t)n);
     double* G = (double*)malloc(sizeof(double) * (size_t)n);
-    double* F = (double*)malloc(sizeof(double) * (size_t)n);
-    orc_hist h;
-    hist_init(&h, m_max, n);
-    orc_info inf;
-    memset(&inf, 0, sizeof(inf));
+    double* Fn = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Cnext = (double*)malloc(sizeof(double) * (size_t)n);
 
     /* C^1 = C_AU^1 = G(C^0); F^0 = C^1 - C^0; E^0 = +inf.  P^0 = Assign(C^0). */
-    orc_assign(X, N, d, C0, K, Pprev, NULL, NULL);
-    inf.assign_passes = 1;
-    orc_update(X, N, d, Pprev, K, C0, G, NULL);
-    for (int64_t i = 0; i < n; ++i) F[i] = G[i] - C0[i];
-    hist_push(&h, G, F);
-    memcpy(C, G, sizeof(double) * (size_t)n);
-    memcpy(CAU, G, sizeof(double) * (size_t)n);
-    int from_lloyd = 1;
-    double E_prev = INFINITY, E_prev2 = INFINITY;
-    int m = p->m_init < m_max ? p->m_init : m_max;
-    if (m < 0) m = 0;
-    int done = 0;
-    int t;
-    for (t = 1; t <= p->max_iter; ++t) {
-        orc_trace rec;
-        memset(&rec, 0, sizeof(rec));
-        rec.t = t;
-        rec.accelerated = !from_lloyd;
-        rec.margin_lo = rec.margin_hi = NAN;
-        /* Check for convergence */
-        orc_assign(X, N, d, C, K, P, NULL, NULL);
-        inf.assign_passes++;
-        int64_t nch = count_changed(P, Pprev, N);
-        rec.n_changed = (int)nch;
-        int conv = nch <= thr;
-        if (conv && from_lloyd) {
-            double E = orc_energy(X, N, d, C, P);
-            rec.E_trial = rec.E = E;
-            rec.margin_safe = NAN;
-            rec.m = m;
-            if (trace) trace[t - 1] = rec;
-            inf.E = E;
-            done = 1;
-            break;
-        }
-        /* Adjust the value of m */
-        double Et = orc_energy(X, N, d, C, P);
-        rec.E_trial = Et;
-        if (!p->lloyd_only && !p->fixed_m && t >= 3) {
-            double num = E_prev - Et, den = E_prev2 - E_prev;
-            rec.margin_lo = num - p->eps1 * den;
-            rec.margin_hi = num - p->eps2 * den;
-        }
-        if (!p->lloyd_only && !p->fixed_m) m = orc_m_rule(m, m_max, t, Et, E_prev, E_prev2, p->eps1, p->eps2);
-        rec.m = m;
-        rec.margin_safe = Et - E_prev;
-        /* Make sure C^t decreases the energy */
-        int reject = !from_lloyd && (conv || Et >= E_prev);
-        if (reject) {
-            memcpy(C, CAU, sizeof(double) * (size_t)n);
-            orc_assign(X, N, d, C, K, P, NULL, NULL);
-            inf.assign_passes++;
-            inf.rejected++;
-            rec.rejected = 1;
-            Et = orc_energy(X, N, d, C, P);
-            nch = count_changed(P, Pprev, N);
-            if (nch <= thr) {
-                rec.E = Et;
-                if (trace) trace[t - 1] = rec;
-                inf.E = Et;
-                done = 1;
-                break;
-            }
-        } else if (!from_lloyd) {
-            inf.accepted++;
-        }
-        rec.E = Et;
-        /* Anderson acceleration */
-        orc_update(X, N, d, P, K, C, G, NULL);
-        memcpy(CAU, G, sizeof(double) * (size_t)n);
-        for (int64_t i = 0; i < n; ++i) F[i] = G[i] - C[i];
-        hist_push(&h, G, F);
-        int m_t = m < t ? m : t;
-        rec.m_t = m_t;
-        int rank = 0;
-        if (m_t > 0) {
-            rank = aa_mix(&h, m_t, p->rank_tol, Cnext, NULL);
-        } else {
-            memcpy(Cnext, G, sizeof(double) * (size_t)n);
-        }
-        rec.rank = rank;
-        from_lloyd = rank == 0;
-        E_prev2 = E_prev;
-        E_prev = Et;
-        memcpy(Pprev, P, sizeof(int32_t) * (size_t)N);
-        memcpy(C, Cnext, sizeof(double) * (size_t)n);
-        if (trace) trace[t - 1] = rec;
+    orc_assign(X, N, d, C0, K, s.Pprev, NULL, NULL);
+    s.assign_passes = 1;
+    orc_update(X, N, d, s.Pprev, K, C0, G, NULL);
+    for (int64_t i = 0; i < n; ++i) s.F[i] = G[i] - C0[i];
+    memcpy(s.C, G, sizeof(double) * (size_t)n);
+    memcpy(s.CAU, G, sizeof(double) * (size_t)n);
+    s.from_lloyd = 1;
+    s.E_prev = s.E_prev2 = INFINITY;
+    s.m = p->m_init < m_max ? p->m_init : m_max;
+    if (s.m < 0) s.m = 0;
+    s.t = 1;
+    while (s.t <= p->max_iter) {
+        const int t = s.t;
+        if (orc_step(X, N, d, K, p, &s, trace ? &trace[t - 1] : NULL, P, G, Fn, Cnext)) break;
     }
-    if (done) {
-        inf.iters = t;
+    orc_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.accepted = s.accepted;
+    inf.rejected = s.rejected;
+    inf.assign_passes = s.assign_passes;
+    if (s.done) {
+        inf.iters = s.t;
         inf.converged = 1;
-        memcpy(C_out, C, sizeof(double) * (size_t)n);
-        memcpy(rho_out, P, sizeof(int32_t) * (size_t)N);
+        inf.E = s.E;
+        memcpy(C_out, s.C, sizeof(double) * (size_t)n);
+        memcpy(rho_out, s.Pprev, sizeof(int32_t) * (size_t)N);
     } else {
         inf.iters = p->max_iter;
         inf.converged = 0;
-        memcpy(C_out, CAU, sizeof(double) * (size_t)n);
-        memcpy(rho_out, Pprev, sizeof(int32_t) * (size_t)N);
-        inf.E = orc_energy(X, N, d, CAU, Pprev);
+        memcpy(C_out, s.CAU, sizeof(double) * (size_t)n);
+        memcpy(rho_out, s.Pprev, sizeof(int32_t) * (size_t)N);
+        inf.E = orc_energy(X, N, d, s.CAU, s.Pprev);
     }
-    inf.m_final = m;
+    inf.m_final = s.m;
     if (info) *info = inf;
-    hist_free(&h);
+    free(s.C);
+    free(s.CAU);
+    free(s.F);
+    free(s.dF);
+    free(s.dG);
+    free(s.Pprev);
     free(P);
-    free(Pprev);
-    free(C);
-    free(Cnext);
-    free(CAU);
     free(G);
-    free(F);
+    free(Fn);
+    free(Cnext);
     return 0;
 }
 

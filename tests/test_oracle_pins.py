@@ -437,3 +437,27 @@ def test_kmeanspp_one_pick_per_separated_cluster():
     for s in range(5):
         idx, _ = oracle.kmeanspp(X, 10, np.random.default_rng(100 + s).random(10))
         assert sorted(lab[idx]) == list(range(10))
+
+
+# ------------------------------------------------------------------------------ one loop pass
+def test_step_reproduces_solve_pass_by_pass():
+    """``step`` is the body of ``solve``: driving it from Algorithm 1's first line gives the same
+    trace records, counts and result bit for bit (the step-parity tests start the GPU and the
+    oracle from one exported state through it)."""
+    X, C0 = datagen.small_2d(seed=1)
+    C_ref, rho_ref, info_ref, tr_ref = oracle.solve(X, C0, trace=True)
+    rho0, _, _ = oracle.assign(X, C0)
+    G, _ = oracle.update(X, rho0, C0.shape[0], C0)
+    st = dict(C=G.copy(), CAU=G.copy(), F=G - C0, count=0, Pprev=rho0, t=1, m=2, from_lloyd=1,
+              E_prev=math.inf, E_prev2=math.inf, assign_passes=1)
+    recs = []
+    while not st.get("done") and st["t"] <= 1000:
+        st, rec = oracle.step(X, st)
+        recs.append(rec)
+    assert [r["E"] for r in recs] == [r["E"] for r in tr_ref]
+    assert [(r["m"], r["rank"], r["rejected"]) for r in recs] == [(r["m"], r["rank"], r["rejected"]) for r in tr_ref]
+    assert (st["t"], st["accepted"], st["rejected"], st["assign_passes"]) == (
+        info_ref["iters"], info_ref["accepted"], info_ref["rejected"], info_ref["assign_passes"])
+    np.testing.assert_array_equal(st["C"], C_ref)
+    np.testing.assert_array_equal(st["Pprev"], rho_ref)
+    assert st["E"] == info_ref["E"]

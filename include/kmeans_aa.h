@@ -44,21 +44,28 @@ typedef enum {
  *               with a per-row error bound; rows whose top-2 gap is inside the bound are
  *               rescored in the direct form in FP32.
  *   KM_BF16_F32 X is float and a BF16 copy of X is supplied (kmeans_data.X_bf16); distances
- *               on tcgen05 tensor cores in BF16 with FP32 accumulation, near-tie rows rescored
- *               in FP32 from X.  Centroids are float.
+ *               on tcgen05 tensor cores as BF16 products with FP32 accumulation: X and the
+ *               centroids are each split into a BF16 high and low part and the product is the
+ *               sum hi.hi + lo.hi + hi.lo (three MMAs), within about 2e-4 |x||c| of the FP32
+ *               product; rows whose best two scores lie within that bound are rescored in FP32
+ *               from X.  Centroids are float.
  * In every mode centroid-space arithmetic (update, residuals, Anderson least squares, energy
  * comparison) is FP64. */
 typedef enum { KM_F64 = 0, KM_F32 = 1, KM_BF16_F32 = 2 } kmeans_prec;
 
-/* The samples.  X_bf16 must hold the BF16 rounding of X when prec == KM_BF16_F32 and is
- * ignored otherwise.  The struct itself lives in host memory; X and X_bf16 are device
- * pointers (host pointers for kmeans_solve_host). */
+/* The samples.  X_bf16 must hold the BF16 rounding of X (to nearest even) when prec ==
+ * KM_BF16_F32 and is ignored otherwise.  X_bf16_lo (KM_BF16_F32, optional) holds the BF16 rounding
+ * of X - X_bf16, the low part of the split the distance products use; NULL = the library computes it
+ * into its workspace (once per solve; on every kmeans_assign call).  The struct itself lives in host
+ * memory; X, X_bf16 and X_bf16_lo are device pointers (host pointers for kmeans_solve_host, which
+ * always computes the low part on the device). */
 typedef struct {
-    const void* X;       /* [N, d]: double for KM_F64, float otherwise */
-    const void* X_bf16;  /* [N, d] uint16 BF16 bit patterns, KM_BF16_F32 only */
+    const void* X;         /* [N, d]: double for KM_F64, float otherwise */
+    const void* X_bf16;    /* [N, d] uint16 BF16 bit patterns, KM_BF16_F32 only */
     int64_t N;
     int32_t d;
-    int32_t prec;        /* kmeans_prec */
+    int32_t prec;          /* kmeans_prec */
+    const void* X_bf16_lo; /* [N, d] uint16 BF16 bit patterns of X - X_bf16, or NULL */
 } kmeans_data;
 
 /* Solver parameters (Algorithm 1; defaults from kmeans_default_params):
@@ -69,7 +76,11 @@ typedef struct {
  *   eps1, eps2 thresholds of the dynamic-m rule (0.02, 0.5)
  *   tol       0 = stop when the assignment no longer changes (the paper's criterion);
  *             > 0 = stop when at most floor(tol*N) samples change cluster
- *   rank_tol  least-squares columns from the first with R_kk <= rank_tol*R_00 on are dropped
+ *   rank_tol  least-squares columns from the first with |R_kk| <= rank_tol*|R_00| on are dropped
+ *             (1e-12), R the triangular factor of the QR of dF (Eq. 7, newest difference first).
+ *             The solver reads R off the Cholesky factor of the FP64 Gram matrix while every pivot
+ *             ratio exceeds 1e-3 (there the two agree to about 1e-10) and otherwise factors dF by
+ *             Householder QR on the device (kmeans_info.ls_qr_solves counts those solves)
  *   fixed_m   1 = keep m at m_init for the whole solve (the fixed-m strategy that Section 3's
  *             "Settings of m" and Tab. 2 compare with the dynamic rule); 0 = dynamic m (default) */
 typedef struct {
@@ -97,6 +108,8 @@ typedef struct {
  *   device_ms      device time of the solve measured with CUDA events (batched solves: of the
  *                  whole batch)
  *   status         kmeans_status of this solve (KM_OK, KM_ENONFINITE, KM_ETIMEOUT)
+ *   ls_qr_solves   least-squares solves (Eq. 7) that took the Householder QR route because the
+ *                  Cholesky factor of the Gram matrix could not be certified (see kmeans_params)
  *   scanned_rows   rows whose assignment took a scan over all K centroids, summed over the passes
  *                  (the rest were settled by Hamerly bounds; 0 on the tensor-core path) */
 typedef struct {
@@ -110,7 +123,7 @@ typedef struct {
     int64_t rescored_rows;
     double device_ms;
     int32_t status;
-    int32_t reserved;
+    int32_t ls_qr_solves;
     int64_t scanned_rows;
 } kmeans_info;
 
@@ -201,6 +214,62 @@ kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
 kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* X_host, int32_t K,
                                 const void* C0_host, const kmeans_params* params,
                                 void* C_out_host, int32_t* rho_out_host, kmeans_info* info);
+
+/* Anderson least squares, Eq. 7, on the device:  theta = argmin || f - sum_j theta_j dF_j ||^2.
+ * The routine of the solver's step, callable on a history the caller supplies.
+ *   dF        [m][n] device doubles, difference j+1 contiguous at dF + j n; dF_1 (j = 0) is the
+ *             newest difference, the column order the rank rule below refers to
+ *   f         [n] device doubles (F^t)
+ *   m         1 <= m <= 32 columns;  n >= 1 rows (K*d in the solver)
+ *   rank_tol  columns from the first with |R_kk| <= rank_tol |R_00| on are dropped (theta = 0),
+ *             R the triangular factor of the QR of dF
+ *   method    0 = the solver's rule: the Cholesky factor of the Gram matrix dF^T dF when every
+ *             pivot ratio exceeds 1e-3, else Householder QR of [dF | f];  1 = Householder QR
+ *             always;  2 = the Gram matrix and its Cholesky factor always (a cross-check: it
+ *             squares the condition number)
+ *   theta     [m] device double output;  rank, qr_used: device int32 outputs (may be NULL):
+ *             columns kept, and 1 if the QR route ran
+ * One thread block, asynchronous on the context's stream; uses the context's workspace
+ * ((m + 1) n doubles and a small state), so the workspace state of an earlier solve is not kept.
+ * KM_EINVAL for NULL pointers or sizes out of range, KM_ENOMEM past the budget. */
+kmeans_status kmeans_lsq(kmeans_ctx* ctx, const double* dF, int64_t n, int32_t m, const double* f, double rank_tol,
+                         int32_t method, double* theta, int32_t* rank, int32_t* qr_used);
+
+/* The solver's state between two loop passes of Algorithm 1, copied to host memory by
+ * kmeans_solve_passes.  The caller supplies the buffers (NULL = not copied); the scalars are filled.
+ * After loop pass t (unless the solve ended in it):
+ *   C      [K*d] C^{t+1}, the iterate the next pass assigns (the accelerated point, or G^t)
+ *   C_AU   [K*d] G^t = Update(P^t) (Algorithm 1's C_AU, the revert target of the next pass)
+ *   F      [K*d] F^t = G^t - C^t
+ *   dF, dG [m_max][K*d] the differences dF_j = F^{t-j+1} - F^{t-j}, dG_j likewise, newest first
+ *          (ring_count of them)
+ *   rho    [N] P^t
+ *   t      the next pass's t;  m  the current m;  m_t, rank  history length and columns kept by
+ *          the last least-squares solve;  theta  its solution (0 past the rank);  from_lloyd 1 if
+ *          C is a plain Lloyd iterate;  E_prev, E_prev2  the stored E^t, E^{t-1};  E_trial  E of
+ *          the last pass's proposed iterate;  done / converged  the solve ended (then C and rho
+ *          hold its result);  accepted, rejected, passes, ls_qr_solves  counters so far.
+ * All arithmetic of the state is FP64 whatever the precision of X. */
+typedef struct {
+    double* C;
+    double* C_AU;
+    double* F;
+    double* dF;
+    double* dG;
+    int32_t* rho;
+    int32_t t, m, m_t, rank, from_lloyd, ring_count, done, converged;
+    int32_t accepted, rejected, passes, ls_qr_solves;
+    double E_prev, E_prev2, E_trial;
+    double theta[32];
+} kmeans_state;
+
+/* The solver of kmeans_solve stopped after `passes` loop passes (earlier if it ends), with its
+ * state copied to *state: the prologue and each loop pass run the same kernels as kmeans_solve,
+ * launched pass by pass from the host.  It exists to check single steps of Algorithm 1 against an
+ * independent implementation started from the same state.  C0 and params as for kmeans_solve;
+ * passes >= 0.  Synchronous. */
+kmeans_status kmeans_solve_passes(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const void* C0,
+                                  const kmeans_params* params, int32_t passes, kmeans_state* state);
 
 /* One instance of a batched solve.  All pointers are device pointers owned by the caller. */
 typedef struct {
@@ -295,9 +364,17 @@ const char* kmeans_server_last_error(const kmeans_server* srv);
  *   - Low-d path only: 1 <= d <= 16 (KM_F64, KM_F32; KM_BF16_F32 is treated as KM_F32).
  *   - Scratch: a fixed array of 8 MiB in device memory that the library holds on every GPU that
  *     loads it, until the process exits.  The array stores one block partial of K*d sums and K
- *     counts per thread block; shapes whose single block partial does not fit return KM_EINVAL.
+ *     counts per thread block.  Shapes are limited first by the pass kernel's shared memory (the
+ *     same limit as kmeans_update: K <= 168 in FP64 at d = 16); a shape within that
+ *     limit whose single block partial did not fit in 8 MiB would return KM_EINVAL.
+ *   - The pass uses kmeans_update's block count for the shape when the array holds that many
+ *     block partials (then the two calls agree bit for bit), else as many as it holds (still
+ *     deterministic for a given device; FP32 results may then differ from kmeans_update's in the
+ *     last bits).
  *   - The first call on a device looks the array's address up (cudaGetSymbolAddress, with that
- *     device current) and caches it; later calls on that device reuse the cached address.
+ *     device current) and caches it for that device's current CUDA context; a call under a new
+ *     context (after cudaDeviceReset) looks it up again.  Make the first call on a device before
+ *     any stream capture.
  *   - Every call shares the array and leaves its contents behind; each call clears what must
  *     start at zero.  Calls that overlap on the GPU (other streams, unordered host threads) race
  *     on the array: serialise them.

@@ -29,7 +29,7 @@ class KmeansError(RuntimeError):
 
 class kmeans_data(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("X_bf16", ctypes.c_void_p), ("N", ctypes.c_int64),
-                ("d", ctypes.c_int32), ("prec", ctypes.c_int32)]
+                ("d", ctypes.c_int32), ("prec", ctypes.c_int32), ("X_bf16_lo", ctypes.c_void_p)]
 
 
 class kmeans_params(ctypes.Structure):
@@ -47,11 +47,21 @@ class kmeans_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
                 ("assign_passes", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("m_final", ctypes.c_int32), ("E", ctypes.c_double), ("rescored_rows", ctypes.c_int64),
-                ("device_ms", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("device_ms", ctypes.c_double), ("status", ctypes.c_int32), ("ls_qr_solves", ctypes.c_int32),
                 ("scanned_rows", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class kmeans_state(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_void_p), ("C_AU", ctypes.c_void_p), ("F", ctypes.c_void_p), ("dF", ctypes.c_void_p),
+                ("dG", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("t", ctypes.c_int32), ("m", ctypes.c_int32), ("m_t", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("from_lloyd", ctypes.c_int32), ("ring_count", ctypes.c_int32), ("done", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("accepted", ctypes.c_int32), ("rejected", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("ls_qr_solves", ctypes.c_int32), ("E_prev", ctypes.c_double),
+                ("E_prev2", ctypes.c_double), ("E_trial", ctypes.c_double), ("theta", ctypes.c_double * 32)]
 
 
 class kmeans_server_stats(ctypes.Structure):
@@ -100,6 +110,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmeans_solve_host.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), vp, vp,
                                     ctypes.POINTER(kmeans_info)]
     L.kmeans_update_static.argtypes = [pd, vp, i32, vp, vp, vp, vp]
+    L.kmeans_lsq.argtypes = [vp, vp, i64, i32, vp, ctypes.c_double, i32, vp, vp, vp]
+    L.kmeans_solve_passes.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), i32,
+                                      ctypes.POINTER(kmeans_state)]
     L.kmeans_solve_batched.argtypes = [vp, ctypes.POINTER(kmeans_problem), i32, ctypes.POINTER(kmeans_params),
                                        ctypes.POINTER(kmeans_info)]
     L.kmeans_batch_describe.argtypes = [vp]
@@ -115,7 +128,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmeans_server_last_error.restype = ctypes.c_char_p
     for name in ("kmeans_create", "kmeans_destroy", "kmeans_set_stream", "kmeans_assign",
                  "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host",
-                 "kmeans_update_static", "kmeans_solve_batched", "kmeans_server_create",
+                 "kmeans_update_static", "kmeans_lsq", "kmeans_solve_passes", "kmeans_solve_batched", "kmeans_server_create",
                  "kmeans_server_destroy", "kmeans_server_submit", "kmeans_server_step",
                  "kmeans_server_poll", "kmeans_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
@@ -146,9 +159,10 @@ def _prec_of(X, X_bf16=None) -> int:
     raise TypeError(f"X must be float64 or float32, got {dt}")
 
 
-def make_data(X, X_bf16=None) -> kmeans_data:
+def make_data(X, X_bf16=None, X_lo=None) -> kmeans_data:
+    """X_bf16: the BF16 rounding of X (tensor-core path); X_lo: optional BF16 rounding of X - X_bf16."""
     assert X.ndim == 2 and (X.is_contiguous() if torch.is_tensor(X) else X.flags.c_contiguous)
-    return kmeans_data(_ptr(X), _ptr(X_bf16), X.shape[0], X.shape[1], _prec_of(X, X_bf16))
+    return kmeans_data(_ptr(X), _ptr(X_bf16), X.shape[0], X.shape[1], _prec_of(X, X_bf16), _ptr(X_lo))
 
 
 def default_params(**kw) -> kmeans_params:
@@ -190,12 +204,12 @@ class Context:
         return int(load().kmeans_workspace_bytes(self.handle))
 
 
-def kmeans_assign(ctx: Context, X, C, rho=None, rho_prev=None, n_changed=None, dmin=None, X_bf16=None):
+def kmeans_assign(ctx: Context, X, C, rho=None, rho_prev=None, n_changed=None, dmin=None, X_bf16=None, X_lo=None):
     """Eq. 3 on the device; returns rho (int32 [N])."""
     N = X.shape[0]
     if rho is None:
         rho = torch.empty(N, dtype=torch.int32, device=X.device)
-    data = make_data(X, X_bf16)
+    data = make_data(X, X_bf16, X_lo)
     _check(ctx, load().kmeans_assign(ctx.handle, ctypes.byref(data), _ptr(C), C.shape[0], _ptr(rho),
                                      _ptr(rho_prev), _ptr(n_changed), _ptr(dmin)))
     return rho
@@ -217,18 +231,23 @@ def kmeans_update_static(X, rho, K: int, C_prev, C_out=None, counts=None, stream
     """kmeans_update without allocation (no context; scratch in a fixed device array).
 
     For callers that must not allocate device memory: pass C_out and counts, otherwise this
-    wrapper allocates them with torch before the call.  Runs on `stream` (default: torch's
-    current stream of X's device); returns (C_out, counts).
+    wrapper allocates them with torch before the call.  Runs on X's device (made current for the
+    call) and on `stream` (default: torch's current stream of that device); returns (C_out, counts).
     """
-    if C_out is None:
-        C_out = torch.empty_like(C_prev)
-    if counts is None:
-        counts = torch.empty(K, dtype=torch.int64, device=X.device)
-    if stream is None:
-        stream = torch.cuda.current_stream(X.device).cuda_stream
-    data = make_data(X)
-    st = load().kmeans_update_static(ctypes.byref(data), _ptr(rho), K, _ptr(C_prev), _ptr(C_out), _ptr(counts),
-                                     ctypes.c_void_p(stream))
+    dev = X.device
+    for name, t in (("rho", rho), ("C_prev", C_prev), ("C_out", C_out), ("counts", counts)):
+        if t is not None and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, X on {dev}")
+    with torch.cuda.device(dev):
+        if C_out is None:
+            C_out = torch.empty_like(C_prev)
+        if counts is None:
+            counts = torch.empty(K, dtype=torch.int64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        data = make_data(X)
+        st = load().kmeans_update_static(ctypes.byref(data), _ptr(rho), K, _ptr(C_prev), _ptr(C_out), _ptr(counts),
+                                         ctypes.c_void_p(stream))
     if st != KM_OK:
         raise KmeansError(st, "kmeans_update_static failed")
     return C_out, counts
@@ -259,13 +278,13 @@ def kmeans_seed_pp(ctx: Context, X, K: int, u, C_out=None, idx_out=None):
     return C_out, idx_out
 
 
-def kmeans_solve(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, **params):
+def kmeans_solve(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None, X_lo=None, **params):
     """Lloyd (lloyd_only=1) or Algorithm 1 on the device; returns (C, rho, info dict)."""
     if C_out is None:
         C_out = torch.empty_like(C0)
     if rho_out is None:
         rho_out = torch.empty(X.shape[0], dtype=torch.int32, device=X.device)
-    data = make_data(X, X_bf16)
+    data = make_data(X, X_bf16, X_lo)
     p = default_params(**params)
     info = kmeans_info()
     _check(ctx, load().kmeans_solve(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0), ctypes.byref(p),
@@ -286,6 +305,44 @@ def kmeans_solve_host(ctx: Context, X, C0, C_out=None, rho_out=None, X_bf16=None
     _check(ctx, load().kmeans_solve_host(ctx.handle, ctypes.byref(data), C0.shape[0], _ptr(C0),
                                          ctypes.byref(p), _ptr(C_out), _ptr(rho_out), ctypes.byref(info)))
     return C_out, rho_out, info.as_dict()
+
+
+def kmeans_lsq(ctx: Context, dF, f, rank_tol: float = 1e-12, method: int = 0, theta=None):
+    """Eq. 7 on the device for a caller's history.  dF: float64 device tensor [m, n] (row j = the
+    difference dF_{j+1}, row 0 the newest), f: [n].  method 0 = the solver's rule, 1 = Householder
+    QR, 2 = Gram matrix + Cholesky.  Returns (theta [m] device tensor, rank, qr_used)."""
+    m, n = dF.shape
+    if theta is None:
+        theta = torch.empty(m, dtype=torch.float64, device=dF.device)
+    out = torch.zeros(2, dtype=torch.int32, device=dF.device)
+    _check(ctx, load().kmeans_lsq(ctx.handle, _ptr(dF), n, m, _ptr(f), float(rank_tol), int(method), _ptr(theta),
+                                  out.data_ptr(), out.data_ptr() + 4))
+    r = out.cpu().tolist()
+    return theta, r[0], r[1]
+
+
+def kmeans_solve_passes(ctx: Context, X, C0, passes: int, X_bf16=None, **params):
+    """The solver stopped after `passes` loop passes; returns its state as a dict of numpy arrays
+    (C, C_AU, F, dF and dG newest first, rho) and scalars (see kmeans_state in the header)."""
+    K, d = C0.shape
+    N = X.shape[0]
+    p = default_params(**params)
+    m_max = 0 if p.lloyd_only else p.m_max
+    n = K * d
+    bufs = dict(C=np.empty((K, d)), C_AU=np.empty((K, d)), F=np.empty((K, d)),
+                dF=np.empty((max(m_max, 1), n)), dG=np.empty((max(m_max, 1), n)), rho=np.empty(N, np.int32))
+    st = kmeans_state()
+    for k, v in bufs.items():
+        setattr(st, k, v.ctypes.data)
+    data = make_data(X, X_bf16)
+    _check(ctx, load().kmeans_solve_passes(ctx.handle, ctypes.byref(data), K, _ptr(C0), ctypes.byref(p), int(passes),
+                                           ctypes.byref(st)))
+    out = {f: getattr(st, f) for f, _ in kmeans_state._fields_ if f not in bufs and f != "theta"}
+    out["theta"] = np.array(st.theta[:], np.float64)
+    out.update(bufs)
+    out["dF"] = bufs["dF"][:st.ring_count]
+    out["dG"] = bufs["dG"][:st.ring_count]
+    return out
 
 
 def kmeans_solve_batched(ctx: Context, Xs, C0s, C_outs=None, rho_outs=None, params=None, check=True,

@@ -31,11 +31,16 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Least squares of Eq. 7 from the Gram matrix, by one warp: columns a = 0..mt-1 are ring slots
 // (hnew - a) mod m_max (a = 0 newest).  Right-looking Cholesky M = L L^T in shared memory, lane r
-// owning row r, with 1/L_kk from rsqrt (no divisions); columns from the first with
-// L_kk <= rank_tol * L_00 on are dropped.  Forward and back substitution give theta.
-// Returns the rank (in every lane); theta[0..MMAX) in shared memory.
-__device__ __forceinline__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
-                       double* sInv, double* sV)
+// owning row r, with 1/L_kk from rsqrt (no divisions).  The Cholesky factor of the Gram matrix is
+// the R of the QR of dF, but its small pivots carry an error of about u (L_00 / L_kk)^2 relative
+// (the Gram matrix squares the condition number).  So the factor is only trusted while every
+// pivot ratio L_kk / L_00 stays above cert_tol: a column from the first with L_kk <= rank_tol *
+// L_00 on is then dropped as the QR would drop it.  A pivot ratio at or below cert_tol (cert_tol >
+// 0) stops the factorisation with *uncert = 1 and the caller solves by Householder QR instead
+// (ls_qr_block).  cert_tol = 0 trusts every pivot (the Gram route alone).  Forward and back
+// substitution give theta.  Returns the rank (in every lane); theta[0..MMAX) in shared memory.
+__device__ __forceinline__ int ls_warp(const SolveState* st, int hnew, int m_max, int mt, double rank_tol,
+                                       double cert_tol, int* uncert, double* sM, double* sInv, double* sV)
 {
     const int lane = threadIdx.x & 31;
     const int sr = lane < mt ? (hnew - lane + m_max) % m_max : 0;
@@ -52,7 +57,12 @@ __device__ __forceinline__ int ls_warp(const SolveState* st, int hnew, int m_max
         const double r = piv > 0.0 ? rsqrt(piv) : 0.0;
         const double lkk = piv * r;
         if (k == 0) l00 = lkk;
-        if (l00 == 0.0 || !(lkk > rank_tol * l00)) break;
+        if (l00 == 0.0) break;
+        if (cert_tol > 0.0 && !(lkk > cert_tol * l00)) {
+            *uncert = 1;
+            break;
+        }
+        if (!(lkk > rank_tol * l00)) break;
         __syncwarp();
         if (lane > k && lane < mt) sM[lane * MMAX + k] *= r;
         if (lane == k) {
@@ -90,8 +100,8 @@ __device__ __forceinline__ int ls_warp(const SolveState* st, int hnew, int m_max
 // the rank-1 updates of a column are independent FMAs instead of a chain through shared memory.
 // Every FP64 operation and its order match ls_warp, so the results are bitwise the same.
 template <int MB>
-__device__ __forceinline__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, double rank_tol, double* sM,
-                           double* sV)
+__device__ __forceinline__ int ls_warp_reg(const SolveState* st, int hnew, int m_max, int mt, double rank_tol,
+                                           double cert_tol, int* uncert, double* sM, double* sV)
 {
     const int lane = threadIdx.x & 31;
     const int sr = lane < mt ? (hnew >= lane ? hnew - lane : hnew - lane + m_max) : 0;   // mt <= m_max
@@ -114,7 +124,10 @@ __device__ __forceinline__ int ls_warp_reg(const SolveState* st, int hnew, int m
             const double r = piv > 0.0 ? rsqrt(piv) : 0.0;
             const double lkk = piv * r;
             if (k == 0) l00 = lkk;
-            if (l00 == 0.0 || !(lkk > rank_tol * l00)) {
+            if (l00 != 0.0 && cert_tol > 0.0 && !(lkk > cert_tol * l00)) {
+                *uncert = 1;
+                go = false;
+            } else if (l00 == 0.0 || !(lkk > rank_tol * l00)) {
                 go = false;
             } else {
                 if (lane > k && lane < mt) m[k] *= r;
@@ -150,6 +163,103 @@ __device__ __forceinline__ int ls_warp_reg(const SolveState* st, int hnew, int m
     }
     sV[lane] = lane < rank ? v : 0.0;
     __syncwarp();
+    return rank;
+}
+
+// Least squares of Eq. 7 by Householder QR of [dF | f], by one whole block: the path taken when the
+// Gram route cannot certify the factor (ls_warp / ls_warp_reg) and the one the QR-only mode
+// always takes.  Column q < mt of the n x (mt + 1) working matrix W (global scratch, column-major)
+// is the ring slot sl[q] of dF (q = 0 newest); column mt is f = F^t.  Step k reflects rows k..n-1
+// with H_k = I - 2 v v^T / (v^T v), v = a_k - alpha e_k, alpha = -sign(a_kk) ||a_k||, R_kk = alpha;
+// the reflector is applied to the later columns and to f, so f's column ends as Q^T f.  As in the
+// oracle, the first column with |R_kk| <= rank_tol |R_00| (or R_00 = 0) and every later (older) one
+// are dropped (theta = 0).  The dot products of a step are summed per thread over fixed rows, then
+// over lanes and warps in a fixed order, so the result is the same on every run.  Cost: about
+// n (mt + 1)(mt + 2) FP64 FMAs on one SM; on data where the Gram route certifies the factor
+// (every pivot ratio above cert_tol) it never runs.  Returns the rank; th[0..MMAX) in shared memory.
+__device__ __noinline__ int ls_qr_block(const double* dF, const int* sl, int mt, const double* f, size_t n,
+                                        double rank_tol, double* W, double* th)
+{
+    constexpr int CW = 8;                                  // columns per sweep of the dot products
+    __shared__ double s_R[MMAX * (MMAX + 1)];             // row k: R_kj (j < mt) and (Q^T f)_k (j = mt)
+    __shared__ double s_red[(FIN_THREADS / 32) * CW];
+    __shared__ double s_dot[MMAX + 1];
+    __shared__ double s_w[MMAX + 1];
+    __shared__ double s_r00;
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nc = mt + 1;
+    for (int q = 0; q < nc; ++q) {
+        const double* src = q < mt ? dF + (size_t)sl[q] * n : f;
+        for (size_t i = tid; i < n; i += blockDim.x) W[(size_t)q * n + i] = __ldcg(src + i);
+    }
+    __syncthreads();
+    const int steps = (size_t)mt < n ? mt : (int)n;
+    int rank = 0;
+    for (int k = 0; k < steps; ++k) {
+        const double* ak = W + (size_t)k * n;
+        for (int j0 = k; j0 < nc; j0 += CW) {              // s_dot[j] = sum_{i >= k} a_ik a_ij, j = k..mt
+            double acc[CW];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) acc[c] = 0.0;
+            for (size_t i = (size_t)k + tid; i < n; i += blockDim.x) {
+                const double v = ak[i];
+#pragma unroll
+                for (int c = 0; c < CW; ++c)
+                    if (j0 + c < nc) acc[c] = fma(v, W[(size_t)(j0 + c) * n + i], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                const double v = warp_sum(acc[c]);
+                if (lane == 0) s_red[warp * CW + c] = v;
+            }
+            __syncthreads();
+            if (tid < CW && j0 + tid < nc) {
+                double v = 0.0;
+                for (int w = 0; w < nw; ++w) v += s_red[w * CW + tid];
+                s_dot[j0 + tid] = v;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const double nrm2 = s_dot[k], akk = ak[k];
+            const double nrm = sqrt(nrm2);
+            const double alpha = akk >= 0.0 ? -nrm : nrm;
+            const double rkk = fabs(alpha);
+            if (k == 0) s_r00 = rkk;
+            const int stop = s_r00 == 0.0 || rkk <= rank_tol * s_r00;
+            if (!stop) {
+                const double vk = akk - alpha;
+                const double vtv = 2.0 * (nrm2 - alpha * akk);     // ||a_k - alpha e_k||^2
+                s_R[k * (MMAX + 1) + k] = alpha;
+                for (int j = k + 1; j < nc; ++j) {
+                    const double ajk = W[(size_t)j * n + k];
+                    const double w = 2.0 * (s_dot[j] - alpha * ajk) / vtv;   // 2 v.a_j / v.v
+                    s_w[j] = w;
+                    s_R[k * (MMAX + 1) + j] = ajk - w * vk;
+                }
+            }
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        rank = k + 1;
+        for (size_t i = (size_t)k + 1 + tid; i < n; i += blockDim.x) {   // rows below k: v_i = a_ik
+            const double v = ak[i];
+            for (int j = k + 1; j < nc; ++j) W[(size_t)j * n + i] = fma(-s_w[j], v, W[(size_t)j * n + i]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {                                        // R[0:rank, 0:rank] theta = (Q^T f)[0:rank]
+        for (int k = rank - 1; k >= 0; --k) {
+            double v = s_R[k * (MMAX + 1) + mt];
+            for (int j = k + 1; j < rank; ++j) v -= s_R[k * (MMAX + 1) + j] * th[j];
+            th[k] = v / s_R[k * (MMAX + 1) + k];
+        }
+    }
+    __syncthreads();
+    if (tid >= rank && tid < MMAX) th[tid] = 0.0;
+    __syncthreads();
     return rank;
 }
 
@@ -238,6 +348,7 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
     __shared__ double s_th[MMAX];
     __shared__ int s_sl[MMAX];
     __shared__ int s_rank;
+    __shared__ int s_unc;
     __shared__ unsigned int s_last;
 
     // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
@@ -425,19 +536,33 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
             st->ring_count = min(count + 1, m_max);
         }
         __syncthreads();
+        // theta: the certified Gram route (one warp), else Householder QR over the ring (whole block)
+        const int mt = min(min(st->m, st->t), st->ring_count);
         if (warp == 0) {
-            const int mt = min(min(st->m, st->t), st->ring_count);
-            int rank = 0;
-            if (mt > 0)
-                rank = m_max <= 16 ? ls_warp_reg<16>(st, hnew, m_max, mt, a.rank_tol, s_M, s_th)
-                                   : ls_warp(st, hnew, m_max, mt, a.rank_tol, s_M, s_inv, s_th);
-            if (mt == 0) s_th[lane] = 0.0;
-            st->theta[lane] = s_th[lane];
             s_sl[lane] = (hnew - lane + m_max) % m_max;
-            if (lane == 0) {
-                s_rank = rank;
-                st->m_t = mt;
+            if (lane == 0) s_unc = 0;
+            __syncwarp();
+            int rank = 0;
+            if (mt > 0 && a.ls_mode != LS_QR) {
+                const double ct = a.ls_mode == LS_GRAM ? 0.0 : LS_CERT_TOL;
+                rank = m_max <= 16 ? ls_warp_reg<16>(st, hnew, m_max, mt, a.rank_tol, ct, &s_unc, s_M, s_th)
+                                   : ls_warp(st, hnew, m_max, mt, a.rank_tol, ct, &s_unc, s_M, s_inv, s_th);
             }
+            if (mt == 0) s_th[lane] = 0.0;
+            if (lane == 0) s_rank = rank;
+        }
+        __syncthreads();
+        if (mt > 0 && (a.ls_mode == LS_QR || s_unc)) {
+            const int rank = ls_qr_block(a.dF, s_sl, mt, a.Fprev, n, a.rank_tol, a.qrw, s_th);
+            if (tid == 0) {
+                s_rank = rank;
+                st->ls_qr += 1;
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            st->theta[lane] = s_th[lane];
+            if (lane == 0) st->m_t = mt;
         }
     } else if (tid == 0) {
         s_rank = 0;
@@ -658,7 +783,7 @@ __global__ void __launch_bounds__(1024) k_prep_batch(BatchPrep b)
 }
 
 struct DevInfo {
-    int iters, accepted, rejected, passes, converged, m_final, status, pad;
+    int iters, accepted, rejected, passes, converged, m_final, status, ls_qr;
     double E;
     long long rescored;
     long long scanned;
@@ -683,7 +808,7 @@ __device__ __forceinline__ void epi_body(const SolveState* st, const double* C64
         f.converged = st->converged;
         f.m_final = st->m;
         f.status = st->status;
-        f.pad = 0;
+        f.ls_qr = st->ls_qr;
         f.E = st->E_final;
         f.rescored = st->rescored;
         f.scanned = st->scanned;
@@ -746,6 +871,86 @@ __global__ void __launch_bounds__(256) k_batch_done(BatchDone b)
     }
 }
 
+// kmeans_lsq: Eq. 7 for a caller's history by one block, with the solver's routines.  The Gram
+// matrix and right-hand side are formed in full (p <= q dot products of length n), placed in the
+// ring slots the solver's Cholesky reads (column c at slot (m - c) mod m, newest at slot 0), then
+// the certified Gram route or the Householder QR as in k_fin.
+__global__ void __launch_bounds__(FIN_THREADS) k_lsq(LsqArgs a)
+{
+    constexpr int CW = 8;
+    __shared__ double s_red[(FIN_THREADS / 32) * CW];
+    __shared__ double s_M[MMAX * MMAX];
+    __shared__ double s_inv[MMAX];
+    __shared__ double s_th[MMAX];
+    __shared__ int s_sl[MMAX];
+    __shared__ int s_unc, s_rank;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int m = a.m;
+    const size_t n = a.n;
+    SolveState* st = a.st;
+    auto slot = [&](int c) { return (m - c) % m; };
+    if (a.mode != LS_QR) {
+        for (int p = 0; p < m; ++p) {
+            const double* ap = a.dF + (size_t)p * n;
+            for (int q0 = p; q0 <= m; q0 += CW) {          // q = m: the right-hand side <dF_p, f>
+                double acc[CW];
+#pragma unroll
+                for (int c = 0; c < CW; ++c) acc[c] = 0.0;
+                for (size_t i = tid; i < n; i += blockDim.x) {
+                    const double v = ap[i];
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) {
+                        const int q = q0 + c;
+                        if (q <= m) acc[c] = fma(v, q < m ? a.dF[(size_t)q * n + i] : a.f[i], acc[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    const double v = warp_sum(acc[c]);
+                    if (lane == 0) s_red[warp * CW + c] = v;
+                }
+                __syncthreads();
+                if (tid < CW && q0 + tid <= m) {
+                    double v = 0.0;
+                    for (int w = 0; w < nw; ++w) v += s_red[w * CW + tid];
+                    const int q = q0 + tid;
+                    if (q == m) {
+                        st->bvec[slot(p)] = v;
+                    } else {
+                        st->gram[slot(p) * MMAX + slot(q)] = v;
+                        st->gram[slot(q) * MMAX + slot(p)] = v;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (warp == 0) {
+        s_sl[lane] = lane;                                   // the caller's column q is at dF + q n
+        if (lane == 0) s_unc = 0;
+        __syncwarp();
+        int rank = 0;
+        if (a.mode != LS_QR) {
+            const double ct = a.mode == LS_GRAM ? 0.0 : LS_CERT_TOL;
+            rank = m <= 16 ? ls_warp_reg<16>(st, 0, m, m, a.rank_tol, ct, &s_unc, s_M, s_th)
+                           : ls_warp(st, 0, m, m, a.rank_tol, ct, &s_unc, s_M, s_inv, s_th);
+        }
+        if (lane == 0) s_rank = rank;
+    }
+    __syncthreads();
+    const int qr = a.mode == LS_QR || s_unc;
+    if (qr) {
+        const int rank = ls_qr_block(a.dF, s_sl, m, a.f, n, a.rank_tol, a.W, s_th);
+        if (tid == 0) s_rank = rank;
+        __syncthreads();
+    }
+    if (tid < m) a.theta[tid] = s_th[tid];
+    if (tid == 0) {
+        if (a.rank) *a.rank = s_rank;
+        if (a.qr_used) *a.qr_used = qr;
+    }
+}
+
 }  // namespace
 
 int fin_blocks(int K, int d, int* KB)
@@ -762,13 +967,22 @@ size_t fin_smem(int KB, int d)
     return sizeof(double) * ((size_t)E + 2 * (size_t)KB * d + 2 * FIN_THREADS + 2 * MMAX * 8);
 }
 
+// A launch whose dynamic shared memory plus the kernel's static shared memory exceeds 48 KB needs
+// the kernel's opt-in limit raised first.
+cudaError_t allow_dyn_smem(const void* fn, size_t dyn)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes + dyn <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s)
 {
     const size_t smem = fin_smem(a.KB, a.d);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_dyn_smem(reinterpret_cast<const void*>(k_fin), smem);
+    if (e != cudaSuccess) return e;
     k_fin<<<nblocks, FIN_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -809,12 +1023,16 @@ cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const 
 
 size_t devinfo_bytes() { return sizeof(DevInfo); }
 
+cudaError_t launch_lsq(const LsqArgs& a, cudaStream_t s)
+{
+    k_lsq<<<1, FIN_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fin_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_dyn_smem(reinterpret_cast<const void*>(k_fin_batch), smem);
+    if (e != cudaSuccess) return e;
     k_fin_batch<<<grid, FIN_THREADS, smem, s>>>(b);
     return cudaGetLastError();
 }

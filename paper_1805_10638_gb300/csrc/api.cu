@@ -49,6 +49,7 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     memset(&key, 0, sizeof(key));
     key.X = X->X;
     key.Xb = X->X_bf16;
+    key.Xl = X->X_bf16_lo;
     key.N = X->N;
     key.d = X->d;
     key.K = K;
@@ -60,6 +61,7 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     key.arena = ctx->arena;
     key.arena_bytes = ctx->arena_bytes;
     key.ham = P.ham ? 1 : 0;
+    key.lsq = ls_mode();
     const Launch L = make_launch(arena_base(ctx), ctx->nsm, P, X, K, C0, p, C_out, rho_out);
     if (!L.maps_ok) return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
     const bool use_graph = graph_mode();
@@ -117,12 +119,17 @@ kmeans_status dense_assign_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
     a.rho_out = rho;
     a.rho_prev = rho_prev;
     a.out_nch = reinterpret_cast<long long*>(n_changed);
-    alignas(64) unsigned char tmX[128], tmC[128], tmC1[128];
-    if (!dense_maps(arena_base(ctx), P, X->X_bf16, X->N, X->d, tmX, tmC, tmC1))
-        return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
+    const void* xlo = dense_xlo(arena_base(ctx), P, X);
+    DenseMaps maps;
+    if (!dense_maps(arena_base(ctx), P, X->X_bf16, xlo, X->N, X->d, &maps))
+        return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 and X_bf16_lo must be 16-byte aligned)");
+    maps.ch[1] = maps.ch[0];
+    maps.cl[1] = maps.cl[0];
     KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    if (!X->X_bf16_lo)
+        KM_CUDA(launch_xsplit(X32, X->X_bf16, const_cast<void*>(xlo), X->N * (int64_t)X->d, ctx->nsm, ctx->stream));
     if ((s = dense_pack_user(ctx, P, C, X->d, K)) != KM_OK) return s;
-    KM_CUDA(launch_dense_pass(a, tmX, tmC, tmC, ctx->nsm, ctx->stream));
+    KM_CUDA(launch_dense_pass(a, maps, ctx->nsm, ctx->stream));
     if (n_changed || dmin)
         KM_CUDA(launch_drow(a, rho, reinterpret_cast<float*>(dmin), at<double>(arena_base(ctx), P.rowe), at<long long>(arena_base(ctx), P.rown),
                             rowred_blocks(ctx), ctx->stream));
@@ -186,7 +193,7 @@ void kmeans_default_params(kmeans_params* p)
     p->eps1 = 0.02;
     p->eps2 = 0.5;
     p->tol = 0.0;
-    p->rank_tol = 1e-6;
+    p->rank_tol = 1e-12;
     p->fixed_m = 0;
 }
 
@@ -401,6 +408,7 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t 
     kmeans_data Xd = *Xh;
     Xd.X = at<void>(arena_base(ctx), P.hX);
     Xd.X_bf16 = nullptr;
+    Xd.X_bf16_lo = nullptr;         // the prologue splits X on the device
     if (P.dense) {
         KM_CUDA(cudaMemcpyAsync(at<void>(arena_base(ctx), P.hXb), Xh->X_bf16, (size_t)Xh->N * Xh->d * 2, cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -414,6 +422,97 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t 
                             ctx->stream));
     KM_CUDA(cudaStreamSynchronize(ctx->stream));
     return s;
+}
+
+kmeans_status kmeans_lsq(kmeans_ctx* ctx, const double* dF, int64_t n, int32_t m, const double* f, double rank_tol,
+                         int32_t method, double* theta, int32_t* rank, int32_t* qr_used)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!dF || !f || !theta) return fail(ctx, KM_EINVAL, "dF, f and theta must not be NULL");
+    if (n < 1 || m < 1 || m > MMAX) return fail(ctx, KM_EINVAL, "need n >= 1 and 1 <= m <= 32");
+    if (method < 0 || method > 2) return fail(ctx, KM_EINVAL, "method must be 0, 1 or 2");
+    if (!(rank_tol >= 0.0)) return fail(ctx, KM_EINVAL, "rank_tol must be >= 0");
+    KM_CUDA(cudaSetDevice(ctx->device));
+    const size_t st_off = 0, w_off = al256(sizeof(SolveState));
+    const size_t total = w_off + al256((size_t)(m + 1) * (size_t)n * 8);
+    kmeans_status s = ensure_arena(ctx, total);
+    if (s != KM_OK) return s;
+    LsqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.dF = dF;
+    a.f = f;
+    a.n = (size_t)n;
+    a.m = m;
+    a.mode = method == 1 ? LS_QR : (method == 2 ? LS_GRAM : LS_AUTO);
+    a.rank_tol = rank_tol;
+    a.W = at<double>(arena_base(ctx), w_off);
+    a.st = at<SolveState>(arena_base(ctx), st_off);
+    a.theta = theta;
+    a.rank = rank;
+    a.qr_used = qr_used;
+    KM_CUDA(launch_lsq(a, ctx->stream));
+    return KM_OK;
+}
+
+kmeans_status kmeans_solve_passes(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, const void* C0,
+                                  const kmeans_params* params, int32_t passes, kmeans_state* state)
+{
+    if (!ctx) return KM_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kmeans_status s = check_data(ctx, X, K, true);
+    if (s != KM_OK) return s;
+    if (!C0 || !state) return fail(ctx, KM_EINVAL, "C0 and state must not be NULL");
+    if (passes < 0) return fail(ctx, KM_EINVAL, "passes must be >= 0");
+    kmeans_params p;
+    if (params) p = *params; else kmeans_default_params(&p);
+    if ((s = validate_params(ctx, p)) != KM_OK) return s;
+    KM_CUDA(cudaSetDevice(ctx->device));
+    Plan P;
+    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P, true, true)) != KM_OK)
+        return s;
+    if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
+    char* base = arena_base(ctx);
+    const Launch L = make_launch(base, ctx->nsm, P, X, K, C0, p, nullptr, nullptr);
+    if (!L.maps_ok) return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
+    KM_CUDA(launch_prologue(L, ctx->stream, 0));
+    for (int i = 0; i < passes; ++i) KM_CUDA(launch_body(L, ctx->stream, 0, 0));
+    KM_CUDA(cudaStreamSynchronize(ctx->stream));
+    SolveState hs;
+    KM_CUDA(cudaMemcpy(&hs, L.st, sizeof(hs), cudaMemcpyDeviceToHost));
+    const size_t n = (size_t)K * X->d;
+    if (state->C) KM_CUDA(cudaMemcpy(state->C, at<double>(base, P.C64), n * 8, cudaMemcpyDeviceToHost));
+    if (state->C_AU) KM_CUDA(cudaMemcpy(state->C_AU, at<double>(base, P.CAU), n * 8, cudaMemcpyDeviceToHost));
+    if (state->F) KM_CUDA(cudaMemcpy(state->F, at<double>(base, P.Fprev), n * 8, cudaMemcpyDeviceToHost));
+    const int m_max = L.m_max;
+    for (int q = 0; q < hs.ring_count && m_max > 0; ++q) {
+        const int slot = (hs.ring_head - q + m_max) % m_max;
+        if (state->dF)
+            KM_CUDA(cudaMemcpy(state->dF + q * n, at<double>(base, P.dF) + slot * n, n * 8, cudaMemcpyDeviceToHost));
+        if (state->dG)
+            KM_CUDA(cudaMemcpy(state->dG + q * n, at<double>(base, P.dG) + slot * n, n * 8, cudaMemcpyDeviceToHost));
+    }
+    // P^t: the buffer the last pass wrote (a pass that did not end the solve flips cur afterwards)
+    const int which = hs.done ? hs.cur : (hs.cur ^ 1);
+    if (state->rho)
+        KM_CUDA(cudaMemcpy(state->rho, which ? L.rhoB : L.rhoA, (size_t)X->N * 4, cudaMemcpyDeviceToHost));
+    state->t = hs.t;
+    state->m = hs.m;
+    state->m_t = hs.m_t;
+    state->rank = hs.rank;
+    state->from_lloyd = hs.from_lloyd;
+    state->ring_count = m_max > 0 ? hs.ring_count : 0;
+    state->done = hs.done;
+    state->converged = hs.converged;
+    state->accepted = hs.accepted;
+    state->rejected = hs.rejected;
+    state->passes = hs.passes;
+    state->ls_qr_solves = hs.ls_qr;
+    state->E_prev = hs.E_prev;
+    state->E_prev2 = hs.E_prev2;
+    state->E_trial = hs.E_trial;
+    for (int j = 0; j < 32; ++j) state->theta[j] = j < hs.rank ? hs.theta[j] : 0.0;
+    return KM_OK;
 }
 
 }  // extern "C"

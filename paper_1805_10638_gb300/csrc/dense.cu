@@ -1,22 +1,25 @@
 // Dense assignment (d = 17..128, d % 8 == 0) on sm_103a tensor cores, and the dense update.
 //
-// Assignment (Eq. 3): scores s_ij = ||c_j||^2 - 2 x_i.c_j with x.c from tcgen05.mma kind::f16
-// (BF16 operands, FP32 accumulation in TMEM).  One persistent CTA per SM walks 128-row tiles of X;
-// per tile it streams the centroids in tiles of 256 through a 2-stage shared-memory ring fed by
-// TMA (128-byte swizzle, K-major), and the epilogue warps read the 128 x 256 FP32 accumulator
-// from TMEM (double buffered, so the MMA of the next centroid tile overlaps the epilogue of this
-// one) and keep a per-row top-2 (value, lowest index).  Warp roles: warp 0 issues TMA, warp 1
-// allocates TMEM and issues the MMAs (one thread), warps 2..17 are the epilogue (four warps per
-// TMEM lane quadrant, each taking a quarter of the columns).  Every wait on an mbarrier is bounded: on
-// timeout the kernel records an error and all roles leave their loops.
+// Assignment (Eq. 3): scores s_ij = ||c_j||^2 - 2 x_i.c_j with x.c from tcgen05.mma kind::f16 (BF16
+// operands, FP32 accumulation in TMEM).  Each operand is split into two BF16 parts, x = x_hi + x_lo
+// + r_x with x_hi = bf16(x), x_lo = bf16(x - x_hi), |r_x| <= u_b^2 |x| (u_b = 2^-8), likewise c, and
+// the product is accumulated as x_hi.c_hi + x_lo.c_hi + x_hi.c_lo: three MMAs per K step, whose
+// error is about 3 u_b^2 |x||c| instead of the 4 u_b |x||c| of a single BF16 product.  One
+// persistent CTA per SM walks 128-row tiles of X.  The X tile (hi and lo, one buffer per 64-wide
+// K-block) stays for the whole row tile; the centroid tiles of 256 stream through a ring of four
+// 32 KB slots (one K-block of the hi or of the lo part each), fed by TMA (128-byte swizzle,
+// K-major).  The epilogue warps read the 128 x 256 FP32 accumulator from TMEM (double buffered, so
+// the MMAs of the next centroid tile overlap the epilogue of this one; four 16-column loads per
+// wait) and keep a per-row top-2 (best value with its lowest index, second-best value).  Warp
+// roles: warp 0 issues TMA, warp 1 allocates TMEM and issues the MMAs (one thread), warps 2..17
+// are the epilogue (four warps per TMEM lane quadrant, each taking a quarter of the columns).
+// Every wait on an mbarrier is bounded: on timeout the kernel records an error and all roles leave
+// their loops.
 //
-// Near ties: the BF16 scores carry a rigorous rounding-error bound (derived where the kernel
-// arguments are built)
-//   B ~= (4 u_b + 4 d u) |x| max|c| + 4 u max|c|^2     (u_b = 2^-9, u = 2^-24);
-// the epilogue keeps per row the three best (value, lowest index) and the fourth-best value.  If the
-// top-2 gap is within 2B, the candidates are the best two or three whose successor is clear of 2B;
-// they are compared in FP32 (direct form).  Only a row with four or more scores within 2B of the
-// best is rescored over all K in FP32.
+// Near ties: the scores carry a rigorous error bound B (derived where the kernel arguments are
+// built; B ~= 1.9e-4 |x| max|c| + 2u max|c|^2 at d = 128).  A row whose top-2 gap is within 2B is
+// rescored over all K in FP32 (direct form, lowest index on ties); every other row takes the best
+// index, which the bound proves is the argmin of the exact scores of the FP32 inputs.
 //
 // Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
@@ -37,10 +40,11 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int TM = 128;            // rows per tile (MMA M)
 constexpr int TN = 256;            // centroids per tile (MMA N)
 constexpr int KBLK = 64;           // bf16 per 128-byte swizzle row
-constexpr int CST = 2;             // centroid-tile stages
+constexpr int CSLOT = 4;           // centroid ring slots (one K-block of the hi or lo part, 32 KB each)
 constexpr int DTHREADS = 576;      // 18 warps: TMA, MMA, 16 epilogue
 constexpr int SEG = 64;            // rows per segment-sum chunk
-constexpr int MREC = 7;            // floats per row and column quarter in the merge buffer
+constexpr int MREC = 3;            // floats per row and column quarter in the merge buffer (v1, v2, i1)
+constexpr int MAXKB = 2;           // K-blocks of 64 (d <= 128)
 constexpr unsigned SPIN_LIMIT = 1u << 28;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -106,17 +110,22 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// Four 16-column loads of 32 lanes x 32 bits (columns col, col+16, col+32, col+48) and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
 {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+    uint32_t r[64];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]), "=r"(r[16 * q + 4]),
+              "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]), "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]),
+              "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]), "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]),
+              "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
+            : "r"(taddr + 16u * q));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -152,14 +161,15 @@ __device__ __forceinline__ int32_t* pass_rho(const DenseArgs& a, const SolveStat
 
 // ------------------------------------------------------------------ assignment (tcgen05)
 struct SmemPlan {
-    uint32_t x, c, cn, merge, bar, slot, abort, total;
+    uint32_t xh, xl, c, cn, merge, bar, slot, abort, total;
 };
 __host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
 {
     SmemPlan p;
     uint32_t o = 0;
-    p.x = o;     o += 2u * nkb * TM * 128;
-    p.c = o;     o += (uint32_t)CST * nkb * TN * 128;
+    p.xh = o;    o += (uint32_t)nkb * TM * 128;       // X hi, one 16 KB chunk per K-block
+    p.xl = o;    o += (uint32_t)nkb * TM * 128;       // X lo
+    p.c = o;     o += (uint32_t)CSLOT * TN * 128;     // centroid ring
     p.cn = o;    o += (uint32_t)Kpad * 4;
     p.merge = o; o += 3 * TM * MREC * 4;
     p.bar = (o + 7) & ~7u; o = p.bar + 16 * 8;
@@ -170,8 +180,7 @@ __host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
 }
 
 __global__ void __launch_bounds__(DTHREADS, 1)
-    k_dense_assign(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC0,
-                   const __grid_constant__ CUtensorMap tmC1, DenseArgs a)
+    k_dense_assign(const __grid_constant__ DenseMaps tm, DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
@@ -180,29 +189,32 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     const int nkb = a.dpad / KBLK;
     const SmemPlan P = dense_smem(nkb, a.Kpad);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t sX = sbase + P.x, sC = sbase + P.c;
+    const uint32_t sXh = sbase + P.xh, sXl = sbase + P.xl, sC = sbase + P.c;
     float* s_cn = reinterpret_cast<float*>(smem + P.cn);
     float* s_merge = reinterpret_cast<float*>(smem + P.merge);
     const uint32_t bar = sbase + P.bar;
-    // barriers: xfull[2] xempty[2] cfull[2] cempty[2] afull[2] aempty[2]
-    const uint32_t xfull = bar, xempty = bar + 16, cfull = bar + 32, cempty = bar + 48, afull = bar + 64,
-                   aempty = bar + 80;
+    // barriers: xfull[2] xempty[2] cfull[4] cempty[4] afull[2] aempty[2]
+    const uint32_t xfull = bar, xempty = bar + 16, cfull = bar + 32, cempty = bar + 64, afull = bar + 96,
+                   aempty = bar + 112;
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem + P.slot);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + P.abort);
-    const CUtensorMap* tmC = set ? &tmC1 : &tmC0;
+    const CUtensorMap* tmCh = &tm.ch[set];
+    const CUtensorMap* tmCl = &tm.cl[set];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nct = a.Kpad / TN, nks = a.dpad / 16;
+    const int nct = a.Kpad / TN;
     const int ntiles = (int)((a.N + TM - 1) / TM);
-    const uint32_t xbytes = (uint32_t)nkb * TM * 128, cbytes = (uint32_t)nkb * TN * 128;
+    constexpr uint32_t XCHUNK = TM * 128, CCHUNK = TN * 128;
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(xfull + 8 * i, 1);
             mbar_init(xempty + 8 * i, 1);
-            mbar_init(cfull + 8 * i, 1);
-            mbar_init(cempty + 8 * i, 1);
             mbar_init(afull + 8 * i, 1);
             mbar_init(aempty + 8 * i, 16);
+        }
+        for (int i = 0; i < CSLOT; ++i) {
+            mbar_init(cfull + 8 * i, 1);
+            mbar_init(cempty + 8 * i, 1);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,35 +232,39 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     const uint32_t tmem = *slot;
 
     if (warp == 0) {
-        if (lane == 0) {   // TMA producer
+        if (lane == 0) {   // TMA producer: per row tile the X chunks, then the centroid chunks in MMA order
             uint32_t xit = 0, cit = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++xit) {
-                const uint32_t xs = xit & 1;
-                if (xit >= 2 && !mbar_wait(xempty + 8 * xs, ((xit >> 1) - 1) & 1, abort)) break;
-                mbar_expect_tx(xfull + 8 * xs, xbytes);
-                for (int kb = 0; kb < nkb; ++kb)
-                    tma_load_2d(sX + xs * xbytes + kb * (TM * 128), &tmX, kb * KBLK, tile * TM, xfull + 8 * xs);
-                for (int ct = 0; ct < nct; ++ct, ++cit) {
-                    const uint32_t cs = cit % CST;
-                    if (cit >= CST && !mbar_wait(cempty + 8 * cs, ((cit / CST) - 1) & 1, abort)) break;
-                    mbar_expect_tx(cfull + 8 * cs, cbytes);
-                    for (int kb = 0; kb < nkb; ++kb)
-                        tma_load_2d(sC + cs * cbytes + kb * (TN * 128), tmC, kb * KBLK, ct * TN, cfull + 8 * cs);
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok && !*abort; tile += gridDim.x, ++xit) {
+                for (int t = 0; t < nct && ok; ++t) {
+                    for (int kb = 0; kb < nkb && ok; ++kb) {
+                        if (t == 0) {
+                            if (xit >= 1 && !mbar_wait(xempty + 8 * kb, (xit - 1) & 1, abort)) { ok = false; break; }
+                            mbar_expect_tx(xfull + 8 * kb, 2 * XCHUNK);
+                            tma_load_2d(sXh + kb * XCHUNK, &tm.xh, kb * KBLK, tile * TM, xfull + 8 * kb);
+                            tma_load_2d(sXl + kb * XCHUNK, &tm.xl, kb * KBLK, tile * TM, xfull + 8 * kb);
+                        }
+                        for (int part = 0; part < 2; ++part, ++cit) {   // 0 = hi, 1 = lo
+                            const uint32_t cs = cit % CSLOT;
+                            if (cit >= CSLOT && !mbar_wait(cempty + 8 * cs, ((cit / CSLOT) - 1) & 1, abort)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(cfull + 8 * cs, CCHUNK);
+                            tma_load_2d(sC + cs * CCHUNK, part ? tmCl : tmCh, kb * KBLK, t * TN, cfull + 8 * cs);
+                        }
+                    }
                 }
             }
             if (*abort) {
                 // let the copies this thread issued land before the block exits (bounded)
-                for (uint32_t s2 = 0; s2 < 2; ++s2) {
-                    if (xit > s2) {
-                        const uint32_t n = (xit - 1 - s2);
-                        const uint32_t st2 = n & 1;
-                        for (unsigned i = 0; i < (1u << 20) && !mbar_try(xfull + 8 * st2, (n >> 1) & 1); ++i) {}
-                    }
-                    if (cit > s2) {
-                        const uint32_t n = (cit - 1 - s2);
-                        const uint32_t st2 = n % CST;
-                        for (unsigned i = 0; i < (1u << 20) && !mbar_try(cfull + 8 * st2, (n / CST) & 1); ++i) {}
-                    }
+                for (int kb = 0; kb < nkb && xit > 0; ++kb) {
+                    const uint32_t n = xit - 1;
+                    for (unsigned i = 0; i < (1u << 20) && !mbar_try(xfull + 8 * kb, n & 1); ++i) {}
+                }
+                for (uint32_t k = 0; k < (uint32_t)CSLOT && k < cit; ++k) {
+                    const uint32_t n = cit - 1 - k;
+                    for (unsigned i = 0; i < (1u << 20) && !mbar_try(cfull + 8 * (n % CSLOT), (n / CSLOT) & 1); ++i) {}
                 }
             }
         }
@@ -258,26 +274,42 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                                    ((uint32_t)(TM >> 4) << 24);
             uint32_t xit = 0, cit = 0, ait = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++xit) {
-                const uint32_t xs = xit & 1;
-                if (!mbar_wait(xfull + 8 * xs, (xit >> 1) & 1, abort)) break;
-                bool ok = true;
-                for (int ct = 0; ct < nct; ++ct, ++cit, ++ait) {
-                    const uint32_t cs = cit % CST, ab = ait & 1;
-                    if (!mbar_wait(cfull + 8 * cs, (cit / CST) & 1, abort)) { ok = false; break; }
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok && !*abort; tile += gridDim.x, ++xit) {
+                for (int t = 0; t < nct && ok; ++t, ++ait) {
+                    const uint32_t ab = ait & 1;
+                    const uint32_t acc = tmem + ab * TN;
                     if (ait >= 2 && !mbar_wait(aempty + 8 * ab, ((ait >> 1) - 1) & 1, abort)) { ok = false; break; }
                     tc_fence_after();
-                    for (int ks = 0; ks < nks; ++ks) {
-                        const uint32_t kb = ks >> 2, off = (ks & 3) * 32;
-                        const uint64_t ad = sdesc(sX + xs * xbytes + kb * (TM * 128) + off);
-                        const uint64_t bd = sdesc(sC + cs * cbytes + kb * (TN * 128) + off);
-                        mma_bf16(tmem + ab * TN, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (t == 0 && !mbar_wait(xfull + 8 * kb, xit & 1, abort)) { ok = false; break; }
+                        // hi part of the centroids: x_hi.c_hi and x_lo.c_hi
+                        uint32_t cs = cit % CSLOT;
+                        if (!mbar_wait(cfull + 8 * cs, (cit / CSLOT) & 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t bd = sdesc(sC + cs * CCHUNK + ks * 32);
+                            mma_bf16(acc, sdesc(sXh + kb * XCHUNK + ks * 32), bd, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                            mma_bf16(acc, sdesc(sXl + kb * XCHUNK + ks * 32), bd, idesc, 1u);
+                        }
+                        mma_commit(cempty + 8 * cs);
+                        ++cit;
+                        // lo part: x_hi.c_lo
+                        cs = cit % CSLOT;
+                        if (!mbar_wait(cfull + 8 * cs, (cit / CSLOT) & 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks)
+                            mma_bf16(acc, sdesc(sXh + kb * XCHUNK + ks * 32), sdesc(sC + cs * CCHUNK + ks * 32), idesc,
+                                     1u);
+                        mma_commit(cempty + 8 * cs);
+                        ++cit;
+                        if (t == nct - 1) mma_commit(xempty + 8 * kb);   // the row tile is done with this X chunk
                     }
-                    mma_commit(cempty + 8 * cs);
+                    if (!ok) break;
                     mma_commit(afull + 8 * ab);
                 }
-                if (!ok) break;
-                mma_commit(xempty + 8 * xs);
             }
         }
     } else if (warp >= 2) {   // epilogue: 16 warps = 4 TMEM lane quadrants x 4 column quarters
@@ -290,9 +322,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
         volatile int* s_go = reinterpret_cast<volatile int*>(smem + P.abort + 4);
         uint32_t ait = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            // per row and quarter: the three best (value, lowest index) and the fourth-best value
-            float v1 = __int_as_float(0x7f800000), v2 = v1, v3 = v1, v4 = v1;
-            int i1 = 0, i2 = 0, i3 = 0;
+            // per row and quarter: the best (value, lowest index) and the second-best value
+            float v1 = __int_as_float(0x7f800000), v2 = v1;
+            int i1 = 0;
             bool ok = true;
             for (int ct = 0; ct < nct; ++ct, ++ait) {
                 const uint32_t ab = ait & 1;
@@ -301,24 +333,23 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 if (ok && !mbar_wait(afull + 8 * ab, (ait >> 1) & 1, abort)) ok = false;
                 if (ok) {
                     tc_fence_after();
-#pragma unroll 1
-                    for (int c16 = 0; c16 < TN / 4 / 16; ++c16) {
-                        const int col = h * (TN / 4) + c16 * 16;
-                        float v[16];
-                        tmem_ld16(tmem + lane_base + ab * TN + col, v);
-                        const int j0 = ct * TN + col;
+                    const int col = h * (TN / 4);
+                    float v[64];
+                    tmem_ld64(tmem + lane_base + ab * TN + col, v);
+                    const int j0 = ct * TN + col;
+                    const float4* cn4 = reinterpret_cast<const float4*>(s_cn + j0);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float s = fmaf(-2.f, v[e], s_cn[j0 + e]);
-                            const int j = j0 + e;
-                            const bool p1 = s < v1, p2 = s < v2, p3 = s < v3;
-                            v4 = fminf(v4, fmaxf(v3, s));
-                            i3 = p2 ? i2 : (p3 ? j : i3);
-                            v3 = fminf(v3, fmaxf(v2, s));
-                            i2 = p1 ? i1 : (p2 ? j : i2);
-                            v2 = fminf(v2, fmaxf(v1, s));
-                            i1 = p1 ? j : i1;
-                            v1 = fminf(v1, s);
+                    for (int e4 = 0; e4 < 16; ++e4) {
+                        const float4 c4 = cn4[e4];
+                        const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = 4 * e4 + u;
+                            const float sc = fmaf(-2.f, v[e], cc[u]);
+                            const bool p1 = sc < v1;
+                            v2 = fminf(v2, fmaxf(v1, sc));
+                            i1 = p1 ? j0 + e : i1;
+                            v1 = fminf(v1, sc);
                         }
                     }
                 }
@@ -332,48 +363,25 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 float* m = s_merge + ((h - 1) * TM + r) * MREC;
                 m[0] = v1;
                 m[1] = v2;
-                m[2] = v3;
-                m[3] = v4;
-                m[4] = __int_as_float(i1);
-                m[5] = __int_as_float(i2);
-                m[6] = __int_as_float(i3);
+                m[2] = __int_as_float(i1);
             }
             named_bar(1, 512);
             if (h == 0 && ok) {
                 for (int hh = 0; hh < 3; ++hh) {
                     const float* m = s_merge + (hh * TM + r) * MREC;
-                    for (int u = 0; u < 3; ++u) {
-                        const float w = m[u];
-                        const int wj = __float_as_int(m[4 + u]);
-                        if (w < v1 || (w == v1 && wj < i1)) {
-                            v4 = fminf(v4, v3);
-                            v3 = v2;
-                            i3 = i2;
-                            v2 = v1;
-                            i2 = i1;
-                            v1 = w;
-                            i1 = wj;
-                        } else if (w < v2 || (w == v2 && wj < i2)) {
-                            v4 = fminf(v4, v3);
-                            v3 = v2;
-                            i3 = i2;
-                            v2 = w;
-                            i2 = wj;
-                        } else if (w < v3 || (w == v3 && wj < i3)) {
-                            v4 = fminf(v4, v3);
-                            v3 = w;
-                            i3 = wj;
-                        } else {
-                            v4 = fminf(v4, w);
-                        }
+                    const float w1 = m[0], w2 = m[1];
+                    const int wj = __float_as_int(m[2]);
+                    if (w1 < v1 || (w1 == v1 && wj < i1)) {
+                        v2 = fminf(v1, w2);
+                        v1 = w1;
+                        i1 = wj;
+                    } else {
+                        v2 = fminf(v2, w1);
                     }
-                    v4 = fminf(v4, m[3]);
                 }
-                const float nb1 = v1, nb2 = v2;
-                const int ni1 = i1;
                 const int64_t row = (int64_t)tile * TM + r;
                 if (row < a.N) {
-                    // ||x^|| of the BF16 row (the operand the MMA saw); ||x|| <= ||x^|| / (1 - u_b)
+                    // ||x_hi|| of the BF16 row; ||x|| <= ||x_hi|| / (1 - u_b) is folded into bcoef_a
                     const uint4* xr = reinterpret_cast<const uint4*>(a.Xb + row * a.d);
                     float xs = 0.f;
                     for (int u = 0; u < a.d / 8; ++u) {
@@ -385,21 +393,11 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                             xs = fmaf(lo, lo, fmaf(hi, hi, xs));
                         }
                     }
-                    const float xn = sqrtf(xs);
-                    const float bnd = a.bcoef_a * xn * cmax + a.bcoef_b * cmax2;
-                    rho[row] = ni1;
-                    if (!(nb2 - nb1 > 2.f * bnd)) {
-                        if (v3 - nb1 > 2.f * bnd || v4 - nb1 > 2.f * bnd) {
-                            // only the two (or three) best can be the argmin: compare them exactly later
-                            const unsigned pos = atomicAdd(a.qcount + 1, 1u);
-                            a.cand[4 * pos] = (int)row;
-                            a.cand[4 * pos + 1] = ni1;
-                            a.cand[4 * pos + 2] = i2;
-                            a.cand[4 * pos + 3] = v3 - nb1 > 2.f * bnd ? -1 : i3;
-                        } else {
-                            const unsigned pos = atomicAdd(a.qcount, 1u);
-                            a.queue[pos] = (int)row;
-                        }
+                    const float bnd = a.bcoef_a * sqrtf(xs) * cmax + a.bcoef_b * cmax2;
+                    rho[row] = i1;
+                    if (!(v2 - v1 > 2.02f * bnd)) {          // near tie: rescore the row over all K in FP32
+                        const unsigned pos = atomicAdd(a.qcount, 1u);
+                        a.queue[pos] = (int)row;
                     }
                 }
             }
@@ -419,56 +417,8 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ near-tie rescoring
-// FP32 direct form sum_k (x_k - c_jk)^2 for the queued rows.  Candidate sets (row, i1, i2, i3 or
-// -1): one warp compares the two or three candidates (lanes split d, fixed butterfly; lowest index
-// wins a tie).  Full rows: see k_rescore_full.
-__global__ void __launch_bounds__(256) k_rescore(DenseArgs a)
-{
-    const int set = pass_set(a.st, a.mode);
-    if (set < 0) return;
-    __shared__ float sx[8][128];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned nfull = a.qcount[0], npair = a.qcount[1];
-    const float* X = a.X;
-    const float* C = a.c32[set];
-    const int d = a.d, K = a.K;
-    int32_t* rho = pass_rho(a, a.st);
-    for (unsigned q = blockIdx.x * 8 + w; q < npair; q += gridDim.x * 8) {
-        const int64_t row = a.cand[4 * q];
-        const int j1 = a.cand[4 * q + 1], j2 = a.cand[4 * q + 2], j3 = a.cand[4 * q + 3];
-        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        for (int k = lane; k < d; k += 32) {
-            const float x = X[row * d + k];
-            const float t1 = x - C[(size_t)j1 * d + k], t2 = x - C[(size_t)j2 * d + k];
-            s1 = fmaf(t1, t1, s1);
-            s2 = fmaf(t2, t2, s2);
-            if (j3 >= 0) {
-                const float t3 = x - C[(size_t)j3 * d + k];
-                s3 = fmaf(t3, t3, s3);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(FULL, s1, o);
-            s2 += __shfl_xor_sync(FULL, s2, o);
-            s3 += __shfl_xor_sync(FULL, s3, o);
-        }
-        if (lane == 0) {
-            float bs = s1;
-            int bj = j1;
-            if (s2 < bs || (s2 == bs && j2 < bj)) {
-                bs = s2;
-                bj = j2;
-            }
-            if (j3 >= 0 && (s3 < bs || (s3 == bs && j3 < bj))) bj = j3;
-            rho[row] = bj;
-        }
-    }
-    (void)sx;
-    (void)nfull;
-}
-
-// Full rescans: 16 queued rows per block (two per warp) share each tile of 64 centroids staged in
+// FP32 direct form sum_k (x_k - c_jk)^2 over all K for the queued near-tie rows.  16 queued rows per
+// block (two per warp) share each tile of 64 centroids staged in
 // shared memory (row stride d+1 floats: lanes reading different centroids hit different banks).
 // Lane l scores centroids c0+l and c0+l+32 of every tile, so each lane visits its centroids in
 // ascending order; a lexicographic (distance, index) butterfly finishes each row.
@@ -543,8 +493,9 @@ __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
 }
 
 // ------------------------------------------------------------------ packing
-// Per centroid (one warp): BF16 copy (zero-padded to dpad, pad rows zero), ||c||^2 in FP32
-// (+inf for pad rows) and the FP32 copy used by the rescoring and the residuals.
+// Per centroid (one warp): the FP32 copy c (used by the rescoring and the residuals), its BF16 split
+// c_hi = bf16(c), c_lo = bf16(c - c_hi) (zero-padded to dpad, pad rows zero) and ||c||^2 of the FP32
+// values, summed in FP64 and rounded once (+inf for pad rows).
 __global__ void __launch_bounds__(256) k_pack_dense(PackArgs a)
 {
     if (a.st && a.check_done && a.st->done) return;
@@ -556,17 +507,26 @@ __global__ void __launch_bounds__(256) k_pack_dense(PackArgs a)
         const float* src32 = a.src32;
         double nrm = 0.0;
         for (int k = lane; k < a.dpad; k += 32) {
-            double v = 0.0;
+            float v = 0.f;
             if (j < a.K && k < a.d) {
-                v = src64 ? src64[(size_t)j * a.d + k] : (double)src32[(size_t)j * a.d + k];
-                a.c32[s][(size_t)j * a.d + k] = (float)v;
+                v = src64 ? (float)src64[(size_t)j * a.d + k] : src32[(size_t)j * a.d + k];
+                a.c32[s][(size_t)j * a.d + k] = v;
             }
-            a.cb[s][(size_t)j * a.dpad + k] = __float2bfloat16_rn((float)v);
-            nrm += v * v;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            a.cb[s][(size_t)j * a.dpad + k] = hi;
+            a.cl[s][(size_t)j * a.dpad + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+            nrm += (double)v * (double)v;
         }
         nrm = warp_sum(nrm);
         if (lane == 0) a.cn[s][j] = j < a.K ? (float)nrm : __int_as_float(0x7f800000);
     }
+}
+
+// The low BF16 part of X: x_lo = bf16(x - x_hi), x_hi the caller's BF16 copy, same [N][d] layout.
+__global__ void __launch_bounds__(256) k_xsplit(const float* X, const __nv_bfloat16* Xh, __nv_bfloat16* Xl, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        Xl[i] = __float2bfloat16_rn(X[i] - __bfloat162float(Xh[i]));
 }
 
 // Row norms ||x|| (FP32, for the error bound) and the non-finite check, once per solve.
@@ -821,7 +781,7 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
         if (a.out_nch) *a.out_nch = ch;
         return;
     }
-    if (a.mode != MODE_EPI) st->rescored += a.qcount[0] + a.qcount[1];
+    if (a.mode != MODE_EPI) st->rescored += a.qcount[0];
     if (a.mode == MODE_EPI) {
         st->E_final = E;
     } else if (a.mode == MODE_INIT) {
@@ -933,8 +893,7 @@ bool make_tmap_bf16(void* map, const void* base, int64_t rows, int cols, int box
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* tmC0, const void* tmC1, int nsm,
-                              cudaStream_t s)
+cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm, cudaStream_t s)
 {
     // assignment
     cudaError_t e = cudaMemsetAsync(a.qcount, 0, 2 * sizeof(unsigned int), s);
@@ -944,14 +903,17 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* t
     if (e != cudaSuccess) return e;
     const int ntiles = (int)((a.N + TM - 1) / TM);
     const int grid = ntiles < nsm ? ntiles : nsm;
-    k_dense_assign<<<grid, DTHREADS, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(tmX),
-                                                *reinterpret_cast<const CUtensorMap*>(tmC0),
-                                                *reinterpret_cast<const CUtensorMap*>(tmC1), a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_rescore<<<nsm * 4, 256, 0, s>>>(a);
+    k_dense_assign<<<grid, DTHREADS, smem, s>>>(maps, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t sm_full = (size_t)(16 * a.d + 64 * (a.d + 1)) * sizeof(float);
     k_rescore_full<<<nsm * 4, 256, sm_full, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xsplit(const float* X, const void* Xh, void* Xl, int64_t n, int nsm, cudaStream_t s)
+{
+    k_xsplit<<<nsm * 8, 256, 0, s>>>(X, reinterpret_cast<const __nv_bfloat16*>(Xh), reinterpret_cast<__nv_bfloat16*>(Xl),
+                                     n);
     return cudaGetLastError();
 }
 

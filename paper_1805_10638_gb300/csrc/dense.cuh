@@ -1,11 +1,21 @@
 // Declarations of the dense (tensor-core) assignment and the sort-based update.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "km_internal.cuh"
 
 namespace km {
+
+// TMA descriptors of one dense pass: X's BF16 hi and lo parts ([N][d]) and the centroids' hi and lo
+// parts ([Kpad][dpad]) for both centroid sets (0 = C^t, 1 = C_AU).
+struct DenseMaps {
+    CUtensorMap xh;
+    CUtensorMap xl;
+    CUtensorMap ch[2];
+    CUtensorMap cl[2];
+};
 
 // Arguments shared by every kernel of one dense pass (assignment + rescoring + update chain).
 struct DenseArgs {
@@ -16,7 +26,7 @@ struct DenseArgs {
     int Kpad;                 // K rounded up to 256 (MMA N)
     int mode;                 // PassMode
     const float* X;           // [N][d] FP32
-    const __nv_bfloat16* Xb;  // [N][d] BF16 copy (the MMA operand)
+    const __nv_bfloat16* Xb;  // [N][d] BF16 copy x_hi (an MMA operand; its row norms feed the bound)
     const float* xnorm;       // [N] ||x||
     const float* cn[2];       // [Kpad] ||c||^2, +inf for pad rows; set 0 = C^t, set 1 = C_AU
     const float* c32[2];      // [K][d] FP32 centroids
@@ -26,9 +36,8 @@ struct DenseArgs {
     int32_t* rho_out;         // standalone output
     const int32_t* rho_prev;  // standalone previous assignment (optional)
     int32_t* rho_pair[2];     // solver ping-pong assignment
-    int* queue;               // [N] rows to rescore over all K
-    int* cand;                // [N][4] (row, i1, i2, i3 or -1): rows whose argmin is one of two or three candidates
-    unsigned int* qcount;     // [2]: full rows, candidate pairs
+    int* queue;               // [N] near-tie rows to rescore over all K
+    unsigned int* qcount;     // [2]: queued rows
     int* err;
     // update chain
     int rows_per_block;
@@ -63,7 +72,8 @@ struct PackArgs {
     int K, Kpad, d, dpad, nsets, check_done;
     const double* src64[2];   // FP64 sources (solver) or NULL
     const float* src32;       // FP32 source (standalone)
-    __nv_bfloat16* cb[2];     // [Kpad][dpad]
+    __nv_bfloat16* cb[2];     // [Kpad][dpad] hi part
+    __nv_bfloat16* cl[2];     // [Kpad][dpad] lo part
     float* cn[2];             // [Kpad]
     float* c32[2];            // [K][d]
     SolveState* st;
@@ -71,8 +81,8 @@ struct PackArgs {
 
 size_t dense_assign_smem(int dpad, int Kpad);
 bool make_tmap_bf16(void* map, const void* base, int64_t rows, int cols, int box_rows);
-cudaError_t launch_dense_pass(const DenseArgs& a, const void* tmX, const void* tmC0, const void* tmC1, int nsm,
-                              cudaStream_t s);
+cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm, cudaStream_t s);
+cudaError_t launch_xsplit(const float* X, const void* Xh, void* Xl, int64_t n, int nsm, cudaStream_t s);
 cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cudaStream_t s);
 cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s);
 cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,

@@ -30,6 +30,14 @@ constexpr int DOTS = 2 * MMAX;      // per-block dot partials: Gram row + right-
 // order-independent add that beats per-warp bins there; with more dimensions the d conversions and
 // 64-bit shared-memory adds per sample cost more than the per-warp bins.
 constexpr int FX_MAX_D = 4;
+// Least squares of Eq. 7 (FinArgs::ls_mode): LS_AUTO solves through the Cholesky factor of the
+// incrementally kept Gram matrix when every pivot ratio L_kk / L_00 exceeds LS_CERT_TOL, and by
+// Householder QR of dF otherwise; LS_QR always takes the QR; LS_GRAM always the Gram route.  At a
+// pivot ratio r the Gram route's R_kk carries a relative error of about u / r^2 (u = 2^-53), so
+// above 1e-3 the factor agrees with the QR's R to about 1e-10 and every rank decision at
+// rank_tol <= 1e-3 is the QR's.
+enum LsMode : int { LS_AUTO = 0, LS_QR = 1, LS_GRAM = 2 };
+constexpr double LS_CERT_TOL = 1e-3;
 constexpr int LOWD_SMEM_MAX = 227 * 1024;   // opt-in dynamic shared memory per block on sm_103a
 constexpr int SM_SMEM = 228 * 1024;         // shared memory per SM
 
@@ -75,6 +83,7 @@ struct SolveState {
     long long scanned;    // rows scanned over all K, summed over the assignment passes
     float xmax;           // max |x_ik| over the samples (FP32 path, set by the INIT pass)
     int fx_s;             // scale 2^fx_s of the last pass's fixed-point residual sums (FP32 path)
+    int ls_qr;            // least-squares solves that took the Householder QR path
     double E_prev;    // stored E^{t-1}
     double E_prev2;   // stored E^{t-2}
     double E_trial;   // E(P^t, C^t) of the proposed iterate
@@ -186,6 +195,8 @@ struct FinArgs {
     int max_iter;
     int lloyd_only;
     double rank_tol;
+    int ls_mode;          // LsMode
+    double* qrw;          // [(m_max + 1) * K*d] working matrix of the QR path
     int use_cond;
     cudaGraphConditionalHandle cond;
     // accelerated iterate in the last block (small K*d)
@@ -244,6 +255,21 @@ struct EpiArgs {
     int64_t N;
     void* info;
     int nblk;
+};
+
+// kmeans_lsq: Eq. 7 for a caller-supplied history (one block).
+struct LsqArgs {
+    const double* dF;     // [m][n], column q contiguous, q = 0 the newest difference
+    const double* f;      // [n]
+    size_t n;
+    int m;
+    int mode;             // LsMode
+    double rank_tol;
+    double* W;            // [(m + 1) * n] working matrix of the QR route
+    SolveState* st;       // gram / bvec workspace
+    double* theta;        // [m] out
+    int* rank;            // out, may be NULL
+    int* qr_used;         // out, may be NULL
 };
 
 // Batched launches: one persistent grid walks a list of work items (instance, block of that
@@ -317,6 +343,7 @@ cudaError_t launch_epi(bool f64, const SolveState* st, const double* C64, const 
                        size_t n, const int32_t* rhoA, const int32_t* rhoB, int32_t* rho_out, int64_t N,
                        void* info, cudaStream_t s);
 size_t devinfo_bytes();
+cudaError_t launch_lsq(const LsqArgs& a, cudaStream_t s);
 
 // Batched launchers (persistent grids over work items).
 cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s);

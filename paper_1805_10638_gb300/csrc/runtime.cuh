@@ -21,6 +21,7 @@ namespace {
 struct GraphKey {
     const void* X;
     const void* Xb;
+    const void* Xl;
     int64_t N;
     int d, K, prec;
     const void* C0;
@@ -30,15 +31,16 @@ struct GraphKey {
     void* arena;
     size_t arena_bytes;
     int ham;
+    int lsq;
 };
 
 struct Plan {
     // offsets into the arena
     size_t st, rhoA, rhoB, C64, CAU, Fprev, dF, dG, cpk0, cpk1, c32_0, c32_1, origin;
-    size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info, acc;
+    size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info, acc, qrw;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
-    size_t cb0, cb1, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
+    size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
         part, pe, pnch, S, rowe, rown;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
@@ -162,16 +164,20 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.Fprev = take(n * 8);
     P.dF = take((size_t)mm * n * 8);
     P.dG = take((size_t)mm * n * 8);
+    P.qrw = take((size_t)(mm + 1) * n * 8);
     P.cpk0 = P.cpk1 = 0;
     P.c32_0 = take(n * 4);
     P.c32_1 = take(n * 4);
     P.origin = take(256);
     P.cb0 = take((size_t)P.Kpad * P.dpad * 2);
     P.cb1 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cl0 = take((size_t)P.Kpad * P.dpad * 2);
+    P.cl1 = take((size_t)P.Kpad * P.dpad * 2);
+    P.xlo = take((size_t)N * d * 2);     // x_lo = bf16(x - x_hi), when the caller does not supply it
     P.cn0 = take((size_t)P.Kpad * 4);
     P.cn1 = take((size_t)P.Kpad * 4);
     P.xnorm = take((size_t)N * 4);
-    P.queue = take((size_t)N * 5 * 4);   // full-rescore rows, then (row, i1, i2, i3) candidate sets
+    P.queue = take((size_t)N * 4);       // near-tie rows
     P.qcount = take(256);
     P.err = take(256);
     P.hist = take((size_t)K * P.nbk * 4);
@@ -204,6 +210,17 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     }
     P.total = o;
     return KM_OK;
+}
+
+// KM_LSQ in the environment picks the least-squares route of Eq. 7: "qr" = Householder QR always,
+// "gram" = the Cholesky factor of the Gram matrix always; unset = the Gram route when it certifies
+// its factor, else QR (the results agree to about 1e-10 relative on well-conditioned histories).
+int ls_mode()
+{
+    const char* v = getenv("KM_LSQ");
+    if (v && !strcmp(v, "qr")) return LS_QR;
+    if (v && !strcmp(v, "gram")) return LS_GRAM;
+    return LS_AUTO;
 }
 
 // KM_HAMERLY=0 in the environment solves without Hamerly bounds (same results, every row scanned).
@@ -265,6 +282,7 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.Fprev = take(n * 8);
     P.dF = take((size_t)mm * n * 8);
     P.dG = take((size_t)mm * n * 8);
+    P.qrw = take((size_t)(mm + 1) * n * 8);
     P.cpk0 = take((size_t)P.Kpad * P.DP * 4);
     P.cpk1 = take((size_t)P.Kpad * P.DP * 4);
     P.c32_0 = take(n * 4);
@@ -415,9 +433,9 @@ struct Launch {
     PackArgs pk;
     const float* X32;
     int nsm;
-    alignas(64) unsigned char tmX[128];
-    alignas(64) unsigned char tmC0[128];
-    alignas(64) unsigned char tmC1[128];
+    DenseMaps maps;
+    const void* xlo = nullptr;   // the low BF16 part of X the passes read
+    bool xsplit = false;         // the prologue computes it into the workspace
     bool maps_ok = true;
 };
 
@@ -439,23 +457,25 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.c32[1] = at<float>(base, P.c32_1);
     a.c64[0] = at<double>(base, P.C64);
     a.c64[1] = at<double>(base, P.CAU);
-    // Rigorous bound on |s - s*| for the score s = fl(||c||^2 - 2 v), v = the MMA's x^.c^ (BF16
-    // operands x^ = bf16(x), c^ = bf16(c): relative error <= u_b = 2^-9 each; their products are
-    // exact in FP32), s* = ||c||^2 - 2 x.c (c, x the FP32 values the rescoring uses):
-    //   2 |x^.c^ - x.c|  <= 2 (2 u_b + u_b^2) |x||c|              (quantisation of the operands)
-    //   2 |v - x^.c^|    <= 2 (2 d u) |x^||c^|                    (FP32 accumulation, allowing 2u
-    //                                                              per addition: truncating adders)
-    //   fl of the fma    <= u (||c||^2 + 2 |x||c|),  ||c||^2 rounded from FP64: u ||c||^2
-    // with |x| <= |x^| (1 + 2 u_b), |c^| <= |c| (1 + u_b).  The epilogue takes |x^| from the BF16
-    // row and max|c| over the centroids.
-    const double ub = 1.0 / 512.0, u = 5.9604644775390625e-8;
-    a.bcoef_a = (float)((2.0 * (2.0 * ub + ub * ub) + 4.0 * d * u * (1.0 + ub) * (1.0 + ub) + 2.0 * u) *
-                        (1.0 + 2.0 * ub));
-    a.bcoef_b = (float)(4.0 * u);
+    // Rigorous bound on |s - s*| for the score s = fl(||c||^2 - 2 v), v the MMA's sum
+    // x_hi.c_hi + x_lo.c_hi + x_hi.c_lo, s* = ||c||^2 - 2 x.c with x, c the FP32 values the rescoring
+    // uses.  BF16 rounding to nearest has unit roundoff u_b = 2^-8: |x - x_hi| <= u_b |x|,
+    // |x - x_hi - x_lo| <= u_b^2 |x| componentwise, likewise c.  Then
+    //   |x.c - (x_hi.c_hi + x_lo.c_hi + x_hi.c_lo)| <= (3 u_b^2 + u_b^3) |x||c|       (dropped terms)
+    //   FP32 accumulation of the 3d exact BF16 products inside the MMA, allowing 2u per addition
+    //   (adders that truncate):                      <= 6 d u (1 + 4 u_b) |x||c|
+    //   the epilogue's fma and the rounding of ||c||^2 (FP64 sum rounded once):
+    //                                                 <= u (||c||^2 + 2 |x||c| (1 + alpha)) + u ||c||^2
+    // so B = (2 alpha + 2 u (1 + alpha)) |x||c| + (2u + u^2) ||c||^2, alpha the first two lines.  The
+    // epilogue takes |x| from the BF16 row (|x| <= |x_hi| / (1 - u_b), and the FP32 sum of squares
+    // of d terms is within (1 + d u)) and max|c| over the centroids.
+    const double ub = 1.0 / 256.0, u = 5.9604644775390625e-8;
+    const double alpha = 3.0 * ub * ub + ub * ub * ub + 6.0 * d * u * (1.0 + 4.0 * ub);
+    a.bcoef_a = (float)((2.0 * alpha + 2.0 * u * (1.0 + alpha)) / (1.0 - ub) * (1.0 + d * u) * 1.01);
+    a.bcoef_b = (float)((2.0 * u + u * u) * 1.01);
     a.rho_pair[0] = at<int32_t>(base, P.rhoA);
     a.rho_pair[1] = at<int32_t>(base, P.rhoB);
     a.queue = at<int>(base, P.queue);
-    a.cand = at<int>(base, P.queue) + N;
     a.qcount = at<unsigned int>(base, P.qcount);
     a.err = at<int>(base, P.err);
     a.rows_per_block = P.rpb;
@@ -488,6 +508,8 @@ PackArgs pack_args(char* base, const Plan& P, int d, int K)
     p.src64[1] = at<double>(base, P.CAU);
     p.cb[0] = at<__nv_bfloat16>(base, P.cb0);
     p.cb[1] = at<__nv_bfloat16>(base, P.cb1);
+    p.cl[0] = at<__nv_bfloat16>(base, P.cl0);
+    p.cl[1] = at<__nv_bfloat16>(base, P.cl1);
     p.cn[0] = at<float>(base, P.cn0);
     p.cn[1] = at<float>(base, P.cn1);
     p.c32[0] = at<float>(base, P.c32_0);
@@ -496,11 +518,20 @@ PackArgs pack_args(char* base, const Plan& P, int d, int K)
     return p;
 }
 
-bool dense_maps(char* base, const Plan& P, const void* Xb, int64_t N, int d, void* tmX, void* tmC0, void* tmC1)
+// The low BF16 part of X the dense pass reads: the caller's, or the workspace copy (then computed by
+// launch_xsplit before the first pass).
+const void* dense_xlo(char* base, const Plan& P, const kmeans_data* X)
 {
-    return make_tmap_bf16(tmX, Xb, N, d, 128) &&
-           make_tmap_bf16(tmC0, at<void>(base, P.cb0), P.Kpad, P.dpad, 256) &&
-           make_tmap_bf16(tmC1, at<void>(base, P.cb1), P.Kpad, P.dpad, 256);
+    return X->X_bf16_lo ? X->X_bf16_lo : static_cast<const void*>(at<void>(base, P.xlo));
+}
+
+bool dense_maps(char* base, const Plan& P, const void* Xb, const void* Xl, int64_t N, int d, DenseMaps* m)
+{
+    return make_tmap_bf16(&m->xh, Xb, N, d, 128) && make_tmap_bf16(&m->xl, Xl, N, d, 128) &&
+           make_tmap_bf16(&m->ch[0], at<void>(base, P.cb0), P.Kpad, P.dpad, 256) &&
+           make_tmap_bf16(&m->ch[1], at<void>(base, P.cb1), P.Kpad, P.dpad, 256) &&
+           make_tmap_bf16(&m->cl[0], at<void>(base, P.cl0), P.Kpad, P.dpad, 256) &&
+           make_tmap_bf16(&m->cl[1], at<void>(base, P.cl1), P.Kpad, P.dpad, 256);
 }
 
 Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int K, const void* C0,
@@ -567,6 +598,8 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     fa.max_iter = p.max_iter;
     fa.lloyd_only = p.lloyd_only;
     fa.rank_tol = p.rank_tol;
+    fa.ls_mode = ls_mode();
+    fa.qrw = at<double>(base, P.qrw);
     fa.fuse_mix = fuse_mix_rule(K, d) ? 1 : 0;
     fa.part_fx = pa.acc ? 1 : 0;
     fa.acc = pa.acc;
@@ -617,7 +650,9 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
         da.max_iter = p.max_iter;
         L.pk = pack_args(base, P, d, K);
         L.pk.check_done = 1;
-        L.maps_ok = dense_maps(base, P, X->X_bf16, X->N, d, L.tmX, L.tmC0, L.tmC1);
+        L.xlo = dense_xlo(base, P, X);
+        L.xsplit = X->X_bf16_lo == nullptr;
+        L.maps_ok = dense_maps(base, P, X->X_bf16, L.xlo, X->N, d, &L.maps);
     }
     return L;
 }
@@ -631,7 +666,7 @@ cudaError_t dense_pass(const Launch& L, int mode, int use_cond, cudaGraphConditi
     a.use_cond = use_cond;
     a.cond = h;
     cudaError_t e = cudaSuccess;
-    if (assign) e = launch_dense_pass(a, L.tmX, L.tmC0, L.tmC1, L.nsm, s);
+    if (assign) e = launch_dense_pass(a, L.maps, L.nsm, s);
     if (e == cudaSuccess) e = launch_dense_update(a, L.P.nbk, L.P.max_chunks, s);
     return e;
 }
@@ -645,6 +680,8 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
             e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
                             nullptr, L.st, L.p.m_init, L.m_max, s, 0);
         if (e == cudaSuccess) e = launch_xnorm(L.X32, L.N, L.d, const_cast<float*>(L.da.xnorm), L.st, L.nsm, s);
+        if (e == cudaSuccess && L.xsplit)
+            e = launch_xsplit(L.X32, L.da.Xb, const_cast<void*>(L.xlo), L.N * (int64_t)L.d, L.nsm, s);
         PackArgs pk = L.pk;
         pk.nsets = 1;
         pk.check_done = 0;
@@ -749,7 +786,7 @@ bool graph_mode()
 }
 
 struct DevInfoH {
-    int iters, accepted, rejected, passes, converged, m_final, status, pad;
+    int iters, accepted, rejected, passes, converged, m_final, status, ls_qr;
     double E;
     long long rescored;
     long long scanned;
@@ -828,7 +865,7 @@ void fill_info(kmeans_info* info, const DevInfoH* di, float ms)
     info->rescored_rows = di->rescored;
     info->device_ms = ms;
     info->status = di->status;
-    info->reserved = 0;
+    info->ls_qr_solves = di->ls_qr;
     info->scanned_rows = di->scanned;
 }
 

@@ -179,6 +179,7 @@ kmeans_status admit_small(kmeans_server* srv, Req& r, int slot)
     kmeans_data Xd = r.Xh;
     Xd.X = r.Xd;
     Xd.X_bf16 = nullptr;
+    Xd.X_bf16_lo = nullptr;
     Xd.prec = r.Xh.prec == KM_F64 ? KM_F64 : KM_F32;
     const Launch L = make_launch(base, srv->ctx->nsm, r.P, &Xd, r.K, r.C0d, r.p, r.Coutd, r.rhod);
     PassArgs pa = L.pa;
@@ -219,6 +220,7 @@ kmeans_status start_large(kmeans_server* srv, Req& r, int lane)
     kmeans_data Xd = r.Xh;
     Xd.X = r.Xd;
     Xd.X_bf16 = r.Xbd;
+    Xd.X_bf16_lo = nullptr;         // the prologue splits X on the device
     const Launch L = make_launch(base, srv->ctx->nsm, r.P, &Xd, r.K, r.C0d, r.p, r.Coutd, r.rhod);
     if (!L.maps_ok) return sfail(srv, KM_ECUDA, "cuTensorMapEncodeTiled failed");
     kmeans_status s = record_while_graph(

@@ -8,11 +8,19 @@
 // the last-block counter) in a file-scope __device__ array of fixed size, KM_STATIC_SCRATCH_BYTES.
 // Every GPU that loads the library holds that array until the process exits.
 //
-// The array's host-side name is only a stand-in; its device address is looked up once per device
-// with cudaGetSymbolAddress (on the first call on that device, with that device current) and
-// cached.  Every call shares the array and finds the previous call's contents there: the counter
-// is cleared on each call and the partials are fully rewritten.  Calls that overlap on the GPU
-// (different streams, or host threads without ordering) race on the array.
+// The array's host-side name is only a stand-in; its device address is looked up with
+// cudaGetSymbolAddress on the first call on a device (with that device current) and cached for
+// that device's current CUDA context: a call under a new context (after cudaDeviceReset, or a
+// primary context released and made again) looks it up again.  Every call shares the array and
+// finds the previous call's contents there: the counter is cleared on each call and the partials
+// are fully rewritten.  Calls that overlap on the GPU (different streams, or host threads without
+// ordering) race on the array.
+//
+// The pass uses the block count kmeans_update uses for the same shape (the kernel's occupancy, at
+// most 4 blocks per SM, at least 1024 rows per block in FP32 and 256 in FP64), so the two calls sum
+// the same partials in the same order and agree bit for bit, unless the array cannot hold that many
+// block partials; then fewer blocks are used and FP32 results may differ in the last bits (the
+// update stays deterministic for a given device).
 #include <mutex>
 
 #include "km_internal.cuh"
@@ -27,17 +35,41 @@ static __device__ __align__(256) unsigned char g_static_scratch[KM_STATIC_SCRATC
 
 std::mutex g_mu;
 void* g_addr[KM_STATIC_MAX_DEVICES] = {};
+void* g_ctx[KM_STATIC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on `device` (which must be current).
+// The driver's current context (cuCtxGetCurrent through the runtime's entry-point query, so the
+// library needs no link against libcuda); NULL if the query is unavailable.
+void* current_context()
+{
+    typedef int (*CtxGetCurrent)(void**);
+    static CtxGetCurrent fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrent>(p);
+    }
+    void* c = nullptr;
+    if (fn && fn(&c) != 0) c = nullptr;
+    return c;
+}
+
+// Device address of the scratch array on `device` (which must be current), looked up on the first
+// call under each context of that device.
 cudaError_t scratch_address(int device, void** out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     if (device < 0 || device >= KM_STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (!g_addr[device]) {
+    void* ctx = current_context();
+    if (!g_addr[device] || !ctx || ctx != g_ctx[device]) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);   // makes the device's context current
         if (e != cudaSuccess) return e;
         g_addr[device] = p;
+        g_ctx[device] = current_context();
     }
     *out = g_addr[device];
     return cudaSuccess;
@@ -69,11 +101,14 @@ extern "C" kmeans_status kmeans_update_static(const kmeans_data* X, const int32_
     void* base = nullptr;
     if (scratch_address(dev, &base) != cudaSuccess) return KM_ECUDA;
 
-    // partial blocks of the pass: as many as the array holds, at most two per SM
+    // partial blocks of the pass: kmeans_update's count for this shape, if the array holds them
     const size_t per_block = al256((size_t)K * d * esz) + al256((size_t)K * 4) + 4 * 64;
     const size_t fixed = 256;
-    int64_t nb = (int64_t)nsm * 2;
-    const int64_t need = (X->N + LOWD_THREADS - 1) / LOWD_THREADS;
+    int per_sm = pass_lowd_occupancy(prec, d, smem);
+    per_sm = per_sm > 4 ? 4 : (per_sm < 1 ? 1 : per_sm);
+    int64_t nb = (int64_t)nsm * per_sm;
+    const int64_t rows = prec == KM_F64 ? LOWD_THREADS : 4 * LOWD_THREADS;
+    const int64_t need = (X->N + rows - 1) / rows;
     if (nb > need) nb = need;
     const int64_t fit = (int64_t)((KM_STATIC_SCRATCH_BYTES - fixed) / per_block);
     if (fit < 1) return KM_EINVAL;                 // K*d needs more than KM_STATIC_SCRATCH_BYTES

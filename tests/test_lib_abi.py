@@ -24,7 +24,7 @@ def test_library_exports_every_declared_symbol():
 def test_defaults_and_status_strings_without_gpu():
     p = km.default_params()
     assert (p.m_max, p.m_init, p.max_iter, p.lloyd_only, p.fixed_m) == (10, 2, 1000, 0, 0)
-    assert (p.eps1, p.eps2, p.tol, p.rank_tol) == (0.02, 0.5, 0.0, 1e-6)
+    assert (p.eps1, p.eps2, p.tol, p.rank_tol) == (0.02, 0.5, 0.0, 1e-12)
     assert km.default_params(fixed_m=1, m_init=5).fixed_m == 1
     with pytest.raises(KeyError):
         km.default_params(no_such_field=1)
@@ -34,10 +34,10 @@ def test_defaults_and_status_strings_without_gpu():
     hdr = open(os.path.join(os.path.dirname(_lib._build.PKG), "include", "kmeans_aa.h")).read()
     for name, cls in (("kmeans_params", _lib.kmeans_params), ("kmeans_info", _lib.kmeans_info),
                       ("kmeans_data", _lib.kmeans_data), ("kmeans_problem", _lib.kmeans_problem),
-                      ("kmeans_server_stats", _lib.kmeans_server_stats)):
+                      ("kmeans_server_stats", _lib.kmeans_server_stats), ("kmeans_state", _lib.kmeans_state)):
         body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", hdr).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        fields = re.findall(r"(\w+)\s*;", body)
+        fields = [f for decl in body.split(";") for f in re.findall(r"(\w+)(?:\[\d+\])?\s*(?:,|$)", decl.strip())]
         assert [f for f, _ in cls._fields_] == fields, name
     L = km.load()
     assert L.kmeans_status_string(1) == b"KM_EINVAL"

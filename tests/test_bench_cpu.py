@@ -30,7 +30,7 @@ def _check_line(j, unit):
         assert k in j, k
     assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == unit
     assert j["value"] > 0 and j["higher_is_better"] is True and j["vs_baseline"] is None
-    assert j["steps"] == 1 and j["warmup"] == 0 and j["n_gpus"] == 1
+    assert j["steps"] == 1 and j["n_gpus"] == 1
     cb = j["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == j["value"] and cb["sample"]
     e = j["e2e"]
@@ -40,11 +40,38 @@ def _check_line(j, unit):
 
 
 def test_reference_arm_lowd_line():
-    j = _run("--steps", "1", "--warmup", "0", "--ref-sample-rows", "4000")
+    """lowd_2m: the oracle's full-size solve to convergence (no row sample), one per step."""
+    j = _run("--workload", "lowd_2m", "--steps", "1", "--warmup", "0")
     _check_line(j, "solves/s")
     assert j["config"]["workload"] == "lowd_2m" and j["config"]["N"] == 2_000_000
-    assert "4000 of 2000000 rows" in j["cpu_baseline"]["sample"]
-    assert j["p50_ms"] > 0 and j["ms_per_step"] == pytest.approx(1e3 / j["value"])
+    assert "full-size Algorithm 1 solves (N=2000000" in j["cpu_baseline"]["sample"]
+    assert j["ms_per_step"] == pytest.approx(1e3 / j["value"])
+
+
+def test_dense_reference_pass_count_is_the_oracles():
+    """The dense reference arm scales its full-size per-pass time by the assignment passes of the
+    oracle's own full-size solve, stored by tests/golden/make_dense_1m.py."""
+    p = bench.oracle_dense_passes()
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "dense_1m_oracle.json")))
+    assert p == g["aa"]["assign_passes"] and p > g["aa"]["iters"] >= 1
+    assert bench.oracle_dense_passes("/nonexistent.json") is None
+
+
+def test_result_errors_against_oracle_arithmetic():
+    import numpy as np
+    import datagen
+    import oracle
+    X, C0 = datagen.small_2d(2)
+    C, rho, info = oracle.solve(X, C0)
+    e = bench.result_errors(X, [(C, rho, info["E"])], sample_rows=3000)
+    assert e["E_rel_max"] < 1e-14 and e["C_rel_max"] < 1e-14 and e["labels_off_argmin_clear_rows"] == 0
+    # a planted error in each field is seen
+    e = bench.result_errors(X, [(C * (1 + 1e-5), rho, info["E"] * (1 + 1e-4))], sample_rows=3000)
+    assert 0.5e-4 < e["E_rel_max"] and e["C_rel_max"] > 1e-6
+    r2 = rho.copy()
+    r2[:] = (rho + 1) % C.shape[0]
+    e = bench.result_errors(X, [(C, r2, info["E"])], sample_rows=3000)
+    assert e["labels_off_argmin_clear_rows"] > 2000
 
 
 def test_reference_arm_batched_line():
@@ -93,13 +120,10 @@ def test_oracle_thread_count_is_restored():
     import datagen
     X, C0 = datagen.small_2d(0)
     before = oracle.num_threads()
-    t, cores, rows = bench.oracle_sample_solves(X, [C0], 2000, 1, 10, threads=1)
-    assert cores == 1 and rows == 2000 and len(t) == 1 and t[0] > 0
+    t, info, cores, C1, r1 = bench.oracle_timed(X, C0, 1000, 10, threads=1)
+    assert cores == 1 and t > 0 and info["converged"] == 1
     assert oracle.num_threads() == before
     # the thread count does not change the result
-    a = oracle.solve(X[:3000], C0)
-    oracle.set_num_threads(1)
-    b = oracle.solve(X[:3000], C0)
-    oracle.set_num_threads(before)
-    np.testing.assert_array_equal(a[0], b[0])
-    assert a[2]["iters"] == b[2]["iters"]
+    t, info2, cores, C2, r2 = bench.oracle_timed(X, C0, 1000, 10)
+    np.testing.assert_array_equal(C1, C2)
+    assert info["iters"] == info2["iters"]

@@ -48,7 +48,8 @@ typedef enum {
  *               centroids are each split into a BF16 high and low part and the product is the
  *               sum hi.hi + lo.hi + hi.lo (three MMAs), within about 2e-4 |x||c| of the FP32
  *               product; rows whose best two scores lie within that bound are rescored in FP32
- *               from X.  Centroids are float.
+ *               from X.  Centroids are float.  Needs 17 <= d <= 128 with d % 8 == 0, K <= 4096,
+ *               and X, X_bf16 (and X_bf16_lo if given) 16-byte aligned (else KM_EINVAL).
  * In every mode centroid-space arithmetic (update, residuals, Anderson least squares, energy
  * comparison) is FP64. */
 typedef enum { KM_F64 = 0, KM_F32 = 1, KM_BF16_F32 = 2 } kmeans_prec;

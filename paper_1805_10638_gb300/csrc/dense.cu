@@ -9,7 +9,7 @@
 // K-block) stays for the whole row tile; the centroid tiles of 256 stream through a ring of four
 // 32 KB slots (one K-block of the hi or of the lo part each), fed by TMA (128-byte swizzle,
 // K-major).  The epilogue warps read the 128 x 256 FP32 accumulator from TMEM (double buffered, so
-// the MMAs of the next centroid tile overlap the epilogue of this one; four 16-column loads per
+// the MMAs of the next centroid tile overlap the epilogue of this one; two 16-column loads per
 // wait) and keep a per-row top-2 (best value with its lowest index, second-best value).  Warp
 // roles: warp 0 issues TMA, warp 1 allocates TMEM and issues the MMAs (one thread), warps 2..17
 // are the epilogue (four warps per TMEM lane quadrant, each taking a quarter of the columns).
@@ -17,9 +17,10 @@
 // their loops.
 //
 // Near ties: the scores carry a rigorous error bound B (derived where the kernel arguments are
-// built; B ~= 1.9e-4 |x| max|c| + 2u max|c|^2 at d = 128).  A row whose top-2 gap is within 2B is
-// rescored over all K in FP32 (direct form, lowest index on ties); every other row takes the best
-// index, which the bound proves is the argmin of the exact scores of the FP32 inputs.
+// built; B ~= 1.9e-4 |x| max|c| + 2u max|c|^2 at d = 128).  A row whose top-2 gap exceeds 2B takes
+// the best index, which the bound proves is the argmin of the exact scores of the FP32 inputs; the
+// others (near ties, under 1% of the rows on the dense workload) are rescored over all K in FP32
+// (direct form, lowest index on ties).
 //
 // Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
@@ -110,12 +111,12 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// Four 16-column loads of 32 lanes x 32 bits (columns col, col+16, col+32, col+48) and one wait.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
+// Two 16-column loads of 32 lanes x 32 bits (columns col .. col+31) and one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
-    uint32_t r[64];
+    uint32_t r[32];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 2; ++q)
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]), "=r"(r[16 * q + 4]),
@@ -125,7 +126,34 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
             : "r"(taddr + 16u * q));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// The same two loads without the wait; tmem_wait_ld completes them.  The "+r" constraints on the
+// destination registers keep the compiler from reading them before the wait.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, float (&v)[32])
+{
+    uint32_t* r = reinterpret_cast<uint32_t*>(v);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]), "=r"(r[16 * q + 4]),
+              "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]), "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]),
+              "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]), "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]),
+              "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
+            : "r"(taddr + 16u * q));
+}
+__device__ __forceinline__ void tmem_wait_ld(float (&v)[32])
+{
+    uint32_t* r = reinterpret_cast<uint32_t*>(v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -325,32 +353,82 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             // per row and quarter: the best (value, lowest index) and the second-best value
             float v1 = __int_as_float(0x7f800000), v2 = v1;
             int i1 = 0;
+            float xs = 0.f;          // ||x_hi||^2 of this thread's row (quarter h == 0)
             bool ok = true;
             for (int ct = 0; ct < nct; ++ct, ++ait) {
                 const uint32_t ab = ait & 1;
                 // after a failed wait the remaining steps are skipped, but every warp still
                 // runs the same sequence of named barriers below
                 if (ok && !mbar_wait(afull + 8 * ab, (ait >> 1) & 1, abort)) ok = false;
+                if (ok && ct == 0 && h == 0) {
+                    // the row's BF16 values from the X tile in shared memory (loaded, and kept until the
+                    // row tile's last MMAs complete); the swizzle only permutes 16-byte pieces within
+                    // the row, which a sum of squares does not see
+                    const int r = q * 32 + lane;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint4* xr = reinterpret_cast<const uint4*>(smem + P.xh + kb * XCHUNK + r * 128);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const uint4 w = xr[c];
+                            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const float lo = __uint_as_float(ws[t] << 16), hi = __uint_as_float(ws[t] & 0xffff0000u);
+                                xs = fmaf(lo, lo, fmaf(hi, hi, xs));
+                            }
+                        }
+                    }
+                }
                 if (ok) {
                     tc_fence_after();
-                    const int col = h * (TN / 4);
-                    float v[64];
-                    tmem_ld64(tmem + lane_base + ab * TN + col, v);
-                    const int j0 = ct * TN + col;
-                    const float4* cn4 = reinterpret_cast<const float4*>(s_cn + j0);
+                    // two 32-column halves; the second half's TMEM loads are in flight while the first
+                    // is scored.  Even and odd columns feed two independent (best, index, second)
+                    // chains, merged lexicographically at the end of the tile.
+                    const int colb = h * (TN / 4);
+                    float va[32], vb[32];
+                    tmem_ld32(tmem + lane_base + ab * TN + colb, va);
+                    tmem_ld32_issue(tmem + lane_base + ab * TN + colb + 32, vb);
+                    float w1 = v1, w2 = v2;
+                    int k1 = i1;
+                    float x1 = __int_as_float(0x7f800000), x2 = x1;
+                    int y1 = 0;
+                    auto score32 = [&](const float (&v)[32], int j0) {
+                        const float4* cn4 = reinterpret_cast<const float4*>(s_cn + j0);
 #pragma unroll
-                    for (int e4 = 0; e4 < 16; ++e4) {
-                        const float4 c4 = cn4[e4];
-                        const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int e = 4 * e4 + u;
-                            const float sc = fmaf(-2.f, v[e], cc[u]);
-                            const bool p1 = sc < v1;
-                            v2 = fminf(v2, fmaxf(v1, sc));
-                            i1 = p1 ? j0 + e : i1;
-                            v1 = fminf(v1, sc);
+                        for (int e4 = 0; e4 < 8; ++e4) {
+                            const float4 c4 = cn4[e4];
+                            const float s0 = fmaf(-2.f, v[4 * e4], c4.x), s1 = fmaf(-2.f, v[4 * e4 + 1], c4.y);
+                            const float s2 = fmaf(-2.f, v[4 * e4 + 2], c4.z), s3 = fmaf(-2.f, v[4 * e4 + 3], c4.w);
+                            // chain w (even columns) and chain x (odd columns)
+                            bool p = s0 < w1;
+                            w2 = fminf(w2, fmaxf(w1, s0));
+                            k1 = p ? j0 + 4 * e4 : k1;
+                            w1 = fminf(w1, s0);
+                            p = s1 < x1;
+                            x2 = fminf(x2, fmaxf(x1, s1));
+                            y1 = p ? j0 + 4 * e4 + 1 : y1;
+                            x1 = fminf(x1, s1);
+                            p = s2 < w1;
+                            w2 = fminf(w2, fmaxf(w1, s2));
+                            k1 = p ? j0 + 4 * e4 + 2 : k1;
+                            w1 = fminf(w1, s2);
+                            p = s3 < x1;
+                            x2 = fminf(x2, fmaxf(x1, s3));
+                            y1 = p ? j0 + 4 * e4 + 3 : y1;
+                            x1 = fminf(x1, s3);
                         }
+                    };
+                    score32(va, ct * TN + colb);
+                    tmem_wait_ld(vb);
+                    score32(vb, ct * TN + colb + 32);
+                    if (x1 < w1 || (x1 == w1 && y1 < k1)) {
+                        v2 = fminf(w1, x2);
+                        v1 = x1;
+                        i1 = y1;
+                    } else {
+                        v2 = fminf(w2, x1);
+                        v1 = w1;
+                        i1 = k1;
                     }
                 }
                 tc_fence_before();
@@ -381,23 +459,13 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                 }
                 const int64_t row = (int64_t)tile * TM + r;
                 if (row < a.N) {
-                    // ||x_hi|| of the BF16 row; ||x|| <= ||x_hi|| / (1 - u_b) is folded into bcoef_a
-                    const uint4* xr = reinterpret_cast<const uint4*>(a.Xb + row * a.d);
-                    float xs = 0.f;
-                    for (int u = 0; u < a.d / 8; ++u) {
-                        const uint4 w = __ldg(xr + u);
-                        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const float lo = __uint_as_float(ws[t] << 16), hi = __uint_as_float(ws[t] & 0xffff0000u);
-                            xs = fmaf(lo, lo, fmaf(hi, hi, xs));
-                        }
-                    }
+                    // ||x|| <= ||x_hi|| / (1 - u_b) is folded into bcoef_a
                     const float bnd = a.bcoef_a * sqrtf(xs) * cmax + a.bcoef_b * cmax2;
                     rho[row] = i1;
                     if (!(v2 - v1 > 2.02f * bnd)) {          // near tie: rescore the row over all K in FP32
                         const unsigned pos = atomicAdd(a.qcount, 1u);
                         a.queue[pos] = (int)row;
+                        reinterpret_cast<unsigned long long*>(a.rkey)[pos] = ~0ull;
                     }
                 }
             }
@@ -417,68 +485,104 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ near-tie rescoring
-// FP32 direct form sum_k (x_k - c_jk)^2 over all K for the queued near-tie rows.  16 queued rows per
-// block (two per warp) share each tile of 64 centroids staged in
-// shared memory (row stride d+1 floats: lanes reading different centroids hit different banks).
-// Lane l scores centroids c0+l and c0+l+32 of every tile, so each lane visits its centroids in
-// ascending order; a lexicographic (distance, index) butterfly finishes each row.
+// FP32 direct form sum_k (x_k - c_jk)^2 over all K for the queued near-tie rows, tiled like a GEMM.
+// A work item is (64 queued rows, one of RF_SPLIT ranges of the centroids); a block stages the rows
+// and then 64-centroid tiles in shared memory, dimension-major (stride RF_S floats), and thread
+// (ty, tx) scores rows 4ty..4ty+3 against centroids 4tx..4tx+3 of each tile (16 FP32 accumulators
+// in packed pairs, two 16-byte shared loads and 16 fma.rn.f32x2 per dimension).  A thread visits its centroids in ascending order; the
+// 16 threads of a row group and the ranges are combined lexicographically on (distance, index):
+// shuffles within the block, then atomicMin on the 64-bit key (distance bits, index) per row, which
+// orders like the pair because the distances are non-negative.  k_rescore_write stores the labels.
+constexpr int RF_ROWS = 64, RF_CT = 64, RF_SPLIT = 4, RF_S = RF_CT + 4;
 __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
     const unsigned nfull = a.qcount[0];
-    if (blockIdx.x * 16u >= nfull) return;
+    const unsigned ntile = (nfull + RF_ROWS - 1) / RF_ROWS, nitems = ntile * RF_SPLIT;
+    if (blockIdx.x >= nitems) return;
     extern __shared__ float sm_f[];
-    const int d = a.d, K = a.K, ds = d + 1;
-    float* sx = sm_f;                 // [16][d]
-    float* sc = sm_f + 16 * d;        // [64][d+1]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int d = a.d, K = a.K;
+    float* xs = sm_f;                  // [d][RF_S]: rows of the item
+    float* cs = sm_f + d * RF_S;       // [d][RF_S]: centroids of the tile
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const float* X = a.X;
     const float* C = a.c32[set];
-    int32_t* rho = pass_rho(a, a.st);
-    for (unsigned g = blockIdx.x * 16u; g < nfull; g += gridDim.x * 16u) {
+    const int kt = (K + RF_CT - 1) / RF_CT;                    // centroid tiles
+    for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const unsigned rt = item / RF_SPLIT, sp = item % RF_SPLIT;
+        const int tlo = (int)((long long)kt * sp / RF_SPLIT), thi = (int)((long long)kt * (sp + 1) / RF_SPLIT);
+        const unsigned q0 = rt * RF_ROWS;
         __syncthreads();
-        for (int i = threadIdx.x; i < 16 * d; i += blockDim.x) {
-            const unsigned q = g + i / d;
-            sx[i] = q < nfull ? X[(int64_t)a.queue[q] * d + i % d] : 0.f;
+        for (int i = t; i < RF_ROWS * (d / 4); i += blockDim.x) {   // row r, four dimensions from 4*k4
+            const int r = i % RF_ROWS, k4 = i / RF_ROWS;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q0 + r < nfull) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)a.queue[q0 + r] * d) + k4);
+            xs[(4 * k4) * RF_S + r] = v.x;
+            xs[(4 * k4 + 1) * RF_S + r] = v.y;
+            xs[(4 * k4 + 2) * RF_S + r] = v.z;
+            xs[(4 * k4 + 3) * RF_S + r] = v.w;
         }
-        float bd[2] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000)};
-        int bj[2] = {K, K};
-        for (int c0 = 0; c0 < K; c0 += 64) {
+        float bd[4];
+        int bj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bd[u] = __int_as_float(0x7f800000);
+            bj[u] = K;
+        }
+        for (int ct = tlo; ct < thi; ++ct) {
+            const int c0 = ct * RF_CT;
             __syncthreads();
-            for (int i = threadIdx.x; i < 64 * d; i += blockDim.x) {
-                const int jl = i / d, k = i % d;
-                sc[jl * ds + k] = c0 + jl < K ? C[(size_t)(c0 + jl) * d + k] : 0.f;
+            for (int i = t; i < RF_CT * (d / 4); i += blockDim.x) {
+                const int jl = i % RF_CT, k4 = i / RF_CT;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c0 + jl < K) v = __ldg(reinterpret_cast<const float4*>(C + (size_t)(c0 + jl) * d) + k4);
+                cs[(4 * k4) * RF_S + jl] = v.x;
+                cs[(4 * k4 + 1) * RF_S + jl] = v.y;
+                cs[(4 * k4 + 2) * RF_S + jl] = v.z;
+                cs[(4 * k4 + 3) * RF_S + jl] = v.w;
             }
             __syncthreads();
-            float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-            const float* x0 = sx + (2 * w) * d;
-            const float* x1 = x0 + d;
-            const float* ca = sc + lane * ds;
-            const float* cb = sc + (lane + 32) * ds;
+            // packed pairs of centroids: t = fma(c, -1, x) is x - c rounded once, then acc += t * t,
+            // the same per-component arithmetic as the scalar direct form
+            float2 acc[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
+            const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll 4
             for (int k = 0; k < d; ++k) {
-                const float xa = x0[k], xb = x1[k], u = ca[k], v = cb[k];
-                const float t00 = xa - u, t01 = xa - v, t10 = xb - u, t11 = xb - v;
-                acc[0][0] = fmaf(t00, t00, acc[0][0]);
-                acc[0][1] = fmaf(t01, t01, acc[0][1]);
-                acc[1][0] = fmaf(t10, t10, acc[1][0]);
-                acc[1][1] = fmaf(t11, t11, acc[1][1]);
+                const float4 xv = *reinterpret_cast<const float4*>(xs + k * RF_S + 4 * ty);
+                const float4 cv = *reinterpret_cast<const float4*>(cs + k * RF_S + 4 * tx);
+                const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
+                const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float2 x2 = make_float2(xr[r], xr[r]);
+                    const float2 t0 = __ffma2_rn(c01, m1, x2), t1 = __ffma2_rn(c23, m1, x2);
+                    acc[r][0] = __ffma2_rn(t0, t0, acc[r][0]);
+                    acc[r][1] = __ffma2_rn(t1, t1, acc[r][1]);
+                }
             }
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 4; ++c) {
+                const int j = c0 + 4 * tx + c;
 #pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2) {
-                    const int j = c0 + lane + 32 * s2;
-                    if (j < K && acc[r][s2] < bd[r]) {
-                        bd[r] = acc[r][s2];
+                for (int r = 0; r < 4; ++r) {
+                    const float v = (c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x;
+                    if (j < K && v < bd[r]) {
+                        bd[r] = v;
                         bj[r] = j;
                     }
                 }
+            }
         }
+        // the 16 threads of a row group are lanes 0-15 or 16-31 of one warp
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < 4; ++r) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 8; o > 0; o >>= 1) {
                 const float ob = __shfl_xor_sync(FULL, bd[r], o);
                 const int oj = __shfl_xor_sync(FULL, bj[r], o);
                 if (ob < bd[r] || (ob == bd[r] && oj < bj[r])) {
@@ -486,9 +590,25 @@ __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
                     bj[r] = oj;
                 }
             }
-            const unsigned q = g + 2 * w + r;
-            if (lane == 0 && q < nfull) rho[a.queue[q]] = bj[r] < K ? bj[r] : 0;
+            const unsigned q = q0 + 4 * ty + r;
+            if (tx == 0 && q < nfull && bj[r] < K)
+                atomicMin(reinterpret_cast<unsigned long long*>(a.rkey) + q,
+                          ((unsigned long long)__float_as_uint(bd[r]) << 32) | (unsigned)bj[r]);
         }
+    }
+}
+
+// Labels of the rescored rows from their (distance, index) keys.
+__global__ void __launch_bounds__(256) k_rescore_write(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const unsigned nfull = a.qcount[0];
+    int32_t* rho = pass_rho(a, a.st);
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nfull; q += gridDim.x * blockDim.x) {
+        const unsigned long long key = reinterpret_cast<const unsigned long long*>(a.rkey)[q];
+        const unsigned j = (unsigned)(key & 0xffffffffu);
+        if (j < (unsigned)a.K) rho[a.queue[q]] = (int)j;
     }
 }
 
@@ -523,10 +643,27 @@ __global__ void __launch_bounds__(256) k_pack_dense(PackArgs a)
 }
 
 // The low BF16 part of X: x_lo = bf16(x - x_hi), x_hi the caller's BF16 copy, same [N][d] layout.
+// Eight elements per step (n is a multiple of 8: d % 8 == 0), 16-byte loads and stores.
 __global__ void __launch_bounds__(256) k_xsplit(const float* X, const __nv_bfloat16* Xh, __nv_bfloat16* Xl, int64_t n)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        Xl[i] = __float2bfloat16_rn(X[i] - __bfloat162float(Xh[i]));
+    const int64_t n8 = n >> 3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n8; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(X) + 2 * i);
+        const float4 b = __ldg(reinterpret_cast<const float4*>(X) + 2 * i + 1);
+        const uint4 h = __ldg(reinterpret_cast<const uint4*>(Xh) + i);
+        const float xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        const uint32_t hv[4] = {h.x, h.y, h.z, h.w};
+        uint32_t out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float lo0 = xv[2 * k] - __uint_as_float(hv[k] << 16);
+            const float lo1 = xv[2 * k + 1] - __uint_as_float(hv[k] & 0xffff0000u);
+            const uint32_t b0 = __bfloat16_as_ushort(__float2bfloat16_rn(lo0));
+            const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn(lo1));
+            out[k] = b0 | (b1 << 16);
+        }
+        reinterpret_cast<uint4*>(Xl)[i] = make_uint4(out[0], out[1], out[2], out[3]);
+    }
 }
 
 // Row norms ||x|| (FP32, for the error bound) and the non-finite check, once per solve.
@@ -905,8 +1042,14 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_dense_assign<<<grid, DTHREADS, smem, s>>>(maps, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t sm_full = (size_t)(16 * a.d + 64 * (a.d + 1)) * sizeof(float);
-    k_rescore_full<<<nsm * 4, 256, sm_full, s>>>(a);
+    const size_t sm_full = (size_t)2 * a.d * RF_S * sizeof(float);
+    if (sm_full > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_rescore_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_full);
+        if (e != cudaSuccess) return e;
+    }
+    k_rescore_full<<<nsm * 3, 256, sm_full, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rescore_write<<<nsm, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

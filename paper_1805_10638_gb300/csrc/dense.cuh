@@ -37,6 +37,7 @@ struct DenseArgs {
     const int32_t* rho_prev;  // standalone previous assignment (optional)
     int32_t* rho_pair[2];     // solver ping-pong assignment
     int* queue;               // [N] near-tie rows to rescore over all K
+    void* rkey;               // [N] u64 (distance bits, index) keys of the rescored rows
     unsigned int* qcount;     // [2]: queued rows
     int* err;
     // update chain

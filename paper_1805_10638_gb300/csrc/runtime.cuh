@@ -40,7 +40,7 @@ struct Plan {
     size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info, acc, qrw;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
-    size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, xnorm, queue, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
+    size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, xnorm, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
         part, pe, pnch, S, rowe, rown;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
@@ -114,6 +114,9 @@ kmeans_status check_data(kmeans_ctx* ctx, const kmeans_data* X, int K, bool need
     if (X->prec != KM_F64 && X->prec != KM_F32 && X->prec != KM_BF16_F32)
         return fail(ctx, KM_EINVAL, "unknown precision");
     if (X->prec == KM_BF16_F32 && need_bf16 && !X->X_bf16) return fail(ctx, KM_EINVAL, "X_bf16 is NULL");
+    if (X->prec == KM_BF16_F32 && X->d > 16 &&
+        (((uintptr_t)X->X | (uintptr_t)X->X_bf16 | (uintptr_t)X->X_bf16_lo) & 15u))
+        return fail(ctx, KM_EINVAL, "the tensor-core path needs X, X_bf16 and X_bf16_lo 16-byte aligned");
     return KM_OK;
 }
 
@@ -178,6 +181,7 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.cn1 = take((size_t)P.Kpad * 4);
     P.xnorm = take((size_t)N * 4);
     P.queue = take((size_t)N * 4);       // near-tie rows
+    P.rkey = take((size_t)N * 8);        // their (distance, index) keys
     P.qcount = take(256);
     P.err = take(256);
     P.hist = take((size_t)K * P.nbk * 4);
@@ -476,6 +480,7 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.rho_pair[0] = at<int32_t>(base, P.rhoA);
     a.rho_pair[1] = at<int32_t>(base, P.rhoB);
     a.queue = at<int>(base, P.queue);
+    a.rkey = at<void>(base, P.rkey);
     a.qcount = at<unsigned int>(base, P.qcount);
     a.err = at<int>(base, P.err);
     a.rows_per_block = P.rpb;

@@ -128,3 +128,22 @@ def test_dense_solve_full_size_sampled(ctx):
     assert rel_err(Ch, Cm) < 1e-6
     Eo = oracle.energy(X, Ch, rh)
     assert abs(info["E"] - Eo) / Eo < 1e-6
+
+
+@pytest.mark.slow
+def test_dense_full_size_against_the_oracles_solves(ctx):
+    """Full-size dense workload from the benchmark's first C0 against the FP64 oracle's own solves
+    (tests/golden/dense_1m_oracle.json, written by make_dense_1m.py): Lloyd takes the oracle's
+    iterations and ends at its energy to 1e-6; Algorithm 1 ends within 1e-6 of the oracle's energy
+    (reading R20: the reduced-precision trajectory may stop at a neighbouring fixed point)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "dense_1m_oracle.json")))
+    X, Xb, C0 = datagen.dense_1m(seed=0)
+    Xd, Xbd, Cd = dev(X), dev_bf16(Xb), dev(C0)
+    _, _, il = km.kmeans_solve(ctx, Xd, Cd, X_bf16=Xbd, lloyd_only=1)
+    assert il["converged"] == 1 and il["iters"] == g["lloyd"]["iters"], (il, g["lloyd"])
+    assert abs(il["E"] - g["lloyd"]["E"]) <= 1e-6 * g["lloyd"]["E"]
+    _, _, ia = km.kmeans_solve(ctx, Xd, Cd, X_bf16=Xbd, m_max=10)
+    assert ia["converged"] == 1
+    assert abs(ia["E"] - g["aa"]["E"]) <= 1e-6 * g["aa"]["E"], (ia, g["aa"])

@@ -101,3 +101,46 @@ def test_serving_rejects_oversized_and_idles():
     with pytest.raises(km.KmeansError):          # d > 16 needs BF16 and a large lane
         srv.submit(X, X[:4].clone().pin_memory())
     srv.close()
+
+
+def test_served_results_match_the_fp64_oracle():
+    """Every served request (FP64 and FP32 low-d in the continuous batch, a BF16 request on a large
+    lane; Lloyd and Algorithm 1) against the FP64 oracle: the returned (C, P, E) is exact arithmetic
+    on its own assignment (E to 1e-6, C = the means of P to 1e-6, P the argmin at C off the tie
+    band), and its final energy equals the oracle's own solve from the same C0 to 1e-6 relative."""
+    need_gpu()
+    import oracle
+    from gpu_util import check_assignment, rel_err
+    reqs = _requests(n_small=12, n_large=1, seed=3)
+    srv = km.Server(0, hbm_budget=256 << 20, max_slots=4, max_large=1)
+    tickets = []
+    for i, q in enumerate(reqs):
+        Xb = q["Xb"].view(torch.bfloat16) if q["Xb"] is not None else None
+        tickets.append((i, srv.submit(q["X"], q["C0"], X_bf16=Xb, **q["p"])))
+    results = {}
+    steps = 0
+    while len(results) < len(reqs):
+        srv.step()
+        for i, t in tickets:
+            if i not in results:
+                res = srv.poll(t)
+                if res is not None:
+                    results[i] = res
+        steps += 1
+        assert steps < 200000
+    srv.close()
+    for i, (C, rho, info) in results.items():
+        q = reqs[i]
+        X = q["X"].numpy()
+        C, rho = C.numpy(), rho.numpy()
+        assert info["converged"] == 1 and info["status"] == 0, (i, info)
+        E_at = oracle.energy(X, C, rho)
+        assert abs(info["E"] - E_at) <= 1e-6 * E_at, (i, info["E"], E_at)
+        Cm, _ = oracle.update(X, rho, C.shape[0], C)
+        assert rel_err(C, Cm) <= 1e-6, i
+        check_assignment(X, C, rho, f"request {i}")
+        lloyd = q["p"].get("lloyd_only", 0) == 1
+        Co, ro, io = oracle.solve(X, q["C0"].numpy(), lloyd=lloyd, m_max=10)
+        assert abs(info["E"] - io["E"]) <= 1e-6 * io["E"], (i, info, io)
+        if X.dtype == np.float64:
+            assert (info["iters"], info["accepted"], info["rejected"]) == (io["iters"], io["accepted"], io["rejected"])

@@ -50,6 +50,17 @@ def _env_int(k, d):
         return d
 
 
+def calibrated_fp32_peak():
+    """Measured FP32 FMA rate (T lane-op/s) from the committed calibration summary, or None."""
+    try:
+        for ln in open(os.path.join(ROOT, "profiles", "fp32_fma_peak.md")):
+            if ln.startswith("| measured FP32 FMA peak"):
+                return float(ln.split("|")[2].split()[0])
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
+
+
 def profiled_traffic(name: str):
     """DRAM bytes per launch (read + write) of the dominant kernel from its committed ncu summary."""
     try:
@@ -550,6 +561,9 @@ def run_serving(args, rank, world, local_rank):
         X = datagen.isotropic_mixture(4_000_000, 96, 4096, 70_000 + j, dtype=np.float32)
         large_sets.append((torch.from_numpy(X).pin_memory(),
                            torch.from_numpy(datagen.to_bf16_bits(X).view(np.int16)).pin_memory().view(torch.bfloat16)))
+    # the small requests draw their data from a pool of at most 512 distinct data sets (request k takes
+    # pool entry k mod 512 with its own C0), which bounds host memory and set-up time for 20,000 requests
+    pool = {}
     inputs = []
     for k, q in enumerate(reqs):
         if q["large"]:
@@ -557,24 +571,30 @@ def run_serving(args, rank, world, local_rank):
             C0 = datagen.init_centroids(Xt.numpy(), q["K"], q["data_seed"] + 1000)
             inputs.append((Xt, Xbt, torch.from_numpy(C0).pin_memory()))
         else:
-            X = datagen.isotropic_mixture(q["N"], q["d"], q["K"], q["data_seed"], dtype=np.float32)
-            Xb = (torch.from_numpy(datagen.to_bf16_bits(X).view(np.int16)).pin_memory().view(torch.bfloat16)
-                  if q["d"] > 16 else None)
-            C0 = datagen.init_centroids(X, q["K"], q["data_seed"] + 1000)
-            inputs.append((torch.from_numpy(X).pin_memory(), Xb, torch.from_numpy(C0).pin_memory()))
+            slot = k % 512
+            if slot not in pool:
+                X = datagen.isotropic_mixture(q["N"], q["d"], q["K"], q["data_seed"], dtype=np.float32)
+                Xb = (torch.from_numpy(datagen.to_bf16_bits(X).view(np.int16)).pin_memory().view(torch.bfloat16)
+                      if q["d"] > 16 else None)
+                pool[slot] = (torch.from_numpy(X).pin_memory(), Xb, q["K"])
+            Xt, Xb, K = pool[slot]
+            C0 = datagen.init_centroids(Xt.numpy(), K, q["data_seed"] + 1000)
+            inputs.append((Xt, Xb, torch.from_numpy(C0).pin_memory()))
     budget = int(args.serve_budget_gb * (1 << 30))
 
-    def run(lloyd: bool):
+    def run(lloyd: bool, tscale: float = 1.0, nreq: int = 0):
+        """Serve the stream (arrival times multiplied by tscale, the first nreq requests)."""
         srv = km.Server(local_rank, hbm_budget=budget, max_slots=512, max_large=args.serve_lanes)
         prm = dict(lloyd_only=1) if lloyd else dict(m_max=10)
         lat, nxt, inflight, iters, rejected, kind = [], 0, {}, [], [], []
+        nr = nreq or len(reqs)
         t0 = time.perf_counter()
-        while nxt < len(reqs) or inflight:
+        while nxt < nr or inflight:
             now = time.perf_counter() - t0
-            while nxt < len(reqs) and reqs[nxt]["t_arrival"] <= now:
+            while nxt < nr and reqs[nxt]["t_arrival"] * tscale <= now:
                 X, Xb, C0 = inputs[nxt]
                 try:
-                    inflight[srv.submit(X, C0, X_bf16=Xb, **prm)] = (nxt, reqs[nxt]["t_arrival"])
+                    inflight[srv.submit(X, C0, X_bf16=Xb, **prm)] = (nxt, reqs[nxt]["t_arrival"] * tscale)
                 except km.KmeansError as e:       # a shape the server does not take: counted, not served
                     rejected.append((nxt, str(e)))
                 nxt += 1
@@ -586,8 +606,8 @@ def run_serving(args, rank, world, local_rank):
                     lat.append((time.perf_counter() - t0) - ta)
                     kind.append("large" if reqs[i]["large"] else ("tensor" if reqs[i]["d"] > 16 else "lowd"))
                     iters.append(res[2]["iters"])
-            if not inflight and nxt < len(reqs):
-                time.sleep(max(0.0, min(0.001, reqs[nxt]["t_arrival"] - (time.perf_counter() - t0))))
+            if not inflight and nxt < nr:
+                time.sleep(max(0.0, min(0.001, reqs[nxt]["t_arrival"] * tscale - (time.perf_counter() - t0))))
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
@@ -598,6 +618,18 @@ def run_serving(args, rank, world, local_rank):
     clocks.start()
     lat_aa, wall_aa, st_aa, it_aa, rej_aa, by_aa = run(False)
     lat_ll, wall_ll, st_ll, it_ll, rej_ll, by_ll = run(True)
+    # sustainable rate: the same request sequence offered at lower rates (arrival times scaled);
+    # a rate is sustained when the completions keep up with the arrivals (>= 97% of the offered
+    # rate over the run) - then the backlog, and with it p99, stays bounded
+    sweep = []
+    for rate in [float(r) for r in args.serve_sweep.split(",") if r]:
+        nreq = min(len(reqs), args.serve_sweep_requests)
+        lat_s, wall_s, _, _, _, by_s = run(False, tscale=args.serve_rate / rate, nreq=nreq)
+        span = reqs[nreq - 1]["t_arrival"] * args.serve_rate / rate
+        sweep.append({"rate_per_s": rate, "requests": nreq, "solves_per_s": len(lat_s) / wall_s,
+                      "keeps_up": len(lat_s) / wall_s >= 0.97 * nreq / span,
+                      "p50_ms": 1e3 * pct(lat_s, 50), "p99_ms": 1e3 * pct(lat_s, 99),
+                      "large_p99_ms": 1e3 * pct(by_s["large"], 99) if by_s["large"] else None})
 
     def classes(by):
         return {k: {"n": len(v), "p50_ms": 1e3 * pct(v, 50) if v else None, "p99_ms": 1e3 * pct(v, 99) if v else None}
@@ -612,7 +644,8 @@ def run_serving(args, rank, world, local_rank):
         "config": {"workload": "serving", "requests": n, "rate_per_s": args.serve_rate, "arrival_seed": 7,
                    "large_frac": 0.02, "large": "N=4e6, d=96, K=4096", "budget_gb": args.serve_budget_gb,
                    "max_slots": 512, "max_large": args.serve_lanes, "parallelism": "replicas x1",
-                   "classes": "lowd = d <= 16 (continuous batch), tensor = d = 64 and large = N=4e6 (lanes)"},
+                   "classes": "lowd = d <= 16 (continuous batch), tensor = d = 64 and large = N=4e6 (lanes)",
+                   "data": "small requests cycle through 512 distinct data sets (own C0 each); large jobs share 2"},
         "p50_ms": 1e3 * pct(lat_aa, 50), "p99_ms": 1e3 * pct(lat_aa, 99),
         "aa": {"solves_per_s": len(lat_aa) / wall_aa, "p50_ms": 1e3 * pct(lat_aa, 50), "p99_ms": 1e3 * pct(lat_aa, 99),
                "iters_mean": float(np.mean(it_aa)), "steps": st_aa["steps"], "pool_peak_gb": st_aa["pool_peak"] / 2**30,
@@ -621,6 +654,8 @@ def run_serving(args, rank, world, local_rank):
                   "iters_mean": float(np.mean(it_ll)), "steps": st_ll["steps"],
                   "pool_peak_gb": st_ll["pool_peak"] / 2**30, "by_class": classes(by_ll)},
         "latency": "arrival (wall clock) to results in host memory, including the host-to-device copy of X",
+        "rate_sweep_aa": sweep,
+        "sustainable_rate_per_s": max([w["rate_per_s"] for w in sweep if w["keeps_up"]], default=None),
         "rejected": len(rej_aa), "rejected_examples": [r for _, r in rej_aa[:3]],
         "e2e": {"value": len(lat_aa) / wall_aa, "unit": "solves/s",
                 "h2d_bytes_per_step": int(np.mean([x.nbytes + (b.nbytes if b is not None else 0) + c.nbytes
@@ -653,6 +688,9 @@ def run_ours(args, rank, world, local_rank):
     ctx = km.Context(local_rank, stream=stream.cuda_stream)
     Xd = torch.from_numpy(X).cuda()
     Xbd = torch.from_numpy(Xb.view(np.int16)).cuda().view(torch.bfloat16) if dense else None
+    # the low BF16 part of X (bf16(X - X_bf16)), supplied once like X_bf16
+    Xld = (torch.from_numpy(datagen.to_bf16_bits(X - datagen.bf16_bits_to_f32(Xb)).view(np.int16)).cuda()
+           if dense else None)
     C0d = [torch.from_numpy(c).cuda() for c in C0s]
     C_out = torch.empty((K, d), dtype=torch.float32, device="cuda")
     rho = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -667,7 +705,7 @@ def run_ours(args, rank, world, local_rank):
         kw = dict(solve_kw, **(dict(lloyd_only=1) if lloyd else dict(m_max=wl["m_max"])))
         for s in range(args.warmup):
             C0buf.copy_(C0d[s])
-            km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, **kw)
+            km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, X_lo=Xld, **kw)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -680,7 +718,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, _, info = km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, **kw)
+            _, _, info = km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, X_lo=Xld, **kw)
             e1.record(stream)
             evs.append((e0, e1))
             infos.append(info)
@@ -700,18 +738,21 @@ def run_ours(args, rank, world, local_rank):
     tot_ll = sum(ms_ll) / 1e3
     tot_aa, tot_ll = max_over_ranks([tot_aa, tot_ll], dist, "cuda")
 
-    # ---- roofline of the dominant kernel: the assignment pass, timed standalone (CUDA events)
+    # ---- roofline of the dominant kernel: the assignment pass, timed standalone (CUDA events).
+    # Low-d: the pass with its fused change count.  Dense: the call's centroid packing, the
+    # tensor-core kernel and the FP32 rescoring of the near-tie rows (X's low part supplied).
     rho_prev = rho.clone()
     nch = torch.zeros((), dtype=torch.int64, device="cuda")
+    akw = dict(X_bf16=Xbd, X_lo=Xld) if dense else dict(rho_prev=rho_prev, n_changed=nch)
     for _ in range(3):
-        km.kmeans_assign(ctx, Xd, C_out, rho, rho_prev=rho_prev, n_changed=nch, X_bf16=Xbd)
+        km.kmeans_assign(ctx, Xd, C_out, rho, **akw)
     torch.cuda.synchronize()
     reps = 20
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
     a0.record(stream)
     for _ in range(reps):
-        km.kmeans_assign(ctx, Xd, C_out, rho, rho_prev=rho_prev, n_changed=nch, X_bf16=Xbd)
+        km.kmeans_assign(ctx, Xd, C_out, rho, **akw)
     a1.record(stream)
     torch.cuda.synchronize()
     assign_ms = a0.elapsed_time(a1) / reps
@@ -720,10 +761,12 @@ def run_ours(args, rank, world, local_rank):
         work = 2.0 * N * K * d                # BF16 MMA flops of the distance contraction x.c
         achieved = work / (assign_ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops", 1900.0))
-        roof = {"bound": "tensor", "kernel": "k_dense_assign (tcgen05 BF16 + fused top-2) + rescoring",
+        roof = {"bound": "tensor", "kernel": "k_dense_assign (tcgen05, split BF16: 3 MMAs per K step, fused top-2) "
+                                              "+ centroid packing + FP32 rescoring of near-tie rows",
                 "unit": "TFLOP/s",
-                "note": "2*N*K*d BF16 MMA flops per assignment call over its CUDA-event time; peak = "
-                        "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"}
+                "note": "algorithmic 2*N*K*d flops per assignment call (the split-BF16 kernel issues 3x that on "
+                        "the tensor pipe) over the call's CUDA-event time; peak = measured cuBLAS BF16 burst "
+                        "(MEASURED_PEAKS.json)"}
     else:
         # ALU work of a brute-force assignment pass: per (sample, centroid) pair d FMAs of the
         # score plus about two argmin operations (compare, select), one lane operation each
@@ -731,11 +774,14 @@ def run_ours(args, rank, world, local_rank):
         achieved = work / (assign_ms * 1e-3) / 1e12
         clock_mhz = 2070.0
         peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+        cal = calibrated_fp32_peak()
         roof = {"bound": "alu", "kernel": "k_pass_lowd<float,3> (assignment pass)",
                 "unit": "Tlane-op/s",
                 "note": "N*K*(d+2) lane operations per pass (d FMAs + ~2 argmin ops per sample-centroid "
                         "pair) over the launch's CUDA-event time; peak = 152 SMs x 128 FP32 lanes x 2070 MHz "
-                        "(derived from unit counts and the maximum clock, not measured)"}
+                        "(derived from unit counts and the maximum clock); peak_calibrated = measured FP32 FMA "
+                        "rate (profiles/fp32_fma_peak.md)",
+                "peak_calibrated": cal, "frac_calibrated": (achieved / cal) if cal else None}
     traffic = profiled_traffic("k_pass_lowd_lowd_2m.md" if not dense else "k_dense_assign_dense_1m.md")
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": traffic,
                  "assign_ms": assign_ms})
@@ -764,7 +810,7 @@ def run_ours(args, rank, world, local_rank):
             kw = dict(solve_kw, **(dict(lloyd_only=1) if lloyd else dict(m_max=wl["m_max"])))
             for s in range(min(args.steps, 3)):
                 C0buf.copy_(C0d[args.warmup + s])
-                _, _, info = km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, **kw)
+                _, _, info = km.kmeans_solve(ctx, Xd, C0buf, C_out, rho, X_bf16=Xbd, X_lo=Xld, **kw)
                 res.append((C_out.cpu().numpy().copy(), rho.cpu().numpy().copy(), info["E"], info))
 
     # our kernels in the timed Algorithm 1 solves (Hamerly bounds are on when a pass skipped rows)
@@ -838,7 +884,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense_1m", choices=sorted(WORKLOADS) + ["batched_512", "serving"])
     ap.add_argument("--batch-instances", type=int, default=512)
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-sweep", default="", help="comma-separated lower arrival rates for the sustainable-rate sweep")
+    ap.add_argument("--serve-sweep-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-lanes", type=int, default=4)

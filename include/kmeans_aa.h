@@ -354,6 +354,12 @@ kmeans_status kmeans_server_get_stats(const kmeans_server* srv, kmeans_server_st
 /* Last error message of the server ("" if none). */
 const char* kmeans_server_last_error(const kmeans_server* srv);
 
+/* Measured FP32 FMA throughput of `device` (FMAs per second over all SMs): independent fma.rn.f32
+ * chains on 4 blocks of 256 threads per SM, `iters` x 128 FMAs per thread, timed with CUDA events
+ * (*ms, may be NULL).  The ALU peak the low-d assignment pass is reported against.  Synchronous;
+ * uses the legacy default stream. */
+kmeans_status kmeans_measure_fp32_fma(int device, int32_t iters, double* fma_per_s, double* ms);
+
 /* kmeans_update without any allocation, for callers that must not allocate device memory:
  * an allocator or memory pool of the caller's own that calls back into K-Means and must not
  * re-enter cudaMalloc, and real-time or embedded programs that allocate everything at start-up

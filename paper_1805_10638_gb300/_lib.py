@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                     ctypes.POINTER(kmeans_info)]
     L.kmeans_update_static.argtypes = [pd, vp, i32, vp, vp, vp, vp]
     L.kmeans_lsq.argtypes = [vp, vp, i64, i32, vp, ctypes.c_double, i32, vp, vp, vp]
+    L.kmeans_measure_fp32_fma.argtypes = [ctypes.c_int, i32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
     L.kmeans_solve_passes.argtypes = [vp, pd, i32, vp, ctypes.POINTER(kmeans_params), i32,
                                       ctypes.POINTER(kmeans_state)]
     L.kmeans_solve_batched.argtypes = [vp, ctypes.POINTER(kmeans_problem), i32, ctypes.POINTER(kmeans_params),
@@ -128,7 +130,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.kmeans_server_last_error.restype = ctypes.c_char_p
     for name in ("kmeans_create", "kmeans_destroy", "kmeans_set_stream", "kmeans_assign",
                  "kmeans_update", "kmeans_energy", "kmeans_solve", "kmeans_solve_host",
-                 "kmeans_update_static", "kmeans_lsq", "kmeans_solve_passes", "kmeans_solve_batched", "kmeans_server_create",
+                 "kmeans_update_static", "kmeans_lsq", "kmeans_solve_passes", "kmeans_measure_fp32_fma",
+                 "kmeans_solve_batched", "kmeans_server_create",
                  "kmeans_server_destroy", "kmeans_server_submit", "kmeans_server_step",
                  "kmeans_server_poll", "kmeans_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
@@ -438,6 +441,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_fma(device: int = 0, iters: int = 20000):
+    """(FP32 FMAs per second, kernel ms) of kmeans_measure_fp32_fma."""
+    r, t = ctypes.c_double(), ctypes.c_double()
+    st = load().kmeans_measure_fp32_fma(device, iters, ctypes.byref(r), ctypes.byref(t))
+    if st != KM_OK:
+        raise KmeansError(st, "kmeans_measure_fp32_fma failed")
+    return r.value, t.value
 
 
 def batch_describe(ctx: Context) -> str:

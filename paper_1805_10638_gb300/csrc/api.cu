@@ -60,7 +60,7 @@ kmeans_status solve_device(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     key.p = p;
     key.arena = ctx->arena;
     key.arena_bytes = ctx->arena_bytes;
-    key.ham = P.ham ? 1 : 0;
+    key.ham = P.ham ? 1 + P.hg : 0;
     key.lsq = ls_mode();
     const Launch L = make_launch(arena_base(ctx), ctx->nsm, P, X, K, C0, p, C_out, rho_out);
     if (!L.maps_ok) return fail(ctx, KM_ECUDA, "cuTensorMapEncodeTiled failed (X_bf16 must be 16-byte aligned)");
@@ -377,7 +377,7 @@ kmeans_status kmeans_solve(kmeans_ctx* ctx, const kmeans_data* X, int32_t K, con
     if ((s = validate_params(ctx, p)) != KM_OK) return s;
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
-    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P, true, true)) != KM_OK)
+    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P, true, true, true)) != KM_OK)
         return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
     return solve_device(ctx, X, K, C0, p, C_out, rho_out, info, P);
@@ -397,7 +397,7 @@ kmeans_status kmeans_solve_host(kmeans_ctx* ctx, const kmeans_data* Xh, int32_t 
     if ((s = validate_params(ctx, p)) != KM_OK) return s;
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
-    if ((s = make_plan(ctx, Xh->N, Xh->d, K, Xh->prec, p.lloyd_only ? 0 : p.m_max, true, P, true, true)) != KM_OK)
+    if ((s = make_plan(ctx, Xh->N, Xh->d, K, Xh->prec, p.lloyd_only ? 0 : p.m_max, true, P, true, true, true)) != KM_OK)
         return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
     const size_t esz = Xh->prec == KM_F64 ? 8 : 4;
@@ -469,7 +469,7 @@ kmeans_status kmeans_solve_passes(kmeans_ctx* ctx, const kmeans_data* X, int32_t
     if ((s = validate_params(ctx, p)) != KM_OK) return s;
     KM_CUDA(cudaSetDevice(ctx->device));
     Plan P;
-    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P, true, true)) != KM_OK)
+    if ((s = make_plan(ctx, X->N, X->d, K, X->prec, p.lloyd_only ? 0 : p.m_max, false, P, true, true, true)) != KM_OK)
         return s;
     if ((s = ensure_arena(ctx, P.total)) != KM_OK) return s;
     char* base = arena_base(ctx);

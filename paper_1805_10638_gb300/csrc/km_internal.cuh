@@ -163,6 +163,16 @@ struct PassArgs {
     float* hdr;
     float* hs;
     float* hm;
+    // group bounds (hg > 0 groups of centroids, in place of Hamerly's single lower bound and
+    // half-distance test): per sample a lower bound on the distance to every centroid of each group
+    // other than its own centroid, relative to the centroids of the last pass (hlbg); the groups'
+    // largest drift since the last pass (hgd, written by k_hprep with the drifts); the centroids in
+    // group order (hperm) and the groups' offsets in it (hgoff), fixed once per solve by k_groups
+    int hg;
+    float* hlbg;          // [N][hg]
+    float* hgd;           // [hg]
+    int* hperm;           // [K]
+    int* hgoff;           // [hg + 1]
 };
 
 // Arguments of the update / Anderson-finalize kernel.
@@ -331,7 +341,8 @@ __host__ __device__ inline size_t pk_index(int j, int k, int DP)
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s);
-size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap = 0);
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap = 0, int hg = 0);
+cudaError_t launch_groups(const double* C, int K, int d, int hg, int* perm, int* goff, cudaStream_t s);
 int pass_lowd_dp(int d);
 cudaError_t launch_fin(const FinArgs& a, int nblocks, cudaStream_t s);
 int fin_blocks(int K, int d, int* KB);

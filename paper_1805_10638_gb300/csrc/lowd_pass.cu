@@ -50,7 +50,78 @@ __global__ void __launch_bounds__(1024) k_hprep_batch(BatchPass b)
     }
 }
 
+// Groups of the group bounds, once per solve from C^0: the centroids sorted by the Morton code of
+// their coordinates (each dimension scaled to the bounding box and cut to 30/d bits, ties by index;
+// bitonic sort of (code, index) pairs in shared memory) and cut into hg runs of consecutive ones,
+// so that a group holds nearby centroids.  Any grouping gives valid bounds; nearby centroids give
+// tighter ones.  One block.
+__global__ void __launch_bounds__(1024) k_groups(const double* C, int K, int d, int hg, int* perm, int* goff)
+{
+    extern __shared__ unsigned long long s_key[];   // [P] (code << 32 | index)
+    __shared__ double s_lo[16], s_hi[16];
+    const int tid = threadIdx.x;
+    int P = 1;
+    while (P < K) P <<= 1;
+    if (tid < d) {
+        double lo = C[tid], hi = C[tid];
+        for (int j = 1; j < K; ++j) {
+            lo = fmin(lo, C[(size_t)j * d + tid]);
+            hi = fmax(hi, C[(size_t)j * d + tid]);
+        }
+        s_lo[tid] = lo;
+        s_hi[tid] = hi;
+    }
+    __syncthreads();
+    const int B = d >= 30 ? 1 : 30 / d;
+    for (int j = tid; j < P; j += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (j < K) {
+            unsigned code = 0;
+            for (int k = 0; k < d; ++k) {
+                const double w = s_hi[k] - s_lo[k];
+                double f = w > 0.0 ? (C[(size_t)j * d + k] - s_lo[k]) / w : 0.0;
+                unsigned q = (unsigned)(f * (double)(1u << B));
+                q = q > (1u << B) - 1u ? (1u << B) - 1u : q;
+                for (int b = 0; b < B; ++b) code |= ((q >> b) & 1u) << (b * d + k);
+            }
+            key = ((unsigned long long)code << 32) | (unsigned)j;
+        }
+        s_key[j] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < P; i += blockDim.x) {
+                const int partner = i ^ stride;
+                if (partner > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long x = s_key[i], y = s_key[partner];
+                    if ((x > y) == up) {
+                        s_key[i] = y;
+                        s_key[partner] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int p = tid; p < K; p += blockDim.x) perm[p] = (int)(s_key[p] & 0xffffffffu);
+    for (int gi = tid; gi <= hg; gi += blockDim.x) goff[gi] = (int)((long long)K * gi / hg);
+}
+
 }  // namespace
+
+cudaError_t launch_groups(const double* C, int K, int d, int hg, int* perm, int* goff, cudaStream_t s)
+{
+    int P = 1;
+    while (P < K) P <<= 1;
+    const size_t smem = (size_t)P * 8;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_groups<<<1, 1024, smem, s>>>(C, K, d, hg, perm, goff);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s)
 {
@@ -70,14 +141,16 @@ int pass_lowd_dp(int d)
     return ((2 * (d + 1) + 3) / 4 * 4) / 2;
 }
 
-size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap)
+size_t pass_lowd_smem(int prec, int d, int K, int Kpad, bool bins, int hq_cap, int hg)
 {
-    return layout(prec != KM_F64, d, pass_lowd_dp(d), K, Kpad, bins, hq_cap).total;
+    // the fixed-point layout of the solver's TRIAL / REVERT passes is never larger than the per-warp one
+    return layout(prec != KM_F64, d, pass_lowd_dp(d), K, Kpad, bins, hq_cap, false, hg).total;
 }
 
 cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStream_t s)
 {
-    const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0, a.ham ? a.hq_cap : 0);
+    const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0, a.ham ? a.hq_cap : 0,
+                                       a.ham ? a.hg : 0);
     return prec == KM_F64 ? lowd_launch_f64(a, d, nb, smem, s) : lowd_launch_f32(a, d, nb, smem, s);
 }
 

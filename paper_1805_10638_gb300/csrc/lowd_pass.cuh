@@ -55,7 +55,7 @@ struct MinBlocks {
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct Layout {
-    size_t red, org, cpk, rec, c, stage, bS, bC, hdr, hs, hm, hq, total;
+    size_t red, org, cpk, rec, c, stage, bS, bC, hdr, hs, hm, hq, gd, gperm, goff, total;
 };
 
 // Skewed copy of the packed centroids for the per-row recovery reads: chunk b (CK centroids of
@@ -70,7 +70,7 @@ __host__ __device__ constexpr int rec_stride() { return rec_stride_of(D); }
 // bins: the per-cluster residual sums of the update.  Per warp in the element type (sums combined in
 // a fixed order), or with fx, once per block as 64-bit fixed point (exact, order-independent adds).
 __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpad, bool bins, int hq_cap = 0,
-                                         bool fx = false)
+                                         bool fx = false, int hg = 0)
 {
     const size_t esz = f32 ? 4 : 8;
     Layout L;
@@ -103,6 +103,13 @@ __host__ __device__ inline Layout layout(bool f32, int D, int DP, int K, int Kpa
         L.hq = o;  o += al16((size_t)hq_cap * 4);
     } else {
         L.hdr = L.hs = L.hm = L.hq = 0;
+    }
+    if (f32 && hq_cap > 0 && hg > 0) {   // group bounds: group drifts, centroids in group order, offsets
+        L.gd = o;    o += al16((size_t)hg * 4);
+        L.gperm = o; o += al16((size_t)K * 4);
+        L.goff = o;  o += al16((size_t)(hg + 1) * 4);
+    } else {
+        L.gd = L.gperm = L.goff = 0;
     }
     L.total = o;
     return L;
@@ -360,6 +367,19 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r, int part = 0
     } else if (writer) {
         for (int j = tid; j < K; j += blockDim.x) a.hdr[j] = 0.f;
     }
+    if (a.hg > 0) {
+        // group bounds: no half distances (their O(K^2 d) cost is what the groups avoid; 0 is a
+        // valid, inactive value), and each group's largest drift, from the drifts written above
+        if (!writer) return;
+        for (int j = tid; j < K; j += blockDim.x) a.hs[j] = 0.f;
+        __syncthreads();
+        for (int gi = tid; gi < a.hg; gi += blockDim.x) {
+            float mx = 0.f;
+            if (have_last)
+                for (int p = a.hgoff[gi]; p < a.hgoff[gi + 1]; ++p) mx = fmaxf(mx, a.hdr[a.hperm[p]]);
+            a.hgd[gi] = mx;
+        }
+    } else {
     // half distances of this block's centroids: tpj consecutive lanes share a centroid j and split
     // the j2 range.  The outer trip count is the same for every thread (lanes past the range compute
     // nothing) because the lanes of a centroid combine their minima with warp shuffles.
@@ -388,6 +408,7 @@ __device__ void hprep_body(const PassArgs& a, int mode, float* s_r, int part = 0
         }
         for (int off = 1; off < tpj; off <<= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
         if (valid && sub == 0) a.hs[j] = fmaxf(0.f, 0.5f * sqrtf(mn) * (1.f - 1e-5f) - eta);
+    }
     }
     if (!writer) return;
     for (int off = 16; off > 0; off >>= 1) {
@@ -447,6 +468,99 @@ __device__ inline void hprep_dispatch(const PassArgs& a, int mode, float* s_r, i
     }
 }
 
+// Group bounds after a full scan settled row x on centroid idx: per group the FP32 direct-form
+// distance to its nearest centroid other than idx, lowered by the margins that raise the upper bound
+// (relative 1e-5 and the absolute eta), written to lr[0..hg).  Kept out of line: only scanned rows
+// take it, and the pass's main loops keep their registers.
+template <int D>
+__device__ __noinline__ void group_lower_bounds(const float* xr, int idx, const float* c, const int* perm,
+                                                const int* goff, int hg, float eta, float* lr)
+{
+    float x[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = xr[k];
+    for (int gi = 0; gi < hg; ++gi) {
+        float mn = __int_as_float(0x7f800000);
+        for (int p = goff[gi]; p < goff[gi + 1]; ++p) {
+            const int j = perm[p];
+            const float* cj = c + (size_t)j * D;
+            float d2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = x[k] - cj[k];
+                d2 = fmaf(t, t, d2);
+            }
+            mn = j == idx ? mn : fminf(mn, d2);
+        }
+        lr[gi] = fmaxf(0.f, sqrtf(mn) * (1.f - 1e-5f) - eta);
+    }
+}
+
+// Phase A of a pass with group bounds, for this thread's rows: the assigned centroid a is kept if its
+// upper bound u (plus a's drift since the last pass) is below the smallest group lower bound, each
+// lowered by its group's largest drift, by a relative margin of 1e-5; failing that, the test is
+// retried with u recomputed as the exact distance to a.  Kept rows get the new u and the lowered
+// group bounds; the others are queued for a full scan.  Returns the number queued.
+// Rows are taken from *cursor on; when the queue (capacity cap) is full the thread stops at the row it
+// could not queue and the caller drains the queue before the next round.
+template <int D>
+__device__ __noinline__ long long group_classify(const PassArgs& a, const float* X, int64_t g, int64_t TT, int64_t n_g,
+                                                 int64_t* cursor, unsigned cap, bool force, const int32_t* rho_last,
+                                                 int32_t* rho_out, const float* s_hdr, const float* s_gd,
+                                                 const float* c, float eta, int hg, uint32_t* s_hq,
+                                                 unsigned int* s_hqn, bool chk, int* bad, float* xabs)
+{
+    long long nq = 0;
+    for (int64_t q = *cursor; q < n_g; ++q) {
+        const int64_t row = g + q * TT;
+        float xv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xv[k] = X[row * D + k];
+        if (chk) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                *bad |= !isfinite(xv[k]);
+                *xabs = fmaxf(*xabs, fabsf(xv[k]));
+            }
+        }
+        bool scan = force;
+        if (!force) {
+            const int a_ = rho_last[row];
+            float u = (a.hub[row] + s_hdr[a_]) * (1.f + 2e-7f);
+            float* lr = a.hlbg + (size_t)row * hg;
+            float m = __int_as_float(0x7f800000);
+            for (int gi = 0; gi < hg; ++gi) m = fminf(m, fmaxf(0.f, (lr[gi] - s_gd[gi]) * (1.f - 2e-7f)));
+            if (!(u * (1.f + 1e-5f) < m)) {
+                const float* ca = c + (size_t)a_ * D;
+                float dd = 0.f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float t = xv[k] - ca[k];
+                    dd = fmaf(t, t, dd);
+                }
+                u = sqrtf(dd) * (1.f + 1e-5f) + eta;
+                scan = !(u * (1.f + 1e-5f) < m);
+            }
+            if (!scan) {
+                rho_out[row] = a_;
+                a.hub[row] = u;
+                for (int gi = 0; gi < hg; ++gi) lr[gi] = fmaxf(0.f, (lr[gi] - s_gd[gi]) * (1.f - 2e-7f));
+            }
+        }
+        if (scan) {
+            const unsigned pos = atomicAdd(s_hqn, 1u);
+            if (pos >= cap) {               // full: this row again in the next round
+                *cursor = q;
+                return nq;
+            }
+            s_hq[pos] = (uint32_t)row;
+            nq += 1;
+        }
+    }
+    *cursor = n_g;
+    return nq;
+}
+
 // The work of block `bid` of a pass launched with `nblk` blocks.  The standalone kernel calls it
 // with (blockIdx.x, gridDim.x); the batched kernel with a work item's (block, blocks of that
 // instance), so that every instance gets exactly the arithmetic of its own launch.
@@ -488,7 +602,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     // the solver's TRIAL / REVERT update sums in 64-bit fixed point (see layout)
     const bool fx = F32 && D <= FX_MAX_D && do_bins && a.acc != nullptr &&
                     (a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
-    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0, fx);
+    const Layout L = layout(F32, D, DP, K, a.Kpad, do_bins, a.ham ? a.hq_cap : 0, fx, a.ham ? a.hg : 0);
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     T* s_stage = reinterpret_cast<T*>(smem + L.stage);
     T* s_bS = reinterpret_cast<T*>(smem + L.bS);
@@ -591,11 +705,20 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     float* s_hm = reinterpret_cast<float*>(smem + L.hm);
     unsigned int* s_hqn = reinterpret_cast<unsigned int*>(s_hm + 8);
     uint32_t* s_hq = reinterpret_cast<uint32_t*>(smem + L.hq);
+    const int HG = ham ? a.hg : 0;               // groups of the group bounds (0: Hamerly)
+    float* s_gd = reinterpret_cast<float*>(smem + L.gd);
+    int* s_gperm = reinterpret_cast<int*>(smem + L.gperm);
+    int* s_goff = reinterpret_cast<int*>(smem + L.goff);
     if constexpr (F32) {
         if (ham) {
             for (int jj = tid; jj < K; jj += blockDim.x) {
                 s_hdr[jj] = a.hdr[jj];
                 s_hs[jj] = a.hs[jj];
+            }
+            if (HG > 0) {
+                for (int jj = tid; jj < K; jj += blockDim.x) s_gperm[jj] = a.hperm[jj];
+                for (int gi = tid; gi <= HG; gi += blockDim.x) s_goff[gi] = a.hgoff[gi];
+                for (int gi = tid; gi < HG; gi += blockDim.x) s_gd[gi] = a.hgd[gi];
             }
             if (tid == 0) *s_hqn = 0u;
             __syncthreads();
@@ -740,6 +863,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     rho_out[row] = idx;
                     a.hub[row] = u;
                     a.hlb[row] = fmaxf(l, 0.f);
+                    if (HG > 0)
+                        group_lower_bounds<D>(xr, idx, reinterpret_cast<const float*>(s_c), s_gperm, s_goff, HG, h_eta,
+                                              a.hlbg + (size_t)row * HG);
                 };
                 // phase A: rows whose bounds show the assigned centroid is still the unique nearest by
                 // a relative margin of 1e-5 (far beyond the FP32 rounding of either score form, so a
@@ -747,7 +873,15 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 const bool force = a.mode == MODE_INIT;
                 const int32_t* rho_last = a.mode == MODE_TRIAL ? rho_prev : rho_out;
                 constexpr int HB = 4;             // rows per thread whose loads are issued together
-                for (int64_t q0 = 0; q0 < n_g; q0 += HB) {
+                // group bounds run phases A and B in rounds, so that a queue of hq_cap rows serves any
+                // number of scans (the INIT pass scans every row); Hamerly runs one round
+                int64_t gcur = 0;
+                for (int rnd = 0;; ++rnd) {
+                if (HG > 0)
+                    nscan += group_classify<D>(a, X, g, TT, n_g, &gcur, (unsigned)a.hq_cap, force, rho_last, rho_out,
+                                               s_hdr, s_gd, reinterpret_cast<const float*>(s_c), h_eta, HG, s_hq,
+                                               s_hqn, (flags & F_CHECK) != 0, &bad, &xabs);
+                for (int64_t q0 = 0; HG == 0 && q0 < n_g; q0 += HB) {
                     int al[HB];
                     float ub[HB], lb[HB], xv[HB][D];
 #pragma unroll
@@ -796,7 +930,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 }
                 __syncthreads();
                 // phase B: full scans of the queued rows, R per thread while whole rounds remain
-                const int nq = (int)*s_hqn;
+                const int nq = (int)min(*s_hqn, (unsigned)a.hq_cap);
                 const int round = (int)blockDim.x * R;
                 int qb = 0;
                 for (; qb + round <= nq; qb += round) {
@@ -865,6 +999,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     if (valid) ham_store(row, idx, second, xn, bnd, need);
                 }
                 __syncthreads();
+                if (HG == 0 || !__syncthreads_or(gcur < n_g)) break;
+                if (tid == 0) *s_hqn = 0u;
+                __syncthreads();
+                }
                 // phase C: the rest of the pass in the same per-thread row order as without bounds,
                 // so the update's sums come out bitwise the same
                 for (int64_t q0 = 0; q0 < n_max; q0 += HB) {

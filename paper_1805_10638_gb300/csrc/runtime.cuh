@@ -47,10 +47,11 @@ struct Plan {
     bool dense;
     int dpad, nbk, rpb, max_chunks;
     size_t smem;
-    // Hamerly bounds of the FP32 solver passes
+    // Hamerly bounds of the FP32 solver passes (hg > 0: group bounds in place of the single lower bound)
     bool ham;
     int hq_cap;
-    size_t hub, hlb, hlast, hprep;
+    int hg;
+    size_t hub, hlb, hlast, hprep, hlbg, hgd, hperm, hgoff;
 };
 
 constexpr int DENSE_RPB = 4096;   // rows per block of the dense update's histogram and scatter
@@ -234,16 +235,29 @@ bool hamerly_mode()
     return !(v && v[0] == '0');
 }
 
+// KM_BOUNDS in the environment picks the bounds of standalone FP32 solves: "group" = group bounds at
+// any K, "hamerly" = Hamerly's bounds at any K (half distances however costly); unset = the rule below.
+int bounds_env()
+{
+    const char* v = getenv("KM_BOUNDS");
+    if (v && !strcmp(v, "group")) return 2;
+    if (v && !strcmp(v, "hamerly")) return 1;
+    return 0;
+}
+
 // Solver plans (ham_ok) on the FP32 low-d path use Hamerly bounds when the centroids' pairwise
 // half-distances stay cheap (K*K*d <= 2^21: the TRIAL pass's last block recomputes them alone when
-// a REVERT pass follows) and the row queue fits in shared memory.
+// a REVERT pass follows) and the row queue fits in shared memory.  Above that, plans that allow it
+// (group_ok: the standalone solver, whose prologue forms the groups) use group bounds: one lower
+// bound per group of nearby centroids (hg = K/64 groups, 2..16), no half distances.
 kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
-                        Plan& P, bool bins = true, bool ham_ok = false)
+                        Plan& P, bool bins = true, bool ham_ok = false, bool group_ok = false)
 {
     P.dense = false;
     P.ham = false;
     P.hq_cap = 0;
-    P.hub = P.hlb = P.hlast = P.hprep = 0;
+    P.hg = 0;
+    P.hub = P.hlb = P.hlast = P.hprep = P.hlbg = P.hgd = P.hperm = P.hgoff = 0;
     P.dpad = P.nbk = P.rpb = P.max_chunks = 0;
     if (prec == KM_BF16_F32 && d > 16) return make_plan_dense(ctx, N, d, K, m_max, host_copies, P);
     if (d > 16) return fail(ctx, KM_EINVAL, "d > 16 needs KM_BF16_F32 (the tensor-core path)");
@@ -255,14 +269,20 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     if (P.smem > (size_t)LOWD_SMEM_MAX)
         return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
     P.nb = pass_blocks(ctx, N, P.smem, prec, d);
-    if (ham_ok && f32 && bins && hamerly_mode() && (int64_t)K * K * d <= (int64_t(1) << 21) &&
-        N < (int64_t(1) << 31)) {
+    const int benv = group_ok ? bounds_env() : 0;
+    const bool cheap_half = (int64_t)K * K * d <= (int64_t(1) << 21) || benv == 1;
+    const bool group = group_ok && K >= 2 && K <= 16384 && benv != 1 && (!cheap_half || benv == 2);
+    if (ham_ok && f32 && bins && hamerly_mode() && (cheap_half || group) && N < (int64_t(1) << 31)) {
         const int64_t per = (int64_t)P.nb * LOWD_THREADS;
-        const int cap = (int)((N + per - 1) / per) * LOWD_THREADS;
-        const size_t sm = pass_lowd_smem(prec, d, K, P.Kpad, bins, cap);
+        const int hg = group ? std::min(std::max(K / 64, 2), std::min(16, K)) : 0;
+        // Hamerly: every row of a block fits the queue; group bounds: at most 2048 per round
+        int cap = (int)((N + per - 1) / per) * LOWD_THREADS;
+        if (hg > 0) cap = std::min(cap, 2048);
+        const size_t sm = pass_lowd_smem(prec, d, K, P.Kpad, bins, cap, hg);
         if (sm <= (size_t)LOWD_SMEM_MAX) {
             P.ham = true;
             P.hq_cap = cap;
+            P.hg = hg;
             P.smem = sm;
         }
     }
@@ -277,6 +297,12 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
         P.hlb = take((size_t)N * 4);
         P.hlast = take(n * 4);
         P.hprep = take(((size_t)2 * P.Kpad + 8) * 4);
+        if (P.hg > 0) {
+            P.hlbg = take((size_t)N * P.hg * 4);
+            P.hgd = take((size_t)P.hg * 4);
+            P.hperm = take((size_t)K * 4);
+            P.hgoff = take((size_t)(P.hg + 1) * 4);
+        }
     }
     P.st = take(sizeof(SolveState));
     P.rhoA = take((size_t)N * 4);
@@ -580,6 +606,11 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     pa.hdr = P.ham ? at<float>(base, P.hprep) : nullptr;
     pa.hs = P.ham ? pa.hdr + P.Kpad : nullptr;
     pa.hm = P.ham ? pa.hdr + 2 * P.Kpad : nullptr;
+    pa.hg = P.hg;
+    pa.hlbg = P.hg ? at<float>(base, P.hlbg) : nullptr;
+    pa.hgd = P.hg ? at<float>(base, P.hgd) : nullptr;
+    pa.hperm = P.hg ? at<int>(base, P.hperm) : nullptr;
+    pa.hgoff = P.hg ? at<int>(base, P.hgoff) : nullptr;
     pa.acc = P.acc ? at<long long>(base, P.acc) : nullptr;
     pa.accC = P.acc ? reinterpret_cast<int32_t*>(pa.acc + (size_t)K * d) : nullptr;
 
@@ -710,6 +741,7 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
     PassArgs a = L.pa;
     a.mode = MODE_INIT;
     a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHECK;
+    if (e == cudaSuccess && a.hg > 0) e = launch_groups(L.ma.C64, L.K, L.d, a.hg, a.hperm, a.hgoff, s);
     if (e == cudaSuccess && a.ham) e = launch_hprep(a, MODE_INIT, s);
     if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
     FinArgs f = L.fa;

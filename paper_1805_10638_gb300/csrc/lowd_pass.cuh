@@ -873,15 +873,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 const bool force = a.mode == MODE_INIT;
                 const int32_t* rho_last = a.mode == MODE_TRIAL ? rho_prev : rho_out;
                 constexpr int HB = 4;             // rows per thread whose loads are issued together
-                // group bounds run phases A and B in rounds, so that a queue of hq_cap rows serves any
-                // number of scans (the INIT pass scans every row); Hamerly runs one round
+                // phases A and B run in rounds, so that a queue of hq_cap rows serves any number of
+                // scans (the INIT pass scans every row): a thread whose row finds the queue full stops
+                // there and resumes after the queue is drained
                 int64_t gcur = 0;
                 for (int rnd = 0;; ++rnd) {
                 if (HG > 0)
                     nscan += group_classify<D>(a, X, g, TT, n_g, &gcur, (unsigned)a.hq_cap, force, rho_last, rho_out,
                                                s_hdr, s_gd, reinterpret_cast<const float*>(s_c), h_eta, HG, s_hq,
                                                s_hqn, (flags & F_CHECK) != 0, &bad, &xabs);
-                for (int64_t q0 = 0; HG == 0 && q0 < n_g; q0 += HB) {
+                bool hfull = false;              // Hamerly: the queue filled up, resume at gcur next round
+                for (int64_t q0 = gcur; HG == 0 && !hfull && q0 < n_g; q0 += HB) {
                     int al[HB];
                     float ub[HB], lb[HB], xv[HB][D];
 #pragma unroll
@@ -923,11 +925,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                             }
                         }
                         if (scan) {
-                            s_hq[atomicAdd(s_hqn, 1u)] = (uint32_t)row;
+                            const unsigned pos = atomicAdd(s_hqn, 1u);
+                            if (pos >= (unsigned)a.hq_cap) {
+                                gcur = q0 + r;
+                                hfull = true;
+                                break;
+                            }
+                            s_hq[pos] = (uint32_t)row;
                             nscan += 1;
                         }
                     }
                 }
+                if (HG == 0 && !hfull) gcur = n_g;
                 __syncthreads();
                 // phase B: full scans of the queued rows, R per thread while whole rounds remain
                 const int nq = (int)min(*s_hqn, (unsigned)a.hq_cap);
@@ -999,7 +1008,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     if (valid) ham_store(row, idx, second, xn, bnd, need);
                 }
                 __syncthreads();
-                if (HG == 0 || !__syncthreads_or(gcur < n_g)) break;
+                if (!__syncthreads_or(gcur < n_g)) break;
                 if (tid == 0) *s_hqn = 0u;
                 __syncthreads();
                 }

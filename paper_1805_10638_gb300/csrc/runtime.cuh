@@ -246,10 +246,12 @@ int bounds_env()
 }
 
 // Solver plans (ham_ok) on the FP32 low-d path use Hamerly bounds when the centroids' pairwise
-// half-distances stay cheap (K*K*d <= 2^21: the TRIAL pass's last block recomputes them alone when
-// a REVERT pass follows) and the row queue fits in shared memory.  Above that, plans that allow it
+// half-distances stay affordable (K*K*d <= 2^23: the TRIAL pass's last block recomputes them alone
+// when a REVERT pass follows) and the pass fits in shared memory.  Above that, plans that allow it
 // (group_ok: the standalone solver, whose prologue forms the groups) use group bounds: one lower
-// bound per group of nearby centroids (hg = K/64 groups, 2..16), no half distances.
+// bound per group of nearby centroids (hg = K/64 groups, 2..16), no half distances.  (The low-d
+// pass's own shared memory caps K near 1,100 at d = 3, so group bounds are mostly reached through
+// KM_BOUNDS=group; measured on GB300 they cost more per pass than the single Hamerly bound.)
 kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int m_max, bool host_copies,
                         Plan& P, bool bins = true, bool ham_ok = false, bool group_ok = false)
 {
@@ -270,14 +272,15 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
         return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
     P.nb = pass_blocks(ctx, N, P.smem, prec, d);
     const int benv = group_ok ? bounds_env() : 0;
-    const bool cheap_half = (int64_t)K * K * d <= (int64_t(1) << 21) || benv == 1;
+    const bool cheap_half = (int64_t)K * K * d <= (int64_t(1) << 23) || benv == 1;
     const bool group = group_ok && K >= 2 && K <= 16384 && benv != 1 && (!cheap_half || benv == 2);
     if (ham_ok && f32 && bins && hamerly_mode() && (cheap_half || group) && N < (int64_t(1) << 31)) {
         const int64_t per = (int64_t)P.nb * LOWD_THREADS;
         const int hg = group ? std::min(std::max(K / 64, 2), std::min(16, K)) : 0;
-        // Hamerly: every row of a block fits the queue; group bounds: at most 2048 per round
+        // rows a block queues for full scans per round (the passes drain the queue in rounds)
         int cap = (int)((N + per - 1) / per) * LOWD_THREADS;
-        if (hg > 0) cap = std::min(cap, 2048);
+        cap = std::min(cap, hg > 0 ? 2048 : 4096);
+        if (const char* v = getenv("KM_HQ_CAP")) cap = std::max(1, std::min(cap, atoi(v)));   // smaller rounds
         const size_t sm = pass_lowd_smem(prec, d, K, P.Kpad, bins, cap, hg);
         if (sm <= (size_t)LOWD_SMEM_MAX) {
             P.ham = true;

@@ -1,6 +1,6 @@
 """Group bounds (Yinyang-style) on the FP32 low-d solver passes.
 
-Where Hamerly's half distances would cost O(K^2 d) per pass (K*K*d > 2^21) the standalone solver
+Where Hamerly's half distances would cost O(K^2 d) per pass (K*K*d > 2^23) the standalone solver
 keeps, per sample, one lower bound per group of nearby centroids (groups fixed from C^0 by Morton
 order) and lowers each by its group's largest drift; KM_BOUNDS=group forces them at any K.  A row
 keeps its label without a scan only when the bounds prove the assigned centroid the unique nearest
@@ -38,12 +38,12 @@ def _same(a, b):
 @pytest.mark.parametrize("shape", [(150_000, 3, 1024, 0), (100_000, 2, 1500, 1), (60_000, 4, 800, 2)])
 @pytest.mark.parametrize("lloyd", [False, True])
 def test_group_bounds_at_large_k_change_nothing(shape, lloyd, monkeypatch):
-    """K*K*d > 2^21: group bounds on by default, bitwise the brute-force solve, fewer rows scanned."""
+    """Group bounds at K = 800..1500: bitwise the brute-force solve, fewer rows scanned."""
     need_gpu()
     N, d, K, seed = shape
-    assert K * K * d > 2 ** 21
     X, C0 = datagen.batched_instance(N, d, K, 5100 + seed, dtype=np.float32)
     p = dict(lloyd_only=1) if lloyd else dict(m_max=10)
+    monkeypatch.setenv("KM_BOUNDS", "group")
     with_b = _solve(X, C0, **p)
     monkeypatch.setenv("KM_HAMERLY", "0")
     without = _solve(X, C0, **p)
@@ -67,6 +67,7 @@ def test_group_bounds_on_anisotropic_mixture(monkeypatch):
     """The low-d workload's mixture at K = 1024 (Dirichlet weights, anisotropic clusters)."""
     need_gpu()
     X, C0 = datagen.lowd_2m(seed=3, N=400_000, K=1024)
+    monkeypatch.setenv("KM_BOUNDS", "group")
     with_b = _solve(X, C0, m_max=10)
     monkeypatch.setenv("KM_HAMERLY", "0")
     without = _solve(X, C0, m_max=10)

@@ -68,3 +68,26 @@ def test_bounds_batched_equal(monkeypatch):
         assert torch.equal(a[0][i], b[0][i]) and torch.equal(a[1][i], b[1][i])
         for f in FIELDS:
             assert a[2][i][f] == b[2][i][f], f
+
+
+@pytest.mark.parametrize("shape", [(300_000, 3, 1024, 7), (200_000, 2, 1500, 8), (120_000, 4, 700, 9)])
+@pytest.mark.parametrize("cap", [None, "300"])
+def test_bounds_at_large_k_in_queue_rounds(shape, cap, monkeypatch):
+    """K*K*d up to 2^23: Hamerly's queue holds at most 4,096 rows per block (KM_HQ_CAP lowers it), so
+    the INIT pass and any pass that queues more rows than that drains the queue in rounds; a thread
+    that finds it full resumes at the same row.  Bitwise the brute-force solve, for both methods."""
+    need_gpu()
+    N, d, K, seed = shape
+    X, C0 = datagen.batched_instance(N, d, K, 4100 + seed, dtype=np.float32)
+    if cap:
+        monkeypatch.setenv("KM_HQ_CAP", cap)
+    for p in (dict(lloyd_only=1), dict(m_max=10)):
+        with_b = _solve(X, C0, **p)
+        monkeypatch.setenv("KM_HAMERLY", "0")
+        without = _solve(X, C0, **p)
+        monkeypatch.delenv("KM_HAMERLY")
+        assert with_b[0].tobytes() == without[0].tobytes()
+        assert np.array_equal(with_b[1], without[1])
+        for f in FIELDS:
+            assert with_b[2][f] == without[2][f], f
+        assert with_b[2]["scanned_rows"] < 0.7 * without[2]["scanned_rows"], (with_b[2], without[2])

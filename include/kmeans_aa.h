@@ -172,12 +172,15 @@ kmeans_status kmeans_assign(kmeans_ctx* ctx, const kmeans_data* X, const void* C
  *   rho     [N] int32 in [0, K)
  *   C_prev  [K, d] (element type of X): centroids for empty clusters
  *   C_out   [K, d] output (element type of X); may alias C_prev
- *   counts  [K] int64 output (cluster sizes N_j); may be NULL */
+ *   counts  [K] int64 output (cluster sizes N_j); may be NULL
+ * For d > 16 (FP32 X: the sort-based update of the tensor-core path) X must be 16-byte aligned and
+ * d a multiple of 8, d <= 128 (else KM_EINVAL). */
 kmeans_status kmeans_update(kmeans_ctx* ctx, const kmeans_data* X, const int32_t* rho,
                             int32_t K, const void* C_prev, void* C_out, int64_t* counts);
 
 /* Energy, Eq. 1, with a given assignment: *E = sum_i ||x_i - c_{rho_i}||^2 (direct form per
- * row in X's precision, accumulated in FP64 in a fixed order).  E is a device double. */
+ * row in X's precision, accumulated in FP64 in a fixed order).  E is a device double.
+ * For d > 16 X must be 16-byte aligned and d a multiple of 8, d <= 128 (else KM_EINVAL). */
 kmeans_status kmeans_energy(kmeans_ctx* ctx, const kmeans_data* X, const void* C, int32_t K,
                             const int32_t* rho, double* E);
 

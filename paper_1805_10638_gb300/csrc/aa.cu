@@ -353,11 +353,11 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
 
     // ---- phase 1/2: sums over the partial blocks in a fixed order.  With split == 1 (E >= the
     // block size) each element goes straight to s_tot; s_part holds only 2*FIN_THREADS entries.
-    // FP32 solver passes after the first (d <= FX_MAX_D) sum in 64-bit fixed point (scale
-    // 2^st->fx_s) straight into the totals acc / accC: read once, converted to FP64 once, and
+    // FP32 solver passes after the first (d <= FX_MAX_D), and every dense update, sum in 64-bit
+    // fixed point (scale 2^fx_s) straight into the totals acc / accC: read once, converted to FP64 once, and
     // cleared for the next pass.  Counts of the other passes are summed as integers.
-    const bool fxp = a.part_fx && a.acc && solver && a.mode != MODE_INIT;
-    const int fxs = fxp ? st->fx_s : 0;
+    const bool fxp = a.acc && (a.part_fx == 2 || (a.part_fx == 1 && solver && a.mode != MODE_INIT));
+    const int fxs = fxp ? (a.fxs_ptr ? *a.fxs_ptr : st->fx_s) : 0;
     long long* s_ipart = reinterpret_cast<long long*>(s_part);
     const size_t Kd = (size_t)K * d;
     // (e, sp): element e, blocks sp, sp + split, ...; split == 1 writes s_tot directly.  Consecutive

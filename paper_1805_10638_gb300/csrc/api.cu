@@ -140,6 +140,7 @@ kmeans_status dense_energy_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
                                 const int32_t* rho, double* E)
 {
     kmeans_status s;
+    if ((uintptr_t)X->X & 15u) return fail(ctx, KM_EINVAL, "the energy with d > 16 needs X 16-byte aligned");
     DenseArgs a = dense_args(arena_base(ctx), P, reinterpret_cast<const float*>(X->X), X->N, X->d, K);
     a.mode = MODE_STANDALONE;
     a.out_E = E;
@@ -154,10 +155,12 @@ kmeans_status dense_update_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
                                 const void* C_prev, void* C_out, int64_t* counts)
 {
     kmeans_status s;
+    if ((uintptr_t)X->X & 15u) return fail(ctx, KM_EINVAL, "the update with d > 16 needs X 16-byte aligned");
     DenseArgs a = dense_args(arena_base(ctx), P, reinterpret_cast<const float*>(X->X), X->N, X->d, K);
     a.mode = MODE_STANDALONE;
     a.rho_out = const_cast<int32_t*>(rho);     // read-only here: the labels of the update
     KM_CUDA(cudaMemsetAsync(a.counter, 0, 256, ctx->stream));
+    KM_CUDA(cudaMemsetAsync(a.acc, 0, (size_t)K * X->d * 8 + (size_t)K * 4, ctx->stream));
     if ((s = dense_pack_user(ctx, P, C_prev, X->d, K)) != KM_OK) return s;
     KM_CUDA(launch_dense_update(a, P.nbk, P.max_chunks, ctx->stream));
     FinArgs f;
@@ -166,9 +169,10 @@ kmeans_status dense_update_call(kmeans_ctx* ctx, const Plan& P, const kmeans_dat
     f.K = K;
     f.d = X->d;
     f.nb = 1;
-    f.part_f64 = 1;
-    f.pS = a.S;
-    f.pCnt = a.counts;
+    f.part_fx = 2;                             // the chain's fixed-point totals
+    f.acc = a.acc;
+    f.accC = a.accC;
+    f.fxs_ptr = reinterpret_cast<const int*>(a.counter + 3);
     f.KB = P.KB;
     f.C_ref = C_prev;
     f.C_out = C_out;

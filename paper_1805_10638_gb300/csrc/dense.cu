@@ -172,6 +172,33 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
+// Compensated FP32 summation (TwoSum): hi + lo carries the running sum with an error of order
+// u^2 of the summed magnitudes, so that a fixed-order sum of many FP32 values needs one FP64
+// conversion at the end instead of one per term (FP64 issue is scarce on this part).
+struct f2sum {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_add(f2sum& s, float v)
+{
+    const float t = s.hi + v;
+    const float bb = t - s.hi;
+    s.lo += (s.hi - (t - bb)) + (v - bb);
+    s.hi = t;
+}
+
+// Butterfly reduction of a compensated sum over the warp (every lane gets the same result).
+__device__ __forceinline__ f2sum warp_sum_f2(f2sum s)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(FULL, s.hi, o), ol = __shfl_xor_sync(FULL, s.lo, o);
+        s.lo += ol;
+        two_sum_add(s, oh);
+    }
+    return s;
+}
+
 // Solver-mode gate shared by every kernel of a pass: returns the centroid set (0 = C^t,
 // 1 = C_AU) or -1 if this launch has nothing to do.
 __device__ __forceinline__ int pass_set(const SolveState* st, int mode)
@@ -486,32 +513,35 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 
 // ------------------------------------------------------------------ near-tie rescoring
 // FP32 direct form sum_k (x_k - c_jk)^2 over all K for the queued near-tie rows, tiled like a GEMM.
-// A work item is (64 queued rows, one of RF_SPLIT ranges of the centroids); a block stages the rows
+// A work item is (64 queued rows, one of `split` ranges of the centroids; split is chosen on the
+// device from the queue length so that the items fill the grid); a block stages the rows
 // and then 64-centroid tiles in shared memory, dimension-major (stride RF_S floats), and thread
 // (ty, tx) scores rows 4ty..4ty+3 against centroids 4tx..4tx+3 of each tile (16 FP32 accumulators
 // in packed pairs, two 16-byte shared loads and 16 fma.rn.f32x2 per dimension).  A thread visits its centroids in ascending order; the
 // 16 threads of a row group and the ranges are combined lexicographically on (distance, index):
 // shuffles within the block, then atomicMin on the 64-bit key (distance bits, index) per row, which
 // orders like the pair because the distances are non-negative.  k_rescore_write stores the labels.
-constexpr int RF_ROWS = 64, RF_CT = 64, RF_SPLIT = 4, RF_S = RF_CT + 4;
+constexpr int RF_ROWS = 64, RF_CT = 64, RF_S = RF_CT + 4;
 __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
     const unsigned nfull = a.qcount[0];
-    const unsigned ntile = (nfull + RF_ROWS - 1) / RF_ROWS, nitems = ntile * RF_SPLIT;
+    const int d = a.d, K = a.K;
+    const int kt = (K + RF_CT - 1) / RF_CT;                    // centroid tiles
+    const unsigned ntile = (nfull + RF_ROWS - 1) / RF_ROWS;
+    const unsigned split = ntile ? max(1u, min((unsigned)kt, gridDim.x / ntile)) : 1u;
+    const unsigned nitems = ntile * split;
     if (blockIdx.x >= nitems) return;
     extern __shared__ float sm_f[];
-    const int d = a.d, K = a.K;
     float* xs = sm_f;                  // [d][RF_S]: rows of the item
     float* cs = sm_f + d * RF_S;       // [d][RF_S]: centroids of the tile
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const float* X = a.X;
     const float* C = a.c32[set];
-    const int kt = (K + RF_CT - 1) / RF_CT;                    // centroid tiles
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const unsigned rt = item / RF_SPLIT, sp = item % RF_SPLIT;
-        const int tlo = (int)((long long)kt * sp / RF_SPLIT), thi = (int)((long long)kt * (sp + 1) / RF_SPLIT);
+        const unsigned rt = item / split, sp = item % split;
+        const int tlo = (int)((long long)kt * sp / split), thi = (int)((long long)kt * (sp + 1) / split);
         const unsigned q0 = rt * RF_ROWS;
         __syncthreads();
         for (int i = t; i < RF_ROWS * (d / 4); i += blockDim.x) {   // row r, four dimensions from 4*k4
@@ -716,38 +746,56 @@ __global__ void __launch_bounds__(256) k_dcount(DenseArgs a)
     }
 }
 
-// 2. One block: per cluster, the exclusive scan over blocks (warp per cluster), then the scan
-//    over clusters of the totals (offsets) and of the chunk counts.
-__global__ void __launch_bounds__(1024) k_dscan(DenseArgs a, int nbk)
+// 2. Per cluster (one warp): the exclusive scan over the blocks of its per-block counts, in place,
+//    and its total.  The last block to finish scans the cluster totals into the clusters' offsets
+//    in perm and in the chunk list, and fills the chunk -> cluster table.
+__global__ void __launch_bounds__(256) k_dscan(DenseArgs a, int nbk)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, K = a.K;
-    for (int j = w; j < K; j += 32) {
+    const int j = blockIdx.x * 8 + w;
+    if (j < K) {
         int* h = a.hist + (size_t)j * nbk;
         int run = 0;
-        for (int b0 = 0; b0 < nbk; b0 += 32) {
-            const int v = b0 + lane < nbk ? h[b0 + lane] : 0;
-            int incl = v;
+        for (int b0 = 0; b0 < nbk; b0 += 128) {
+            int v[4];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += t;
+            for (int u = 0; u < 4; ++u) {
+                const int b = b0 + 32 * u + lane;
+                v[u] = b < nbk ? h[b] : 0;
             }
-            if (b0 + lane < nbk) h[b0 + lane] = run + incl - v;
-            run += __shfl_sync(FULL, incl, 31);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int incl = v[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int b = b0 + 32 * u + lane;
+                if (b < nbk) h[b] = run + incl - v[u];
+                run += __shfl_sync(FULL, incl, 31);
+            }
         }
         if (lane == 0) a.counts[j] = run;
     }
+    __shared__ unsigned int s_last;
+    __shared__ int s_tot[8], s_ch[8];
+    __threadfence();
     __syncthreads();
-    // scan over clusters: offsets of each cluster in perm, and of its chunks
-    __shared__ int s_tot[32], s_ch[32];
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.counter + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // thread t owns the clusters [t*per, (t+1)*per): its totals, a block scan, then its offsets
+    const int per = (K + 255) / 256;
+    const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
     int tot = 0, chn = 0;
-    const int per = (K + 1023) / 1024;
-    const int j0 = threadIdx.x * per;
-    for (int j = j0; j < min(K, j0 + per); ++j) {
-        tot += a.counts[j];
-        chn += (a.counts[j] + SEG - 1) / SEG;
+    for (int jj = j0; jj < j1; ++jj) {
+        const int c = __ldcg(a.counts + jj);
+        tot += c;
+        chn += (c + SEG - 1) / SEG;
     }
     int it = tot, ic = chn;
 #pragma unroll
@@ -763,33 +811,25 @@ __global__ void __launch_bounds__(1024) k_dscan(DenseArgs a, int nbk)
         s_ch[w] = ic;
     }
     __syncthreads();
-    if (w == 0) {
-        int v1 = s_tot[lane], v2 = s_ch[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t1 = __shfl_up_sync(FULL, v1, o), t2 = __shfl_up_sync(FULL, v2, o);
-            if (lane >= o) {
-                v1 += t1;
-                v2 += t2;
-            }
-        }
-        s_tot[lane] = v1 - s_tot[lane];
-        s_ch[lane] = v2 - s_ch[lane];
+    int off = it - tot, coff = ic - chn;
+    for (int ww = 0; ww < w; ++ww) {
+        off += s_tot[ww];
+        coff += s_ch[ww];
     }
-    __syncthreads();
-    int off = s_tot[w] + it - tot, coff = s_ch[w] + ic - chn;
-    for (int j = j0; j < min(K, j0 + per); ++j) {
-        a.off[j] = off;
-        a.choff[j] = coff;
-        const int nc = (a.counts[j] + SEG - 1) / SEG;
-        for (int c = 0; c < nc; ++c) a.chunk_cluster[coff + c] = j;
-        off += a.counts[j];
+    for (int jj = j0; jj < j1; ++jj) {
+        const int c = __ldcg(a.counts + jj);
+        const int nc = (c + SEG - 1) / SEG;
+        a.off[jj] = off;
+        a.choff[jj] = coff;
+        for (int q = 0; q < nc; ++q) a.chunk_cluster[coff + q] = jj;
+        off += c;
         coff += nc;
     }
-    if (threadIdx.x == 1023) {
+    if (threadIdx.x == 255) {
         a.off[K] = off;
         *a.nchunks = coff;
     }
+    if (threadIdx.x == 0) a.counter[1] = 0u;      // ready for the next pass
 }
 
 // 3. Stable scatter of row indices by label: one warp per block of rows, rows in order.
@@ -821,68 +861,130 @@ __global__ void __launch_bounds__(32) k_dscatter(DenseArgs a)
     }
 }
 
-// 4. Residual sums per chunk of <= 64 rows of one cluster (rows in perm order), FP32 within the
-//    chunk, and the chunk's energy.  One warp per chunk, lanes over d.
+// 4. Residual sums per chunk of <= SEG rows of one cluster (rows in perm order), FP32 within the
+//    chunk, the energy of the block's eight chunks (in chunk order) and the largest |partial|.  One
+//    warp per chunk: lane l holds the dimensions 4l..4l+3 (d <= 128, d % 8 == 0; 16-byte loads),
+//    the chunk's row indices sit two per lane, and rows are loaded eight at a time so that eight
+//    loads per lane are in flight; the sums still run over the rows in order.
+constexpr int SEG_UNROLL = 8;
 __global__ void __launch_bounds__(256) k_dsegsum(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
-    const int lane = threadIdx.x & 31, d = a.d;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = a.d;
     const int nch = *a.nchunks;
-    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (c >= nch) return;
-    const int j = a.chunk_cluster[c];
-    const int lc = c - a.choff[j];
-    const int p0 = a.off[j] + lc * SEG;
-    const int p1 = min(a.off[j + 1], p0 + SEG);
-    const float* X = a.X;
-    float cj[4], acc[4];
-    const bool use64 = a.mode == MODE_EPI;   // G^t was not packed when the loop stopped at max_iter
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int k = lane + 32 * u;
-        cj[u] = k < d ? (use64 ? (float)a.c64[1][(size_t)j * d + k] : a.c32[set][(size_t)j * d + k]) : 0.f;
-        acc[u] = 0.f;
-    }
-    float e = 0.f;
-    for (int p = p0; p < p1; ++p) {
-        const int64_t row = a.perm[p];
-        const float* x = X + row * d;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = lane + 32 * u;
-            if (k < d) {
-                const float r = x[k] - cj[u];
-                acc[u] += r;
-                e = fmaf(r, r, e);
+    const int c = blockIdx.x * 8 + w;
+    __shared__ double s_e[8];
+    __shared__ float s_m[8];
+    double ew = 0.0;
+    float am = 0.f;
+    if (c < nch) {
+        const int j = a.chunk_cluster[c];
+        const int lc = c - a.choff[j];
+        const int p0 = a.off[j] + lc * SEG;
+        const int n = min(a.off[j + 1] - p0, SEG);
+        const bool act = 4 * lane < d;
+        const bool use64 = a.mode == MODE_EPI;   // G^t was not packed when the loop stopped at max_iter
+        float4 cj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+            const size_t o = (size_t)j * d + 4 * lane;
+            if (use64) {
+                const double* c64 = a.c64[1] + o;
+                cj = make_float4((float)c64[0], (float)c64[1], (float)c64[2], (float)c64[3]);
+            } else {
+                cj = *reinterpret_cast<const float4*>(a.c32[set] + o);
             }
         }
-    }
+        const int ra = lane < n ? a.perm[p0 + lane] : 0;
+        const int rb = lane + 32 < n ? a.perm[p0 + 32 + lane] : 0;
+        const float* X = a.X + 4 * lane;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float e = 0.f;
+        for (int p = 0; p < n; p += SEG_UNROLL) {
+            float4 xv[SEG_UNROLL];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int k = lane + 32 * u;
-        if (k < d) a.part[(size_t)c * d + k] = acc[u];
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                const int q = p + u;
+                const int r1 = __shfl_sync(FULL, ra, q & 31), r2 = __shfl_sync(FULL, rb, q & 31);
+                const int64_t row = q < 32 ? r1 : r2;
+                xv[u] = (act && q < n) ? __ldg(reinterpret_cast<const float4*>(X + row * d))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                if (p + u < n) {
+                    const float r0 = xv[u].x - cj.x, r1 = xv[u].y - cj.y, r2 = xv[u].z - cj.z, r3 = xv[u].w - cj.w;
+                    acc.x += r0;
+                    acc.y += r1;
+                    acc.z += r2;
+                    acc.w += r3;
+                    e = fmaf(r0, r0, e);
+                    e = fmaf(r1, r1, e);
+                    e = fmaf(r2, r2, e);
+                    e = fmaf(r3, r3, e);
+                }
+            }
+        }
+        if (act) *reinterpret_cast<float4*>(a.part + (size_t)c * d + 4 * lane) = acc;
+        const f2sum es = warp_sum_f2(f2sum{e, 0.f});
+        ew = (double)es.hi + (double)es.lo;
+        float m = fmaxf(fmaxf(fabsf(acc.x), fabsf(acc.y)), fmaxf(fabsf(acc.z), fabsf(acc.w)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+        am = m;
     }
-    const double ew = warp_sum((double)e);
-    if (lane == 0) a.pe[c] = ew;
+    if (lane == 0) {
+        s_e[w] = ew;
+        s_m[w] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        float m = 0.f;
+        for (int i = 0; i < 8; ++i) {
+            t += s_e[i];
+            m = fmaxf(m, s_m[i]);
+        }
+        a.pe[blockIdx.x] = t;
+        if (m > 0.f) atomicMax(a.counter + 2, __float_as_uint(m));   // non-negative: ordered as integers
+    }
 }
 
-// 5. Per cluster: fixed-order FP64 sum of its chunk partials -> S [K][d]; the last block sums the
-//    energy and the change count in a fixed order and runs the controller.
-__global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
+// 5. Per chunk (one warp, lane l on dimensions 4l..4l+3, the blocks of k_dsegsum): the chunk's
+//    FP32 partial in 64-bit fixed point, added into its cluster's totals acc [K][d] with integer
+//    atomics (exact, so the totals do not depend on the order: a cluster of any size costs one
+//    atomic per chunk and dimension, and the work stays balanced over chunks); the cluster sizes
+//    into accC.  The scale 2^fxs keeps every total, at most nch * max|partial|, below 2^61.  The last
+//    block sums the energy partials of the k_dsegsum blocks and the change counts in a fixed order,
+//    publishes fxs for k_fin and runs the controller.
+__global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
 {
     SolveState* st = a.st;
     const int set = pass_set(st, a.mode);
     if (set < 0) return;
     const int lane = threadIdx.x & 31, d = a.d, K = a.K;
-    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (j < K) {
-        const int c0 = a.choff[j], nc = (a.counts[j] + SEG - 1) / SEG;
-        for (int k = lane; k < d; k += 32) {
-            double s = 0.0;
-            for (int c = c0; c < c0 + nc; ++c) s += (double)a.part[(size_t)(c)*d + k];
-            a.S[(size_t)j * d + k] = s;
+    const int nch = *a.nchunks;
+    const float amax = __uint_as_float(__ldcg(a.counter + 2));
+    int fxs = 0;
+    if (amax > 0.f) {
+        fxs = 60 - ilogb((double)amax * (double)nch);
+        fxs = fxs > 100 ? 100 : (fxs < -100 ? -100 : fxs);
+    }
+    if (a.mode != MODE_EPI) {                      // the epilogue pass needs only the energy
+        const float fxf = ldexpf(1.f, fxs);
+        const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+        if (c < nch && 4 * lane < d) {
+            const int j = a.chunk_cluster[c];
+            const float4 v = *reinterpret_cast<const float4*>(a.part + (size_t)c * d + 4 * lane);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.acc) + (size_t)j * d + 4 * lane;
+            const long long q[4] = {__float2ll_rn(v.x * fxf), __float2ll_rn(v.y * fxf), __float2ll_rn(v.z * fxf),
+                                    __float2ll_rn(v.w * fxf)};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (q[t] != 0) atomicAdd(dst + t, (unsigned long long)q[t]);
         }
+        for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj < K; jj += gridDim.x * blockDim.x)
+            a.accC[jj] = a.counts[jj];
     }
     __threadfence();
     __syncthreads();
@@ -893,9 +995,17 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int nch = *a.nchunks;
     double E = 0.0;
-    for (int c = threadIdx.x; c < nch; c += blockDim.x) E += __ldcg(a.pe + c);
+    {
+        double e4[4] = {0.0, 0.0, 0.0, 0.0};
+        int b = threadIdx.x;
+        for (; b + 3 * 256 < nseg; b += 4 * 256) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e4[u] += __ldcg(a.pe + b + 256 * u);
+        }
+        for (; b < nseg; b += 256) e4[0] += __ldcg(a.pe + b);
+        E = (e4[0] + e4[1]) + (e4[2] + e4[3]);
+    }
     long long ch = 0;
     for (int b = threadIdx.x; b < nbk; b += blockDim.x) ch += __ldcg(a.pnch + b);
     E = warp_sum(E);
@@ -905,56 +1015,90 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk)
         s_rl[threadIdx.x >> 5] = ch;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    E = 0.0;
-    ch = 0;
-    for (int w = 0; w < 8; ++w) {
-        E += s_red[w];
-        ch += s_rl[w];
+    if (threadIdx.x == 0) {
+        E = 0.0;
+        ch = 0;
+        for (int w = 0; w < 8; ++w) {
+            E += s_red[w];
+            ch += s_rl[w];
+        }
+        *a.counter = 0u;
+        a.counter[2] = 0u;                         // max |partial| of the next pass
+        a.counter[3] = (unsigned int)fxs;          // read by k_fin
+        if (a.mode == MODE_STANDALONE) {
+            if (a.out_E) *a.out_E = E;
+            if (a.out_nch) *a.out_nch = ch;
+        } else {
+            if (a.mode != MODE_EPI) st->rescored += a.qcount[0];
+            if (a.mode == MODE_EPI) {
+                st->E_final = E;
+            } else if (a.mode == MODE_INIT) {
+                st->passes += 1;
+                st->E_trial = E;
+            } else {
+                if (a.mode == MODE_TRIAL)
+                    controller_trial(st, E, ch, a.thr, a.lloyd_only, a.fixed_m, a.eps1, a.eps2, a.m_max, a.max_iter);
+                else
+                    controller_revert(st, E, ch, a.thr);
+                if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+            }
+        }
     }
-    *a.counter = 0u;
-    if (a.mode == MODE_STANDALONE) {
-        if (a.out_E) *a.out_E = E;
-        if (a.out_nch) *a.out_nch = ch;
-        return;
-    }
-    if (a.mode != MODE_EPI) st->rescored += a.qcount[0];
-    if (a.mode == MODE_EPI) {
-        st->E_final = E;
-    } else if (a.mode == MODE_INIT) {
-        st->passes += 1;
-        st->E_trial = E;
-    } else {
-        if (a.mode == MODE_TRIAL)
-            controller_trial(st, E, ch, a.thr, a.lloyd_only, a.fixed_m, a.eps1, a.eps2, a.m_max, a.max_iter);
-        else
-            controller_revert(st, E, ch, a.thr);
-        if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    // the safeguard fired: the REVERT pass adds into cleared totals
+    if (a.mode == MODE_TRIAL) {
+        __syncthreads();
+        if (st->revert && !st->done) {
+            const size_t n = (size_t)K * d;
+            for (size_t i = threadIdx.x; i < n; i += blockDim.x) a.acc[i] = 0;
+            for (int jj = threadIdx.x; jj < K; jj += blockDim.x) a.accC[jj] = 0;
+        }
     }
 }
 
 // Standalone calls: per-row direct-form FP32 squared distance to the assigned centroid (optional
 // output), change count and energy; block partials summed in a fixed order by the last block.
+// One warp per row, lane l on dimensions 4l..4l+3 (d <= 128, d % 8 == 0; 16-byte loads), four rows
+// in flight; the row's lane partials are summed by a fixed butterfly.
 __global__ void __launch_bounds__(256) k_drow(DenseArgs a, const int32_t* rho_in, float* dmin, double* pe,
                                               long long* pn)
 {
-    const int d = a.d;
-    const float* C = a.c32[0];
+    const int d = a.d, lane = threadIdx.x & 31;
+    const bool act = 4 * lane < d;
+    const float* C = a.c32[0] + 4 * lane;
+    const float* X = a.X + 4 * lane;
     double e = 0.0;
     long long nch = 0;
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += T) {
-        const int j = rho_in[i];
-        const float* x = a.X + i * d;
-        const float* c = C + (size_t)j * d;
-        float acc = 0.f;
-        for (int k = 0; k < d; ++k) {
-            const float t = x[k] - c[k];
-            acc = fmaf(t, t, acc);
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t i0 = w0; i0 < a.N; i0 += 4 * W) {
+        int j[4];
+        float4 xv[4], cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * W;
+            j[u] = i < a.N ? rho_in[i] : 0;
+            j[u] = (j[u] >= 0 && j[u] < a.K) ? j[u] : 0;      // out-of-range labels read centroid 0
+            xv[u] = (act && i < a.N) ? __ldg(reinterpret_cast<const float4*>(X + i * d)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (dmin) dmin[i] = acc;
-        e += acc;
-        if (a.rho_prev) nch += a.rho_prev[i] != j;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            cv[u] = act ? *reinterpret_cast<const float4*>(C + (size_t)j[u] * d) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * W;
+            const float t0 = xv[u].x - cv[u].x, t1 = xv[u].y - cv[u].y, t2 = xv[u].z - cv[u].z, t3 = xv[u].w - cv[u].w;
+            float acc = fmaf(t0, t0, 0.f);
+            acc = fmaf(t1, t1, acc);
+            acc = fmaf(t2, t2, acc);
+            acc = fmaf(t3, t3, acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (i < a.N && lane == 0) {
+                if (dmin) dmin[i] = acc;
+                e += (double)acc;
+                if (a.rho_prev) nch += a.rho_prev[i] != j[u];
+            }
+        }
     }
     __shared__ double s_e[8];
     __shared__ long long s_n[8];
@@ -1065,7 +1209,7 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
     cudaError_t e;
     k_dcount<<<nbk, 256, (size_t)a.K * 4, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_dscan<<<1, 1024, 0, s>>>(a, nbk);
+    k_dscan<<<(a.K + 7) / 8, 256, 0, s>>>(a, nbk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t sm_sc = (size_t)(a.K + a.rows_per_block) * 4;
     if (sm_sc > 48 * 1024) {
@@ -1074,11 +1218,12 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
     }
     k_dscatter<<<nbk, 32, sm_sc, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_dsegsum<<<(max_chunks + 7) / 8, 256, 0, s>>>(a);
+    const int nseg = (max_chunks + 7) / 8;
+    k_dsegsum<<<nseg, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    k_dsegfin<<<(a.K + 7) / 8, 256, 0, s>>>(a, nbk);
+    // the last-block counters counter[0..1] and the slots counter[2..3] are zero at the start of
+    // every call and reset by the kernels that use them
+    k_dsegfin<<<nseg, 256, 0, s>>>(a, nbk, nseg);
     return cudaGetLastError();
 }
 

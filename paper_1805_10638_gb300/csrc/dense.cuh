@@ -50,10 +50,12 @@ struct DenseArgs {
     int* nchunks;
     int* perm;                // [N]
     float* part;              // [max_chunks][d]
-    double* pe;               // [max_chunks]
+    double* pe;               // [max_chunks / 8]: energy of each k_dsegsum block
     long long* pnch;          // [nbk]
-    double* S;                // [K][d] residual sums (FP64)
-    unsigned int* counter;
+    long long* acc;           // [K][d] int64 fixed-point residual sums (scale 2^counter[3]), read and
+    int32_t* accC;            // [K]    cleared by k_fin; cluster sizes
+    unsigned int* counter;    // [0]: k_dsegfin's last block, [1]: k_dscan's, [2]: max |chunk partial|
+                              // (FP32 bits), [3]: the pass's fixed-point scale exponent
     double* out_E;
     long long* out_nch;
     // controller

@@ -185,9 +185,11 @@ struct FinArgs {
     const void* pS;       // [nb][K][d]
     const int32_t* pCnt;  // [nb][K]
     int KB;               // centroids per block
-    int part_fx;          // FP32 solver: TRIAL / REVERT sums are int64 fixed point (scale st->fx_s)
+    int part_fx;          // 1: FP32 low-d solver, TRIAL / REVERT sums are int64 fixed point (scale
+                          // st->fx_s); 2: every pass's sums are (dense update chain, scale *fxs_ptr)
     long long* acc;       //   ... accumulated by the pass in acc [K][d] and accC [K] (read, then zeroed)
     int32_t* accC;
+    const int* fxs_ptr;   // part_fx == 2: the scale exponent written by the pass
     // standalone update
     const void* C_ref;    // reference centroids of the residuals (C_prev), element type T
     void* C_out;          // [K][d] element type T

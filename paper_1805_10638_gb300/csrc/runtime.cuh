@@ -41,7 +41,7 @@ struct Plan {
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
     size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, xnorm, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
-        part, pe, pnch, S, rowe, rown;
+        part, pe, pnch, rowe, rown;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
     bool dense;
@@ -54,7 +54,7 @@ struct Plan {
     size_t hub, hlb, hlast, hprep, hlbg, hgd, hperm, hgoff;
 };
 
-constexpr int DENSE_RPB = 4096;   // rows per block of the dense update's histogram and scatter
+constexpr int DENSE_RPB = 1024;   // rows per block of the dense update's histogram and scatter (at least K)
 constexpr int DENSE_SEG = 64;     // rows per segment-sum chunk
 
 }  // namespace
@@ -151,8 +151,9 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.DP = 0;
     P.nb = 1;
     P.nfin = fin_blocks(K, d, &P.KB);
-    P.rpb = DENSE_RPB;
-    P.nbk = (int)((N + DENSE_RPB - 1) / DENSE_RPB);
+    // the per-block histograms hold K * nbk counts: rows per block >= K keeps them within N entries
+    P.rpb = std::max(DENSE_RPB, (K + 255) / 256 * 256);
+    P.nbk = (int)((N + P.rpb - 1) / P.rpb);
     P.max_chunks = (int)((N + DENSE_SEG - 1) / DENSE_SEG) + K;
     P.smem = 0;
     const size_t n = (size_t)K * d;
@@ -195,13 +196,12 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.part = take((size_t)P.max_chunks * d * 4);
     P.pe = take((size_t)P.max_chunks * 8);
     P.pnch = take((size_t)P.nbk * 8);
-    P.S = take(n * 8);
+    P.acc = take(n * 8 + (size_t)K * 4);     // fixed-point residual sums + counts of a pass
     P.rowe = take(4096 * 8);
     P.rown = take(4096 * 8);
-    P.pS = P.S;
+    P.pS = 0;
     P.pCnt = P.counts;
     P.pE = P.pNch = P.pResc = P.pScan = P.pBad = 0;
-    P.acc = 0;
     P.pDots = take((size_t)P.nfin * DOTS * 8);
     P.info = take(256);
     if (host_copies) {
@@ -523,7 +523,8 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.part = at<float>(base, P.part);
     a.pe = at<double>(base, P.pe);
     a.pnch = at<long long>(base, P.pnch);
-    a.S = at<double>(base, P.S);
+    a.acc = at<long long>(base, P.acc);
+    a.accC = reinterpret_cast<int32_t*>(a.acc + (size_t)K * d);
     a.counter = at<unsigned int>(base, P.counter);
     a.st = at<SolveState>(base, P.st);
     return a;
@@ -672,8 +673,8 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     L.nsm = nsm;
     L.X32 = reinterpret_cast<const float*>(X->X);
     if (P.dense) {
-        fa.part_f64 = 1;                 // S: FP64 residual sums per cluster, one "partial block"
-        fa.part_fx = 0;
+        fa.part_fx = 2;                  // the update chain's int64 fixed-point totals
+        fa.fxs_ptr = reinterpret_cast<const int*>(at<unsigned int>(base, P.counter) + 3);
         fa.fuse_mix = 0;
         fa.fp32_path = 0;
         ma.fp32_path = 0;                // the mix only writes C; the BF16 packing is separate
@@ -715,6 +716,8 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
 {
     if (L.P.dense) {
         cudaError_t e = cudaMemsetAsync(L.pa.counter, 0, 256, s);
+        if (e == cudaSuccess)      // the fixed-point totals the update chain adds into
+            e = cudaMemsetAsync(L.da.acc, 0, (size_t)L.K * L.d * 8 + (size_t)L.K * 4, s);
         if (e == cudaSuccess)
             e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
                             nullptr, L.st, L.p.m_init, L.m_max, s, 0);

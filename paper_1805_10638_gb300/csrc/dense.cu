@@ -512,101 +512,202 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ near-tie rescoring
-// FP32 direct form sum_k (x_k - c_jk)^2 over all K for the queued near-tie rows, tiled like a GEMM.
-// A work item is (64 queued rows, one of `split` ranges of the centroids; split is chosen on the
-// device from the queue length so that the items fill the grid); a block stages the rows
-// and then 64-centroid tiles in shared memory, dimension-major (stride RF_S floats), and thread
-// (ty, tx) scores rows 4ty..4ty+3 against centroids 4tx..4tx+3 of each tile (16 FP32 accumulators
-// in packed pairs, two 16-byte shared loads and 16 fma.rn.f32x2 per dimension).  A thread visits its centroids in ascending order; the
-// 16 threads of a row group and the ranges are combined lexicographically on (distance, index):
+// The label of a queued near-tie row is the lexicographic minimum of (D_j, j) over all K, D_j the
+// FP32 direct form sum_k (x_k - c_jk)^2 (each difference rounded once, fma accumulation in k order).
+// Work items are (64 queued rows, one of `split` ranges of the centroids; split is chosen on the
+// device from the queue length so that the items fill the grid).  A block copies the rows and then
+// 64-centroid tiles into shared memory with cp.async (16-byte pieces of whole rows, row-major with a
+// stride of d + 4 floats; the next tile is in flight while the current one is scored); thread
+// (ty, tx) takes rows 4ty..4ty+3 against centroids tx, tx+16, tx+32, tx+48 of each tile.
+//   Filter: the expanded FP32 score s~_j = ||c_j||^2 - 2 x.c_j (one fma per dimension, packed in
+//   pairs: half the arithmetic of the direct form) is within B = 2u max||c||^2 + 2(g_d + u)(1 + g_d)
+//   |x| max||c|| of s_j = d_j - ||x||^2 (g_d = d u / (1 - d u)), and D_j within (d + 2) u d_j of d_j.
+//   With m the smallest s~ seen so far for the row (over the 16 threads of the row group), a
+//   centroid whose D_j could be the minimum (or tie it) has s~_j <= m + M, M = 1.01 (2B +
+//   2 (d + 3) u (||x||^2 + m + B)) (m only falls, so testing against the current m never drops one).
+//   Only those get the direct form, so the result is bitwise the direct-form scan over all K.
+// The 16 threads of a row group and the ranges are combined lexicographically on (distance, index):
 // shuffles within the block, then atomicMin on the 64-bit key (distance bits, index) per row, which
 // orders like the pair because the distances are non-negative.  k_rescore_write stores the labels.
-constexpr int RF_ROWS = 64, RF_CT = 64, RF_S = RF_CT + 4;
+constexpr int RF_ROWS = 64, RF_CT = 64;
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NG>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NG) : "memory");
+}
+
+size_t rescore_smem(int d) { return (size_t)3 * RF_ROWS * (d + 4) * sizeof(float); }
+
 __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
     if (set < 0) return;
     const unsigned nfull = a.qcount[0];
-    const int d = a.d, K = a.K;
+    const int d = a.d, K = a.K, S = d + 4, d4 = d / 4;
     const int kt = (K + RF_CT - 1) / RF_CT;                    // centroid tiles
     const unsigned ntile = (nfull + RF_ROWS - 1) / RF_ROWS;
     const unsigned split = ntile ? max(1u, min((unsigned)kt, gridDim.x / ntile)) : 1u;
     const unsigned nitems = ntile * split;
     if (blockIdx.x >= nitems) return;
-    extern __shared__ float sm_f[];
-    float* xs = sm_f;                  // [d][RF_S]: rows of the item
-    float* cs = sm_f + d * RF_S;       // [d][RF_S]: centroids of the tile
-    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    extern __shared__ __align__(16) float sm_f[];
+    float* xs = sm_f;                               // [64][S]: rows of the item
+    float* const csb = sm_f + RF_ROWS * S;          // [2][64][S]: centroid tiles (double buffer)
+    __shared__ float s_cn[2][RF_CT];                // ||c||^2 of the tiles (+inf past K)
+    __shared__ float s_red[8];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15, lane = t & 31;
     const float* X = a.X;
     const float* C = a.c32[set];
+    const float* CN = a.cn[set];
+    // max ||c||^2 over the centroids (the filter's error bound)
+    float cm2 = 0.f;
+    for (int j = t; j < K; j += blockDim.x) cm2 = fmaxf(cm2, CN[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cm2 = fmaxf(cm2, __shfl_xor_sync(FULL, cm2, o));
+    if (lane == 0) s_red[t >> 5] = cm2;
+    __syncthreads();
+    cm2 = 0.f;
+    for (int w = 0; w < 8; ++w) cm2 = fmaxf(cm2, s_red[w]);
+    const float u = 5.9604644775390625e-8f;
+    const float gd = (float)d * u / (1.f - (float)d * u);
+    const float cmax = sqrtf(cm2) * (1.f + 2.f * u);
+    auto stage_tile = [&](int ct, int buf) {
+        const int c0 = ct * RF_CT;
+        float* cs = csb + buf * RF_CT * S;
+        for (int i = t; i < RF_CT * d4; i += blockDim.x) {
+            const int jl = i / d4, k4 = i - jl * d4;
+            const bool ok = c0 + jl < K;
+            cp_async16(cs + jl * S + 4 * k4, C + (size_t)(ok ? c0 + jl : 0) * d + 4 * k4, ok);
+        }
+        if (t < RF_CT) s_cn[buf][t] = c0 + t < K ? CN[c0 + t] : __int_as_float(0x7f800000);
+    };
     for (unsigned item = blockIdx.x; item < nitems; item += gridDim.x) {
         const unsigned rt = item / split, sp = item % split;
         const int tlo = (int)((long long)kt * sp / split), thi = (int)((long long)kt * (sp + 1) / split);
         const unsigned q0 = rt * RF_ROWS;
         __syncthreads();
-        for (int i = t; i < RF_ROWS * (d / 4); i += blockDim.x) {   // row r, four dimensions from 4*k4
-            const int r = i % RF_ROWS, k4 = i / RF_ROWS;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q0 + r < nfull) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)a.queue[q0 + r] * d) + k4);
-            xs[(4 * k4) * RF_S + r] = v.x;
-            xs[(4 * k4 + 1) * RF_S + r] = v.y;
-            xs[(4 * k4 + 2) * RF_S + r] = v.z;
-            xs[(4 * k4 + 3) * RF_S + r] = v.w;
+        for (int i = t; i < RF_ROWS * d4; i += blockDim.x) {
+            const int r = i / d4, k4 = i - r * d4;
+            const bool ok = q0 + r < nfull;
+            cp_async16(xs + r * S + 4 * k4, X + (ok ? (int64_t)a.queue[q0 + r] : 0) * d + 4 * k4, ok);
         }
-        float bd[4];
+        stage_tile(tlo, 0);
+        cp_async_commit();
+        float xn2[4], bnd[4], m[4], bd[4];
         int bj[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            bd[u] = __int_as_float(0x7f800000);
-            bj[u] = K;
-        }
         for (int ct = tlo; ct < thi; ++ct) {
-            const int c0 = ct * RF_CT;
-            __syncthreads();
-            for (int i = t; i < RF_CT * (d / 4); i += blockDim.x) {
-                const int jl = i % RF_CT, k4 = i / RF_CT;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (c0 + jl < K) v = __ldg(reinterpret_cast<const float4*>(C + (size_t)(c0 + jl) * d) + k4);
-                cs[(4 * k4) * RF_S + jl] = v.x;
-                cs[(4 * k4 + 1) * RF_S + jl] = v.y;
-                cs[(4 * k4 + 2) * RF_S + jl] = v.z;
-                cs[(4 * k4 + 3) * RF_S + jl] = v.w;
+            const int buf = (ct - tlo) & 1;
+            if (ct + 1 < thi) {
+                stage_tile(ct + 1, buf ^ 1);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
-            // packed pairs of centroids: t = fma(c, -1, x) is x - c rounded once, then acc += t * t,
-            // the same per-component arithmetic as the scalar direct form
-            float2 acc[4][2];
+            if (ct == tlo) {
+                // ||x||^2 of the thread's rows (an upper bound: the FP32 sum times 1 + 2 d u) and the
+                // per-row filter constants
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float sq = 0.f;
+                    const float* xr = xs + (4 * ty + r) * S;
+                    for (int k = tx; k < d; k += 16) sq = fmaf(xr[k], xr[k], sq);
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
+                    xn2[r] = sq * (1.f + 2.f * (float)d * u);
+                    bnd[r] = 2.f * u * cm2 + 2.f * (gd + u) * (1.f + gd) * sqrtf(xn2[r]) * cmax;
+                    m[r] = __int_as_float(0x7f800000);
+                    bd[r] = __int_as_float(0x7f800000);
+                    bj[r] = K;
+                }
+            }
+            const float* cs = csb + buf * RF_CT * S;
+            const int c0 = ct * RF_CT;
+            // expanded dot products x.c: rows 4ty+r, centroids tx+16c, dimensions in steps of four;
+            // each accumulator pair holds the even and the odd dimensions (operands straight from the
+            // 16-byte loads, no register moves), added at the end
+            float2 acc[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
-            const float2 m1 = make_float2(-1.f, -1.f);
-#pragma unroll 4
-            for (int k = 0; k < d; ++k) {
-                const float4 xv = *reinterpret_cast<const float4*>(xs + k * RF_S + 4 * ty);
-                const float4 cv = *reinterpret_cast<const float4*>(cs + k * RF_S + 4 * tx);
-                const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
-                const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
+                for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+            for (int k4 = 0; k4 < d4; ++k4) {
+                float4 xv[4], cv[4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float2 x2 = make_float2(xr[r], xr[r]);
-                    const float2 t0 = __ffma2_rn(c01, m1, x2), t1 = __ffma2_rn(c23, m1, x2);
-                    acc[r][0] = __ffma2_rn(t0, t0, acc[r][0]);
-                    acc[r][1] = __ffma2_rn(t1, t1, acc[r][1]);
-                }
-            }
+                for (int r = 0; r < 4; ++r) xv[r] = *reinterpret_cast<const float4*>(xs + (4 * ty + r) * S + 4 * k4);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = c0 + 4 * tx + c;
+                for (int c = 0; c < 4; ++c) cv[c] = *reinterpret_cast<const float4*>(cs + (tx + 16 * c) * S + 4 * k4);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float v = (c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x;
-                    if (j < K && v < bd[r]) {
-                        bd[r] = v;
-                        bj[r] = j;
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        acc[r][c] = __ffma2_rn(make_float2(xv[r].x, xv[r].y), make_float2(cv[c].x, cv[c].y), acc[r][c]);
+                        acc[r][c] = __ffma2_rn(make_float2(xv[r].z, xv[r].w), make_float2(cv[c].z, cv[c].w), acc[r][c]);
                     }
+            }
+            // scores, the rows' running minima, then the candidates
+            unsigned cand = 0u;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                float sc[4];
+                float tm = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float dot = acc[r][c].x + acc[r][c].y;
+                    sc[c] = fmaf(-2.f, dot, s_cn[buf][tx + 16 * c]);
+                    tm = fminf(tm, sc[c]);
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) tm = fminf(tm, __shfl_xor_sync(FULL, tm, o));
+                m[r] = fminf(m[r], tm);
+                const float M = 1.01f * (2.f * bnd[r] + 2.f * (float)(d + 3) * u * fmaxf(0.f, xn2[r] + m[r] + bnd[r]));
+                const float lim = m[r] + M;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c0 + tx + 16 * c < K && sc[c] <= lim) cand |= 1u << (4 * r + c);
+            }
+            // direct form for the candidates, one per lane per round
+            while (__any_sync(FULL, cand != 0u)) {
+                int r = 0, c = 0;
+                const bool has = cand != 0u;
+                if (has) {
+                    const int bb = __ffs(cand) - 1;
+                    cand &= cand - 1u;
+                    r = bb >> 2;
+                    c = bb & 3;
+                }
+                if (has) {
+                    const float* xr = xs + (4 * ty + r) * S;
+                    const float* cr = cs + (tx + 16 * c) * S;
+                    float dd = 0.f;
+                    for (int k4 = 0; k4 < d4; ++k4) {          // dimensions in order, four per load
+                        const float4 xv = *reinterpret_cast<const float4*>(xr + 4 * k4);
+                        const float4 cv = *reinterpret_cast<const float4*>(cr + 4 * k4);
+                        const float t0 = xv.x - cv.x, t1 = xv.y - cv.y, t2 = xv.z - cv.z, t3 = xv.w - cv.w;
+                        dd = fmaf(t0, t0, dd);
+                        dd = fmaf(t1, t1, dd);
+                        dd = fmaf(t2, t2, dd);
+                        dd = fmaf(t3, t3, dd);
+                    }
+                    const int j = c0 + tx + 16 * c;
+#pragma unroll
+                    for (int rr = 0; rr < 4; ++rr)
+                        if (rr == r && (dd < bd[rr] || (dd == bd[rr] && j < bj[rr]))) {
+                            bd[rr] = dd;
+                            bj[rr] = j;
+                        }
                 }
             }
+            __syncthreads();      // the next iteration copies into this buffer
         }
         // the 16 threads of a row group are lanes 0-15 or 16-31 of one warp
 #pragma unroll
@@ -1186,12 +1287,12 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_dense_assign<<<grid, DTHREADS, smem, s>>>(maps, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t sm_full = (size_t)2 * a.d * RF_S * sizeof(float);
+    const size_t sm_full = rescore_smem(a.d);
     if (sm_full > 48 * 1024) {
         e = cudaFuncSetAttribute(k_rescore_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_full);
         if (e != cudaSuccess) return e;
     }
-    k_rescore_full<<<nsm * 3, 256, sm_full, s>>>(a);
+    k_rescore_full<<<nsm * 2, 256, sm_full, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rescore_write<<<nsm, 256, 0, s>>>(a);
     return cudaGetLastError();

@@ -874,21 +874,23 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                 const int32_t* rho_last = a.mode == MODE_TRIAL ? rho_prev : rho_out;
                 constexpr int HB = 4;             // rows per thread whose loads are issued together
                 // phases A and B run in rounds, so that a queue of hq_cap rows serves any number of
-                // scans (the INIT pass scans every row): a thread whose row finds the queue full stops
-                // there and resumes after the queue is drained
+                // scans (the INIT pass scans every row).  Hamerly: a round classifies at most
+                // hq_cap / blockDim.x rows per thread, so the queue cannot overflow; group bounds: a
+                // thread whose row finds the queue full stops there and resumes after it is drained
                 int64_t gcur = 0;
+                const int64_t rpr = (int64_t)(a.hq_cap / (int)blockDim.x);
                 for (int rnd = 0;; ++rnd) {
                 if (HG > 0)
                     nscan += group_classify<D>(a, X, g, TT, n_g, &gcur, (unsigned)a.hq_cap, force, rho_last, rho_out,
                                                s_hdr, s_gd, reinterpret_cast<const float*>(s_c), h_eta, HG, s_hq,
                                                s_hqn, (flags & F_CHECK) != 0, &bad, &xabs);
-                bool hfull = false;              // Hamerly: the queue filled up, resume at gcur next round
-                for (int64_t q0 = gcur; HG == 0 && !hfull && q0 < n_g; q0 += HB) {
+                const int64_t qend = min(n_g, gcur + rpr);
+                for (int64_t q0 = gcur; HG == 0 && q0 < qend; q0 += HB) {
                     int al[HB];
                     float ub[HB], lb[HB], xv[HB][D];
 #pragma unroll
                     for (int r = 0; r < HB; ++r) {
-                        const bool v = q0 + r < n_g;
+                        const bool v = q0 + r < qend;
                         const int64_t row = g + (v ? q0 + r : q0) * TT;
                         al[r] = force ? 0 : rho_last[row];
                         ub[r] = force ? 0.f : a.hub[row];
@@ -898,7 +900,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     }
 #pragma unroll
                     for (int r = 0; r < HB; ++r) {
-                        if (q0 + r >= n_g) break;
+                        if (q0 + r >= qend) break;
                         const int64_t row = g + (q0 + r) * TT;
                         check(xv[r]);
                         bool scan = force;
@@ -925,18 +927,12 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                             }
                         }
                         if (scan) {
-                            const unsigned pos = atomicAdd(s_hqn, 1u);
-                            if (pos >= (unsigned)a.hq_cap) {
-                                gcur = q0 + r;
-                                hfull = true;
-                                break;
-                            }
-                            s_hq[pos] = (uint32_t)row;
+                            s_hq[atomicAdd(s_hqn, 1u)] = (uint32_t)row;
                             nscan += 1;
                         }
                     }
                 }
-                if (HG == 0 && !hfull) gcur = n_g;
+                if (HG == 0) gcur = qend;
                 __syncthreads();
                 // phase B: full scans of the queued rows, R per thread while whole rounds remain
                 const int nq = (int)min(*s_hqn, (unsigned)a.hq_cap);

@@ -277,10 +277,21 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     if (ham_ok && f32 && bins && hamerly_mode() && (cheap_half || group) && N < (int64_t(1) << 31)) {
         const int64_t per = (int64_t)P.nb * LOWD_THREADS;
         const int hg = group ? std::min(std::max(K / 64, 2), std::min(16, K)) : 0;
-        // rows a block queues for full scans per round (the passes drain the queue in rounds)
+        // rows a block queues for full scans per round (the passes drain the queue in rounds): all of
+        // a block's rows when they fit in shared memory, else as many whole rows per thread as fit
+        // (group bounds: at most 2048); Hamerly's rounds take hq_cap / LOWD_THREADS rows per thread
         int cap = (int)((N + per - 1) / per) * LOWD_THREADS;
-        cap = std::min(cap, hg > 0 ? 2048 : 4096);
-        if (const char* v = getenv("KM_HQ_CAP")) cap = std::max(1, std::min(cap, atoi(v)));   // smaller rounds
+        if (hg > 0) cap = std::min(cap, 2048);
+        if (const char* v = getenv("KM_HQ_CAP"))            // smaller rounds (tests)
+            cap = std::max(LOWD_THREADS, std::min(cap, atoi(v) / LOWD_THREADS * LOWD_THREADS));
+        // the queue may not lower the blocks per SM the grid was sized for
+        const int per_sm = std::max(1, (int)std::min<int64_t>(4, (P.nb + ctx->nsm - 1) / ctx->nsm));
+        const size_t budget = std::min<size_t>(LOWD_SMEM_MAX, (SM_SMEM - 1024) / per_sm - 1024);
+        const size_t sm1 = pass_lowd_smem(prec, d, K, P.Kpad, bins, LOWD_THREADS, hg);   // one row per thread
+        if (sm1 <= budget) {
+            const int fit = LOWD_THREADS + (int)((budget - sm1) / 4) / LOWD_THREADS * LOWD_THREADS;
+            cap = std::min(cap, fit);
+        }
         const size_t sm = pass_lowd_smem(prec, d, K, P.Kpad, bins, cap, hg);
         if (sm <= (size_t)LOWD_SMEM_MAX) {
             P.ham = true;

@@ -129,12 +129,14 @@ def measured_peaks():
         return {}
 
 
-def load_data(wl):
-    """(X f32, X_bf16 uint16 or None) of the workload."""
+def load_data(wl, rows=0):
+    """(X f32, X_bf16 uint16 or None) of the workload (rows > 0: that many rows of the same
+    generator, a smaller case for profiler captures)."""
+    kw = dict(N=rows) if rows > 0 else {}
     if wl["workload"] == "dense_1m":
-        X, Xb, _ = datagen.dense_1m(seed=wl["data_seed"])
+        X, Xb, _ = datagen.dense_1m(seed=wl["data_seed"], **kw)
         return X, Xb
-    X, _ = datagen.lowd_2m(seed=wl["data_seed"])
+    X, _ = datagen.lowd_2m(seed=wl["data_seed"], **kw)
     return X, None
 
 
@@ -678,9 +680,11 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.rows > 0:        # a profiler case, not a bench line: the JSON says so
+        wl.update(N=args.rows, note="smaller case of the same generator for profiler captures; not a bench value")
     dense = wl["workload"] == "dense_1m"
-    X, Xb = load_data(wl)
+    X, Xb = load_data(wl, args.rows)
     N, d, K = X.shape[0], X.shape[1], wl["K"]
     nsteps = args.steps + args.warmup
     C0s = [datagen.init_centroids(X, K, 1000 + s) for s in range(nsteps)]
@@ -891,6 +895,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-lanes", type=int, default=4)
     ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="profiler captures only: N rows of the workload's generator instead of its full size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-solves", type=int, default=2)
     args = ap.parse_args()

@@ -390,18 +390,23 @@ def batched_data(n_inst: int, seed: int = 0):
 
 
 def parse_tuning(desc: str):
-    """Per low-d group of kmeans_batch_describe: (d, lane ops of one pass, chosen grid, its time in us)."""
+    """Per low-d group of kmeans_batch_describe: (d, lane ops of one pass, chosen grid, its time in
+    us).  A group reads "... v0(occ 3) 152:528.4us ... v1(occ 3) ... -> variant V grid G"."""
     out = []
     for part in desc.split(";"):
         part = part.strip()
-        if " d=" not in part or "-> grid" not in part:
+        if " d=" not in part or "-> variant" not in part:
             continue
         d = int(part.split(" d=")[1].split()[0])
         ops = float(part.split(" ops=")[1].split()[0])
-        grid = int(part.split("-> grid")[1].split()[0])
+        tail = part.split("-> variant")[1].split()
+        var, grid = int(tail[0]), int(tail[2])
         t = None
-        for tok in part.split():
-            if tok.startswith(f"{grid}:") and tok.endswith("us"):
+        cur = None
+        for tok in part.split("->")[0].split():
+            if tok.startswith("v") and "(occ" in tok:
+                cur = int(tok[1:tok.index("(")])
+            elif cur == var and tok.startswith(f"{grid}:") and tok.endswith("us"):
                 t = float(tok[len(str(grid)) + 1:-2])
         out.append((d, ops, grid, t))
     return out

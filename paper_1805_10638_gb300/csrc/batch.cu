@@ -43,6 +43,7 @@ struct BGroup {
     std::vector<int2> items;
     size_t items_off;
     int grid;
+    int variant;     // launch shape of the pass kernel: 0 = default rows per thread, 1 = half (FP32)
 };
 
 struct BLayout {
@@ -97,7 +98,8 @@ cudaError_t batch_passes(const Batch& B, int mode, int flags, cudaStream_t s)
         if (e != cudaSuccess) return e;
     }
     for (const BGroup& g : B.groups) {
-        cudaError_t e = launch_pass_lowd_batch(pass_launch(B, g, mode, flags, false), g.prec, g.d, g.grid, g.smem, s);
+        cudaError_t e =
+            launch_pass_lowd_batch(pass_launch(B, g, mode, flags, false), g.prec, g.d, g.grid, g.smem, s, g.variant);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -168,55 +170,70 @@ cudaError_t batch_epilogue(const Batch& B, cudaStream_t s)
     return e;
 }
 
-// Launch shapes of the pass kernels.  After running the batch's prologue (so every instance holds
-// its packed C^1), time for each group a pass that does the loop pass's work (assignment, bins,
-// energy) at every persistent grid from 1 block per SM up to the occupancy limit, and with one
-// block per work item; keep the fastest.  The timed passes write only scratch (the second
-// assignment buffer and the block partials); the solve's own prologue runs again afterwards.
+// Launch shapes of the pass kernels, per group of instances (precision, d, shared-memory class),
+// picked by timing on the batch's own data.  After running the batch's prologue (so every instance
+// holds its packed C^1), time for each group a pass that does the loop pass's work (assignment,
+// bins, energy) for every candidate: the kernel variant (FP32: the default rows per thread of the
+// scan or half of them, which trades registers and instruction-level parallelism against
+// occupancy) x the persistent grid (1 block per SM up to the variant's occupancy limit, and one
+// block per work item); keep the fastest.  Every candidate gives bitwise the same results (same
+// rows per block, same order of the per-thread sums), so the choice only changes the speed.  The
+// timed passes write only scratch (the second assignment buffer and the block partials); the
+// solve's own prologue runs again afterwards.
 kmeans_status tune_batch(kmeans_ctx* ctx, Batch& B, std::string& desc)
 {
     const char* env = getenv("KM_TUNE");
     const bool tune = !(env && env[0] == '0') && B.n_lowd > 0;
     char buf[256];
-    std::vector<int> occs;
     for (BGroup& g : B.groups) {
-        occs.push_back(pass_lowd_batch_occupancy(g.prec, g.d, g.smem));
-        g.grid = std::min((int)g.items.size(), ctx->nsm * std::min(occs.back(), 2));
+        const char* fv = getenv("KM_BATCH_VARIANT");
+        g.variant = fv && g.prec != KM_F64 ? std::min(std::max(atoi(fv), 0), LOWD_BATCH_VARIANTS - 1) : 0;
+        const int occ = pass_lowd_batch_occupancy(g.prec, g.d, g.smem, g.variant);
+        g.grid = std::min((int)g.items.size(), ctx->nsm * std::min(occ, 2));
     }
     if (tune) KM_CUDA(batch_prologue(B, ctx->stream));
     for (size_t gi = 0; gi < B.groups.size(); ++gi) {
         BGroup& g = B.groups[gi];
-        const int occ = occs[gi];
         const int nit = (int)g.items.size();
-        std::vector<int> cand;
-        for (int bps = 1; bps <= occ; ++bps) cand.push_back(std::min(nit, ctx->nsm * bps));
-        cand.push_back(nit);
-        std::sort(cand.begin(), cand.end());
-        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        snprintf(buf, sizeof(buf), "%s d=%d cls=%d ops=%.6g items=%d occ=%d", g.prec == KM_F64 ? "f64" : "f32", g.d,
-                 g.cls, g.ops, nit, occ);
+        const int nvar = g.prec == KM_F64 ? 1 : LOWD_BATCH_VARIANTS;
+        const char* fv = getenv("KM_BATCH_VARIANT");     // restrict the tuner to one variant (tests)
+        const int v0 = fv && nvar > 1 ? std::min(std::max(atoi(fv), 0), nvar - 1) : 0;
+        const int v1 = fv && nvar > 1 ? v0 + 1 : nvar;
+        snprintf(buf, sizeof(buf), "%s d=%d cls=%d ops=%.6g items=%d", g.prec == KM_F64 ? "f64" : "f32", g.d, g.cls,
+                 g.ops, nit);
         desc += buf;
-        if (tune && cand.size() > 1) {
+        if (tune) {
             const BatchPass b = pass_launch(B, g, MODE_STANDALONE, F_ASSIGN | F_BINS | F_ENERGY, true);
             float best = 1e30f;
-            for (int grid : cand) {
-                KM_CUDA(launch_pass_lowd_batch(b, g.prec, g.d, grid, g.smem, ctx->stream));
-                KM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-                for (int r = 0; r < 3; ++r) KM_CUDA(launch_pass_lowd_batch(b, g.prec, g.d, grid, g.smem, ctx->stream));
-                KM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
-                KM_CUDA(cudaEventSynchronize(ctx->ev1));
-                float ms = 0.f;
-                KM_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-                ms /= 3.f;
-                snprintf(buf, sizeof(buf), " %d:%.1fus", grid, ms * 1e3f);
+            for (int v = v0; v < v1; ++v) {
+                const int occ = pass_lowd_batch_occupancy(g.prec, g.d, g.smem, v);
+                std::vector<int> cand;
+                for (int bps = 1; bps <= occ; ++bps) cand.push_back(std::min(nit, ctx->nsm * bps));
+                cand.push_back(nit);
+                std::sort(cand.begin(), cand.end());
+                cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+                snprintf(buf, sizeof(buf), " v%d(occ %d)", v, occ);
                 desc += buf;
-                if (ms < best) {
-                    best = ms;
-                    g.grid = grid;
+                for (int grid : cand) {
+                    KM_CUDA(launch_pass_lowd_batch(b, g.prec, g.d, grid, g.smem, ctx->stream, v));
+                    KM_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+                    for (int r = 0; r < 3; ++r) KM_CUDA(launch_pass_lowd_batch(b, g.prec, g.d, grid, g.smem, ctx->stream, v));
+                    KM_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+                    KM_CUDA(cudaEventSynchronize(ctx->ev1));
+                    float ms = 0.f;
+                    KM_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+                    ms /= 3.f;
+                    snprintf(buf, sizeof(buf), " %d:%.1fus", grid, ms * 1e3f);
+                    desc += buf;
+                    if (ms < best) {
+                        best = ms;
+                        g.grid = grid;
+                        g.variant = v;
+                    }
                 }
             }
         }
-        snprintf(buf, sizeof(buf), " -> grid %d; ", g.grid);
+        snprintf(buf, sizeof(buf), " -> variant %d grid %d; ", g.variant, g.grid);
         desc += buf;
     }
     return KM_OK;
@@ -281,6 +298,7 @@ kmeans_status batch_solve(kmeans_ctx* ctx, const kmeans_problem* pr, int n, cons
             g.smem = 0;
             g.items_off = 0;
             g.grid = 1;
+            g.variant = 0;
             B.groups.push_back(g);
             gi = (int)B.groups.size() - 1;
         }

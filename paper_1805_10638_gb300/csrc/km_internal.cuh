@@ -359,8 +359,11 @@ size_t devinfo_bytes();
 cudaError_t launch_lsq(const LsqArgs& a, cudaStream_t s);
 
 // Batched launchers (persistent grids over work items).
-cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s);
-int pass_lowd_batch_occupancy(int prec, int d, size_t smem);
+// variant: 0 = the default rows per thread of the scan, 1 = half of them (FP32 only; same results)
+cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s,
+                                   int variant = 0);
+int pass_lowd_batch_occupancy(int prec, int d, size_t smem, int variant = 0);
+constexpr int LOWD_BATCH_VARIANTS = 2;
 int pass_lowd_occupancy(int prec, int d, size_t smem);   // resident blocks per SM (CUDA occupancy API)
 cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_hprep_batch(const BatchPass& b, int grid, cudaStream_t s);

@@ -1,6 +1,6 @@
 // Per-precision entry points of the low-d pass kernels, one instantiation unit each
-// (lowd_std_f32.cu, lowd_std_f64.cu, lowd_batch_f32.cu, lowd_batch_f64.cu), dispatched on d
-// (1..16) inside each unit.
+// (lowd_std_f32.cu, lowd_std_f64.cu, lowd_batch_f32.cu, lowd_batch_f32_v1.cu, lowd_batch_f64.cu),
+// dispatched on d (1..16) inside each unit.
 #pragma once
 
 #include "km_internal.cuh"
@@ -19,5 +19,8 @@ int lowd_occupancy_f32(int d, size_t smem);
 int lowd_occupancy_f64(int d, size_t smem);
 int lowd_batch_occupancy_f32(int d, size_t smem);
 int lowd_batch_occupancy_f64(int d, size_t smem);
+// the batched FP32 pass with half the rows per thread in the scan (lowd_batch_f32_v1.cu)
+cudaError_t lowd_batch_launch_f32_v1(const BatchPass& b, int d, int grid, size_t smem, cudaStream_t s);
+int lowd_batch_occupancy_f32_v1(int d, size_t smem);
 
 }  // namespace km

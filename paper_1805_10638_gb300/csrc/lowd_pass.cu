@@ -154,9 +154,11 @@ cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStr
     return prec == KM_F64 ? lowd_launch_f64(a, d, nb, smem, s) : lowd_launch_f32(a, d, nb, smem, s);
 }
 
-cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s,
+                                   int variant)
 {
-    return prec == KM_F64 ? lowd_batch_launch_f64(b, d, grid, smem, s) : lowd_batch_launch_f32(b, d, grid, smem, s);
+    if (prec == KM_F64) return lowd_batch_launch_f64(b, d, grid, smem, s);
+    return variant == 1 ? lowd_batch_launch_f32_v1(b, d, grid, smem, s) : lowd_batch_launch_f32(b, d, grid, smem, s);
 }
 
 int pass_lowd_occupancy(int prec, int d, size_t smem)
@@ -164,9 +166,10 @@ int pass_lowd_occupancy(int prec, int d, size_t smem)
     return prec == KM_F64 ? lowd_occupancy_f64(d, smem) : lowd_occupancy_f32(d, smem);
 }
 
-int pass_lowd_batch_occupancy(int prec, int d, size_t smem)
+int pass_lowd_batch_occupancy(int prec, int d, size_t smem, int variant)
 {
-    return prec == KM_F64 ? lowd_batch_occupancy_f64(d, smem) : lowd_batch_occupancy_f32(d, smem);
+    if (prec == KM_F64) return lowd_batch_occupancy_f64(d, smem);
+    return variant == 1 ? lowd_batch_occupancy_f32_v1(d, smem) : lowd_batch_occupancy_f32(d, smem);
 }
 
 }  // namespace km

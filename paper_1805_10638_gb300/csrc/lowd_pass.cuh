@@ -564,12 +564,14 @@ __device__ __noinline__ long long group_classify(const PassArgs& a, const float*
 // The work of block `bid` of a pass launched with `nblk` blocks.  The standalone kernel calls it
 // with (blockIdx.x, gridDim.x); the batched kernel with a work item's (block, blocks of that
 // instance), so that every instance gets exactly the arithmetic of its own launch.
-template <typename T, int D>
+// RV: rows per thread of the FP32 scan (0: Shape<D>::R).  Each row's scan and the order in which
+// rows are finished do not depend on it, so every RV gives bitwise the same results.
+template <typename T, int D, int RV = 0>
 __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, const int nblk, unsigned char* smem)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int DP = Shape<D>::DP;
-    constexpr int R = F32 ? Shape<D>::R : 1;
+    constexpr int R = F32 ? (RV > 0 ? RV : Shape<D>::R) : 1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     SolveState* st = a.st;
@@ -1268,7 +1270,7 @@ __global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_l
 // turn; an item does what that block of the instance's own launch would do (same rows, same
 // partial slot, the instance's last item runs its reduction and controller).  No item waits for
 // another, so any grid size is safe.
-template <typename T, int D>
+template <typename T, int D, int RV = 0>
 __global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_lowd_batch(BatchPass b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1278,7 +1280,7 @@ __global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_l
         a.mode = b.mode;
         a.flags = b.flags;
         a.use_cond = 0;
-        pass_body<T, D>(a, w.y, a.nblk, smem);
+        pass_body<T, D, RV>(a, w.y, a.nblk, smem);
         __syncthreads();
     }
 }
@@ -1306,10 +1308,10 @@ cudaError_t launch_one(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T, int D>
+template <typename T, int D, int RV = 0>
 cudaError_t launch_batch_one(const BatchPass& b, int grid, size_t smem, cudaStream_t s)
 {
-    auto kern = k_pass_lowd_batch<T, D>;
+    auto kern = k_pass_lowd_batch<T, D, RV>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern));
@@ -1330,11 +1332,11 @@ int pass_occ(size_t smem)
     return n > 0 ? n : 1;
 }
 
-template <typename T, int D>
+template <typename T, int D, int RV = 0>
 int batch_occ(size_t smem)
 {
     int n = 0;
-    auto kern = k_pass_lowd_batch<T, D>;
+    auto kern = k_pass_lowd_batch<T, D, RV>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern)) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;

@@ -127,3 +127,11 @@ def test_oracle_thread_count_is_restored():
     t, info2, cores, C2, r2 = bench.oracle_timed(X, C0, 1000, 10)
     np.testing.assert_array_equal(C1, C2)
     assert info["iters"] == info2["iters"]
+
+
+def test_parse_tuning_reads_the_chosen_variant_and_grid():
+    desc = ("f32 d=2 cls=4 ops=1.5e+09 items=4676 v0(occ 3) 152:528.4us 4676:239.8us "
+            "v1(occ 3) 152:517.0us 4676:243.9us -> variant 0 grid 4676; "
+            "f32 d=16 cls=4 ops=1.3e+09 items=2872 v0(occ 2) 2872:468.5us v1(occ 2) 2872:428.9us "
+            "-> variant 1 grid 2872; fin items=13859 grid=608")
+    assert bench.parse_tuning(desc) == [(2, 1.5e9, 4676, 239.8), (16, 1.3e9, 2872, 428.9)]

@@ -90,6 +90,21 @@ def test_batched_repeat_and_launch_modes(monkeypatch):
     _same(first, _run_batch(ctx2, inst))
 
 
+@pytest.mark.parametrize("variant", ["0", "1"])
+def test_batched_kernel_variants_change_nothing(variant, monkeypatch):
+    """The autotuner picks, per group of instances, the pass kernel's rows per thread (default or
+    half) and its grid; forcing either variant gives bitwise the standalone solves."""
+    need_gpu()
+    inst = _instances(12, seed=2)
+    monkeypatch.setenv("KM_BATCH_VARIANT", variant)
+    ctx = km.Context(0)
+    batch = _run_batch(ctx, inst)
+    desc = km.batch_describe(ctx)
+    assert f"-> variant {variant}" in desc or "f64" in desc, desc
+    monkeypatch.delenv("KM_BATCH_VARIANT")
+    _same(batch, _run_alone(km.Context(0), inst))
+
+
 def test_batched_fp64_instance_matches_oracle():
     need_gpu()
     X, C0 = datagen.small_2d(seed=3)

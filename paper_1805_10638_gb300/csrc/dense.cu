@@ -1142,6 +1142,8 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
                 else
                     controller_revert(st, E, ch, a.thr);
                 if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+                if (a.mode == MODE_TRIAL && a.use_cond_rev)      // does the REVERT chain run at all
+                    cudaGraphSetConditional(a.cond_rev, (st->revert && !st->done) ? 1u : 0u);
             }
         }
     }

@@ -69,6 +69,8 @@ struct DenseArgs {
     int max_iter;
     int use_cond;
     cudaGraphConditionalHandle cond;
+    int use_cond_rev;                     // TRIAL chain in a graph: sets the REVERT chain's IF node
+    cudaGraphConditionalHandle cond_rev;
 };
 
 struct PackArgs {

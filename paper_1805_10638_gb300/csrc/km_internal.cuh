@@ -140,6 +140,8 @@ struct PassArgs {
     double* out_E;
     int use_cond;
     cudaGraphConditionalHandle cond;
+    int use_cond_rev;                     // TRIAL pass in a graph: sets the REVERT pass's IF node
+    cudaGraphConditionalHandle cond_rev;
     // controller parameters
     int m_max;
     int max_iter;

@@ -1236,8 +1236,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     controller_trial(st, E, ch, a.thr, a.lloyd_only, a.fixed_m, a.eps1, a.eps2, a.m_max, a.max_iter);
                 else
                     controller_revert(st, E, ch, a.thr);
-                // the kernel that ends the solve also ends the graph's while loop
+                // the kernel that ends the solve also ends the graph's while loop; the TRIAL pass
+                // also decides whether the REVERT pass runs at all
                 if (st->done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+                if (a.mode == MODE_TRIAL && a.use_cond_rev)
+                    cudaGraphSetConditional(a.cond_rev, (st->revert && !st->done) ? 1u : 0u);
             }
         }
     }

@@ -708,14 +708,62 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
     return L;
 }
 
+// Capture of a conditional IF node inside a loop body that is being captured on a stream: the
+// handle (value 0 at every graph launch) belongs to the body graph, the kernels captured before the
+// node set it each iteration, and the chain inside the node is captured into the node's own graph.
+struct IfCapture {
+    cudaGraph_t body = nullptr;
+    cudaGraphConditionalHandle h = 0;
+};
+
+cudaError_t if_handle(cudaStream_t s, IfCapture& c)
+{
+    cudaStreamCaptureStatus cs;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &c.body, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    return cudaGraphConditionalHandleCreate(&c.h, c.body, 0, cudaGraphCondAssignDefault);
+}
+
+// Runs the chain f launches inside an IF node on c.h that depends on everything s captured so far;
+// the capture on s then resumes after the node.
+template <typename F>
+cudaError_t if_chain(cudaStream_t s, const IfCapture& c, F f)
+{
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    cudaGraph_t tmp = nullptr;
+    if ((e = cudaStreamEndCapture(s, &tmp)) != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = c.h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t nif;
+    if ((e = cudaGraphAddNode(&nif, c.body, dv.data(), nullptr, dv.size(), &cp)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return e;
+    const cudaError_t ef = f();
+    e = cudaStreamEndCapture(s, &tmp);
+    if (ef != cudaSuccess) return ef;
+    if (e != cudaSuccess) return e;
+    return cudaStreamBeginCaptureToGraph(s, c.body, &nif, nullptr, 1, cudaStreamCaptureModeRelaxed);
+}
+
 // One dense pass (assignment, rescoring, update chain with the controller) in the given mode.
 cudaError_t dense_pass(const Launch& L, int mode, int use_cond, cudaGraphConditionalHandle h, cudaStream_t s,
-                       bool assign = true)
+                       bool assign = true, int use_rev = 0, cudaGraphConditionalHandle hr = 0)
 {
     DenseArgs a = L.da;
     a.mode = mode;
     a.use_cond = use_cond;
     a.cond = h;
+    a.use_cond_rev = use_rev;
+    a.cond_rev = hr;
     cudaError_t e = cudaSuccess;
     if (assign) e = launch_dense_pass(a, L.maps, L.nsm, s);
     if (e == cudaSuccess) e = launch_dense_update(a, L.P.nbk, L.P.max_chunks, s);
@@ -777,9 +825,23 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
 // update + history + least squares, accelerated iterate (which also ends the graph loop).
 cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraphConditionalHandle h)
 {
+    // Inside a graph the REVERT pass sits in an IF node that its TRIAL pass sets, so an accepted
+    // accelerated iterate launches nothing for it; the REVERT kernels still check the flag.
+    IfCapture ic;
+    const char* ife = getenv("KM_REVERT_IF");         // 0: plain launches (the kernels return at once)
+    const int lowd_if = ife ? (ife[0] == '1' || ife[0] == '3') : 0;
+    const int dense_if = ife ? (ife[0] == '2' || ife[0] == '3') : 1;
+    const int use_rev_if = L.P.dense ? dense_if : lowd_if;
+    if (use_cond && use_rev_if) {
+        const cudaError_t e = if_handle(s, ic);
+        if (e != cudaSuccess) return e;
+    }
     if (L.P.dense) {
-        cudaError_t e = dense_pass(L, MODE_TRIAL, use_cond, h, s);
-        if (e == cudaSuccess) e = dense_pass(L, MODE_REVERT, use_cond, h, s);
+        cudaError_t e = dense_pass(L, MODE_TRIAL, use_cond, h, s, true, use_cond && use_rev_if, ic.h);
+        if (e == cudaSuccess) {
+            auto rev = [&]() { return dense_pass(L, MODE_REVERT, use_cond, h, s); };
+            e = use_cond && use_rev_if ? if_chain(s, ic, rev) : rev();
+        }
         FinArgs f = L.fa;
         f.mode = MODE_TRIAL;
         f.use_cond = use_cond;
@@ -796,10 +858,16 @@ cudaError_t launch_body(const Launch& L, cudaStream_t s, int use_cond, cudaGraph
     a.flags = F_ASSIGN | F_BINS | F_ENERGY | F_CHANGED;
     a.use_cond = use_cond;
     a.cond = h;
+    a.use_cond_rev = use_cond && use_rev_if;
+    a.cond_rev = ic.h;
     cudaError_t e = a.ham ? launch_hprep(a, MODE_TRIAL, s) : cudaSuccess;
     if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
     a.mode = MODE_REVERT;       // its bound inputs come from the TRIAL pass's last block
-    if (e == cudaSuccess) e = launch_pass_lowd(a, L.prec, L.d, L.P.nb, s);
+    a.use_cond_rev = 0;
+    if (e == cudaSuccess) {
+        auto rev = [&]() { return launch_pass_lowd(a, L.prec, L.d, L.P.nb, s); };
+        e = use_cond && use_rev_if ? if_chain(s, ic, rev) : rev();
+    }
     FinArgs f = L.fa;
     f.mode = MODE_TRIAL;
     f.use_cond = use_cond;

@@ -227,7 +227,7 @@ __host__ __device__ inline SmemPlan dense_smem(int nkb, int Kpad)
     p.c = o;     o += (uint32_t)CSLOT * TN * 128;     // centroid ring
     p.cn = o;    o += (uint32_t)Kpad * 4;
     p.merge = o; o += 3 * TM * MREC * 4;
-    p.bar = (o + 7) & ~7u; o = p.bar + 16 * 8;
+    p.bar = (o + 7) & ~7u; o = p.bar + 17 * 8;
     p.slot = o;  o += 8;
     p.abort = o; o += 16;
     p.total = o + 1024;   // room to align the base to 1024 bytes
@@ -248,9 +248,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     float* s_cn = reinterpret_cast<float*>(smem + P.cn);
     float* s_merge = reinterpret_cast<float*>(smem + P.merge);
     const uint32_t bar = sbase + P.bar;
-    // barriers: xfull[2] xempty[2] cfull[4] cempty[4] afull[2] aempty[2]
+    // barriers: xfull[2] xempty[2] cfull[4] cempty[4] afull[2] aempty[2] xread
     const uint32_t xfull = bar, xempty = bar + 16, cfull = bar + 32, cempty = bar + 64, afull = bar + 96,
-                   aempty = bar + 112;
+                   aempty = bar + 112, xread = bar + 128;
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem + P.slot);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + P.abort);
     const CUtensorMap* tmCh = &tm.ch[set];
@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             mbar_init(cfull + 8 * i, 1);
             mbar_init(cempty + 8 * i, 1);
         }
+        mbar_init(xread, 4);    // the four quarter-0 epilogue warps have read the row tile's X norms
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -295,6 +296,10 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     for (int kb = 0; kb < nkb && ok; ++kb) {
                         if (t == 0) {
                             if (xit >= 1 && !mbar_wait(xempty + 8 * kb, (xit - 1) & 1, abort)) { ok = false; break; }
+                            // the previous row tile's X is also read by the epilogue (row norms) at its first
+                            // centroid tile, which can lag the MMAs by two accumulator tiles: with one or two
+                            // centroid tiles (K <= 512) the MMAs release X before that
+                            if (xit >= 1 && kb == 0 && !mbar_wait(xread, (xit - 1) & 1, abort)) { ok = false; break; }
                             mbar_expect_tx(xfull + 8 * kb, 2 * XCHUNK);
                             tma_load_2d(sXh + kb * XCHUNK, &tm.xh, kb * KBLK, tile * TM, xfull + 8 * kb);
                             tma_load_2d(sXl + kb * XCHUNK, &tm.xl, kb * KBLK, tile * TM, xfull + 8 * kb);
@@ -396,7 +401,8 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                         const uint4* xr = reinterpret_cast<const uint4*>(smem + P.xh + kb * XCHUNK + r * 128);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            const uint4 w = xr[c];
+                            // lane l takes piece c ^ (l & 7): eight different bank groups per phase
+                            const uint4 w = xr[c ^ (lane & 7)];
                             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
@@ -405,6 +411,10 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                             }
                         }
                     }
+                }
+                if (ct == 0 && h == 0) {      // done with the row tile's X in shared memory
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(xread);
                 }
                 if (ok) {
                     tc_fence_after();

@@ -367,6 +367,7 @@ cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid
 int pass_lowd_batch_occupancy(int prec, int d, size_t smem, int variant = 0);
 constexpr int LOWD_BATCH_VARIANTS = 2;
 int pass_lowd_occupancy(int prec, int d, size_t smem);   // resident blocks per SM (CUDA occupancy API)
+int pass_lowd_occupancy_ao(int d, size_t smem);          // the same for the FP32 assignment-only kernel
 cudaError_t launch_hprep(const PassArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_hprep_batch(const BatchPass& b, int grid, cudaStream_t s);
 cudaError_t launch_fin_batch(const BatchFin& b, int grid, size_t smem, cudaStream_t s);

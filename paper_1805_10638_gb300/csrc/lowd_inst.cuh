@@ -19,6 +19,9 @@ int lowd_occupancy_f32(int d, size_t smem);
 int lowd_occupancy_f64(int d, size_t smem);
 int lowd_batch_occupancy_f32(int d, size_t smem);
 int lowd_batch_occupancy_f64(int d, size_t smem);
+// the FP32 pass without update bins and bounds (lowd_ao_f32.cu)
+cudaError_t lowd_launch_f32_ao(const PassArgs& a, int d, int nb, size_t smem, cudaStream_t s);
+int lowd_occupancy_f32_ao(int d, size_t smem);
 // the batched FP32 pass with half the rows per thread in the scan (lowd_batch_f32_v1.cu)
 cudaError_t lowd_batch_launch_f32_v1(const BatchPass& b, int d, int grid, size_t smem, cudaStream_t s);
 int lowd_batch_occupancy_f32_v1(int d, size_t smem);

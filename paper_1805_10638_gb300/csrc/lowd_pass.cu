@@ -151,7 +151,10 @@ cudaError_t launch_pass_lowd(const PassArgs& a, int prec, int d, int nb, cudaStr
 {
     const size_t smem = pass_lowd_smem(prec, d, a.K, a.Kpad, (a.flags & F_BINS) != 0, a.ham ? a.hq_cap : 0,
                                        a.ham ? a.hg : 0);
-    return prec == KM_F64 ? lowd_launch_f64(a, d, nb, smem, s) : lowd_launch_f32(a, d, nb, smem, s);
+    if (prec == KM_F64) return lowd_launch_f64(a, d, nb, smem, s);
+    // FP32 passes without update bins and bounds: the assignment-only kernel
+    if (!(a.flags & F_BINS) && !a.ham) return lowd_launch_f32_ao(a, d, nb, smem, s);
+    return lowd_launch_f32(a, d, nb, smem, s);
 }
 
 cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid, size_t smem, cudaStream_t s,
@@ -160,6 +163,8 @@ cudaError_t launch_pass_lowd_batch(const BatchPass& b, int prec, int d, int grid
     if (prec == KM_F64) return lowd_batch_launch_f64(b, d, grid, smem, s);
     return variant == 1 ? lowd_batch_launch_f32_v1(b, d, grid, smem, s) : lowd_batch_launch_f32(b, d, grid, smem, s);
 }
+
+int pass_lowd_occupancy_ao(int d, size_t smem) { return lowd_occupancy_f32_ao(d, smem); }
 
 int pass_lowd_occupancy(int prec, int d, size_t smem)
 {

@@ -566,7 +566,9 @@ __device__ __noinline__ long long group_classify(const PassArgs& a, const float*
 // instance), so that every instance gets exactly the arithmetic of its own launch.
 // RV: rows per thread of the FP32 scan (0: Shape<D>::R).  Each row's scan and the order in which
 // rows are finished do not depend on it, so every RV gives bitwise the same results.
-template <typename T, int D, int RV = 0>
+// AO: a pass without update bins and without bounds (the standalone assignment and energy calls):
+// that code is compiled out, so the kernel fits a tighter register budget.
+template <typename T, int D, int RV = 0, bool AO = false>
 __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, const int nblk, unsigned char* smem)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -596,10 +598,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
     }
     const int flags = a.flags;
     const bool do_assign = flags & F_ASSIGN;
-    const bool do_bins = flags & F_BINS;
+    const bool do_bins = !AO && (flags & F_BINS);
     const int K = a.K;
     // Hamerly bounds: FP32 solver passes that assign (INIT computes the bounds, TRIAL and REVERT use them)
-    const bool ham = F32 && a.ham && do_assign &&
+    const bool ham = !AO && F32 && a.ham && do_assign &&
                      (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
     // the solver's TRIAL / REVERT update sums in 64-bit fixed point (see layout)
     const bool fx = F32 && D <= FX_MAX_D && do_bins && a.acc != nullptr &&
@@ -619,13 +621,28 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
         float* dst = reinterpret_cast<float*>(smem + L.cpk);
         float* dc = reinterpret_cast<float*>(smem + L.c);
         if (flags & F_PACK) {
-            // standalone call: o = mean of the given centroids (FP64, fixed order), then pack
+            // standalone call: o = mean of the given centroids (a shift that only keeps the FP32
+            // scores small; FP32 sums in a fixed order: per thread, butterfly, warps in order), then pack
             const float* Cr = a.rawC;
-            for (int k = 0; k < D; ++k) {
-                double v = 0.0;
-                for (int j = tid; j < K; j += blockDim.x) v += (double)Cr[(size_t)j * D + k];
-                v = block_sum_d(v, s_red);
-                if (tid == 0) s_org[k] = (float)(v / K);
+            float ov[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) ov[k] = 0.f;
+            for (int j = tid; j < K; j += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < D; ++k) ov[k] += Cr[(size_t)j * D + k];
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) ov[k] += __shfl_xor_sync(FULL, ov[k], off);
+            float* fr = reinterpret_cast<float*>(s_red);        // [W][D] <= 128 floats
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < D; ++k) fr[warp * D + k] = ov[k];
+            __syncthreads();
+            if (tid < D) {
+                float v = 0.f;
+                for (int w = 0; w < W; ++w) v += fr[w * D + tid];
+                s_org[tid] = v / (float)K;
             }
             __syncthreads();
             for (int j = tid; j < a.Kpad; j += blockDim.x) {
@@ -637,7 +654,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, const int bid, cons
                     for (int k = 0; k < D; ++k) {
                         const float c = Cr[(size_t)j * D + k];
                         dc[(size_t)j * D + k] = c;
-                        const float cc = (float)((double)c - (double)s_org[k]);
+                        const float cc = c - s_org[k];           // rounded once, as in FP64 then FP32
                         dst[pk_index(j, k, DP)] = -2.f * cc;
                         nrm += (double)cc * (double)cc;
                     }
@@ -1269,6 +1286,24 @@ __global__ void __launch_bounds__(LOWD_THREADS, MinBlocks<T, D>::value) k_pass_l
     pass_body<T, D>(a, blockIdx.x, gridDim.x, smem);
 }
 
+// Resident blocks per SM of the assignment-only FP32 pass: without the bins and bounds code the
+// scan fits 64 registers for d <= 3, so four blocks (32 warps) hide more latency; d = 7, 8 keep
+// their registers at two blocks (three spill here).
+template <typename T, int D>
+struct AoBlocks {
+    static constexpr int value = !std::is_same<T, float>::value ? MinBlocks<T, D>::value
+                                 : D <= 3                        ? 4
+                                 : D <= 6                        ? 3
+                                                                 : 2;
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(LOWD_THREADS, AoBlocks<T, D>::value) k_pass_lowd_ao(PassArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    pass_body<T, D, 0, true>(a, blockIdx.x, gridDim.x, smem);
+}
+
 // Persistent batched pass: each block takes work items (instance, block of that instance) in
 // turn; an item does what that block of the instance's own launch would do (same rows, same
 // partial slot, the instance's last item runs its reduction and controller).  No item waits for
@@ -1323,6 +1358,30 @@ cudaError_t launch_batch_one(const BatchPass& b, int grid, size_t smem, cudaStre
     }
     kern<<<grid, LOWD_THREADS, smem, s>>>(b);
     return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t launch_one_ao(const PassArgs& a, int nb, size_t smem, cudaStream_t s)
+{
+    auto kern = k_pass_lowd_ao<T, D>;
+    static bool attr_set = false;
+    if (!attr_set || smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<nb, LOWD_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int D>
+int pass_occ_ao(size_t smem)
+{
+    int n = 0;
+    auto kern = k_pass_lowd_ao<T, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_limit(kern)) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, LOWD_THREADS, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
 }
 
 template <typename T, int D>

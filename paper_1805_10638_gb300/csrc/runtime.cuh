@@ -125,9 +125,9 @@ kmeans_status check_data(kmeans_ctx* ctx, const kmeans_data* X, int K, bool need
 // memory size, at most 4 per SM), and at least 1024 rows per block on the FP32 path (256 on the
 // FP64 path) so that the per-block staging and partial sums stay small against the scan.  The
 // count fixes the order of the update's sums; batched solves reuse it per instance.
-int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem, int prec, int d)
+int pass_blocks(kmeans_ctx* ctx, int64_t N, size_t smem, int prec, int d, bool ao = false)
 {
-    int per_sm = pass_lowd_occupancy(prec, d, smem);
+    int per_sm = ao ? pass_lowd_occupancy_ao(d, smem) : pass_lowd_occupancy(prec, d, smem);
     if (per_sm > 4) per_sm = 4;
     if (per_sm < 1) per_sm = 1;
     int64_t nb = (int64_t)ctx->nsm * per_sm;
@@ -270,7 +270,9 @@ kmeans_status make_plan(kmeans_ctx* ctx, int64_t N, int d, int K, int prec, int 
     P.smem = pass_lowd_smem(prec, d, K, P.Kpad, bins);
     if (P.smem > (size_t)LOWD_SMEM_MAX)
         return fail(ctx, KM_EINVAL, bins ? "K*d too large for the fused low-d update" : "K*d too large");
-    P.nb = pass_blocks(ctx, N, P.smem, prec, d);
+    // FP32 plans without update bins (the standalone assignment and energy calls) run the
+    // assignment-only kernel, with its own resident blocks per SM
+    P.nb = pass_blocks(ctx, N, P.smem, prec, d, f32 && !bins);
     const int benv = group_ok ? bounds_env() : 0;
     const bool cheap_half = (int64_t)K * K * d <= (int64_t(1) << 23) || benv == 1;
     const bool group = group_ok && K >= 2 && K <= 16384 && benv != 1 && (!cheap_half || benv == 2);

@@ -72,26 +72,29 @@ def profiled_traffic(name: str):
     return None
 
 
-def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool) -> int:
+def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool, rejected: int = 0) -> int:
     """Kernels one solve launches.  Low-d: the prologue (k_prep, [k_hprep], INIT pass, k_fin,
     [k_mix]), per loop pass the same with the TRIAL and REVERT passes in place of the INIT pass,
     and the epilogue (EPI pass, k_epi); k_hprep with Hamerly bounds, k_mix unless the mix is fused
-    into k_fin.  Dense: 14 in the prologue, 19 per loop pass (two 8-kernel assignment and update
-    chains, k_fin, k_mix, the BF16 packing), 4 in the epilogue."""
+    into k_fin.  Dense: 13 in the prologue (k_prep, k_xcheck, two packings, the INIT chain of 7:
+    assignment, rescan, rescan labels, count, scan, scatter, segment sums; k_fin, k_mix), per loop
+    pass 10 (the TRIAL chain, k_fin, k_mix, the packing) plus the REVERT chain's 7 when the
+    safeguard fired (it sits in a conditional node otherwise), 5 in the epilogue."""
     if dense:
-        return 18 + 19 * iters
+        return 18 + 10 * iters + 7 * rejected
     per = 3 + int(ham) + int(not fused_mix)
     return per * (iters + 1) + 2
 
 
 def batched_launches(loops: int, ngrp: int, ham: bool, mix: bool, dense_iters) -> int:
+    # dense_iters: (iterations, rejected) of each tensor-core instance
     """Kernels of one batched solve.  Low-d chain: prologue (k_prep_batch, [k_hprep_batch], one
     INIT pass per group, k_fin_batch, [k_mix_batch]), per loop step ([k_hprep_batch], TRIAL and
     REVERT passes per group, k_fin_batch, [k_mix_batch], k_batch_done), epilogue (EPI pass per
     group, k_epi_batch); plus one tensor-core chain per dense instance."""
     h, m = int(ham), int(mix)
     lowd = (2 + h + ngrp + m) + loops * (h + 2 * ngrp + 2 + m) + ngrp + 1 if ngrp else 0
-    return lowd + sum(solve_launches(it, True, False, False) for it in dense_iters)
+    return lowd + sum(solve_launches(it, True, False, False, rj) for it, rj in dense_iters)
 
 
 def same_energy_speed(ms_aa, ms_ll, E_aa, E_ll, rtol: float = 1e-6):
@@ -511,7 +514,7 @@ def run_batched(args, rank, world, local_rank):
     ngrp = len(groups)
     ham = any(inf[i]["scanned_rows"] < inf[i]["assign_passes"] * data[i][0].shape[0] for inf in inf_aa for i in lowd)
     mix = any(data[i][2] * data[i][0].shape[1] > 64 for i in lowd)
-    launches = sum(batched_launches(L, ngrp, ham, mix, [inf[i]["iters"] for i in dense])
+    launches = sum(batched_launches(L, ngrp, ham, mix, [(inf[i]["iters"], inf[i]["rejected"]) for i in dense])
                    for inf, L in zip(inf_aa, loops))
     E_aa = np.array([[inf[i]["E"] for i in range(n)] for inf in inf_aa])
     E_ll = np.array([[inf[i]["E"] for i in range(n)] for inf in inf_ll])
@@ -824,7 +827,7 @@ def run_ours(args, rank, world, local_rank):
 
     # our kernels in the timed Algorithm 1 solves (Hamerly bounds are on when a pass skipped rows)
     ham = (not dense) and any(i["scanned_rows"] < i["assign_passes"] * N for i in inf_aa)
-    launches = sum(solve_launches(i["iters"], dense, ham, K * d <= 64) for i in inf_aa)
+    launches = sum(solve_launches(i["iters"], dense, ham, K * d <= 64, i["rejected"]) for i in inf_aa)
     if rank == 0:
         E_aa = np.array([i["E"] for i in inf_aa])
         E_ll = np.array([i["E"] for i in inf_ll])

@@ -807,20 +807,36 @@ __global__ void __launch_bounds__(256) k_xsplit(const float* X, const __nv_bfloa
     }
 }
 
-// Row norms ||x|| (FP32, for the error bound) and the non-finite check, once per solve.
-__global__ void __launch_bounds__(256) k_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st)
+// Once per solve: the non-finite check of X and the largest ||x|| (FP32 bits into *xmax: the norms
+// are non-negative, so their bits order like the values), which bounds the update's fixed-point
+// sums.  One warp per row, lane l on dimensions 4l..4l+3 (d <= 128, d % 8 == 0), four rows in flight.
+__global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st)
 {
+    const int lane = threadIdx.x & 31;
+    const bool act = 4 * lane < d;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const float* Xl = X + 4 * lane;
     int bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const float* x = X + i * d;
-        float s = 0.f;
-        for (int k = 0; k < d; ++k) {
-            bad |= !isfinite(x[k]);
-            s = fmaf(x[k], x[k], s);
+    float mx = 0.f;
+    for (int64_t i0 = w0; i0 < N; i0 += 4 * W) {
+        float4 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * W;
+            xv[u] = (act && i < N) ? __ldg(reinterpret_cast<const float4*>(Xl + i * d)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        xnorm[i] = sqrtf(s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bad |= !isfinite(xv[u].x) | !isfinite(xv[u].y) | !isfinite(xv[u].z) | !isfinite(xv[u].w);
+            float sq = fmaf(xv[u].x, xv[u].x, fmaf(xv[u].y, xv[u].y, fmaf(xv[u].z, xv[u].z, xv[u].w * xv[u].w)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
+            mx = fmaxf(mx, sq);
+        }
     }
-    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0 && st) st->status = KM_ENONFINITE;
+    if (__any_sync(FULL, bad) && lane == 0 && st) st->status = KM_ENONFINITE;
+    if (lane == 0 && mx > 0.f) atomicMax(xmax, __float_as_uint(sqrtf(mx) * (1.f + 1e-5f)));
 }
 
 // ------------------------------------------------------------------ update chain
@@ -940,6 +956,25 @@ __global__ void __launch_bounds__(256) k_dscan(DenseArgs a, int nbk)
         a.off[K] = off;
         *a.nchunks = coff;
     }
+    if (a.prescaled) {
+        // the scale before the sums: a cluster's residual sum is at most N (max||x|| + max||c||) in
+        // every component, kept below 2^61
+        const float* cn = a.cn[set];
+        float cm = 0.f;
+        for (int jj = threadIdx.x; jj < K; jj += blockDim.x) cm = fmaxf(cm, cn[jj]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(FULL, cm, o));
+        __shared__ float s_cm[8];
+        if (lane == 0) s_cm[w] = cm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int ww = 0; ww < 8; ++ww) cm = fmaxf(cm, s_cm[ww]);
+            const double rb = (double)a.N * ((double)__uint_as_float(a.counter[4]) + sqrt((double)cm) * 1.0001);
+            int fxs = rb > 0.0 ? 60 - ilogb(rb) : 0;
+            fxs = fxs > 100 ? 100 : (fxs < -100 ? -100 : fxs);
+            a.counter[3] = (unsigned int)fxs;
+        }
+    }
     if (threadIdx.x == 0) a.counter[1] = 0u;      // ready for the next pass
 }
 
@@ -972,131 +1007,13 @@ __global__ void __launch_bounds__(32) k_dscatter(DenseArgs a)
     }
 }
 
-// 4. Residual sums per chunk of <= SEG rows of one cluster (rows in perm order), FP32 within the
-//    chunk, the energy of the block's eight chunks (in chunk order) and the largest |partial|.  One
-//    warp per chunk: lane l holds the dimensions 4l..4l+3 (d <= 128, d % 8 == 0; 16-byte loads),
-//    the chunk's row indices sit two per lane, and rows are loaded eight at a time so that eight
-//    loads per lane are in flight; the sums still run over the rows in order.
-constexpr int SEG_UNROLL = 8;
-__global__ void __launch_bounds__(256) k_dsegsum(DenseArgs a)
-{
-    const int set = pass_set(a.st, a.mode);
-    if (set < 0) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = a.d;
-    const int nch = *a.nchunks;
-    const int c = blockIdx.x * 8 + w;
-    __shared__ double s_e[8];
-    __shared__ float s_m[8];
-    double ew = 0.0;
-    float am = 0.f;
-    if (c < nch) {
-        const int j = a.chunk_cluster[c];
-        const int lc = c - a.choff[j];
-        const int p0 = a.off[j] + lc * SEG;
-        const int n = min(a.off[j + 1] - p0, SEG);
-        const bool act = 4 * lane < d;
-        const bool use64 = a.mode == MODE_EPI;   // G^t was not packed when the loop stopped at max_iter
-        float4 cj = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act) {
-            const size_t o = (size_t)j * d + 4 * lane;
-            if (use64) {
-                const double* c64 = a.c64[1] + o;
-                cj = make_float4((float)c64[0], (float)c64[1], (float)c64[2], (float)c64[3]);
-            } else {
-                cj = *reinterpret_cast<const float4*>(a.c32[set] + o);
-            }
-        }
-        const int ra = lane < n ? a.perm[p0 + lane] : 0;
-        const int rb = lane + 32 < n ? a.perm[p0 + 32 + lane] : 0;
-        const float* X = a.X + 4 * lane;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        float e = 0.f;
-        for (int p = 0; p < n; p += SEG_UNROLL) {
-            float4 xv[SEG_UNROLL];
-#pragma unroll
-            for (int u = 0; u < SEG_UNROLL; ++u) {
-                const int q = p + u;
-                const int r1 = __shfl_sync(FULL, ra, q & 31), r2 = __shfl_sync(FULL, rb, q & 31);
-                const int64_t row = q < 32 ? r1 : r2;
-                xv[u] = (act && q < n) ? __ldg(reinterpret_cast<const float4*>(X + row * d))
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < SEG_UNROLL; ++u) {
-                if (p + u < n) {
-                    const float r0 = xv[u].x - cj.x, r1 = xv[u].y - cj.y, r2 = xv[u].z - cj.z, r3 = xv[u].w - cj.w;
-                    acc.x += r0;
-                    acc.y += r1;
-                    acc.z += r2;
-                    acc.w += r3;
-                    e = fmaf(r0, r0, e);
-                    e = fmaf(r1, r1, e);
-                    e = fmaf(r2, r2, e);
-                    e = fmaf(r3, r3, e);
-                }
-            }
-        }
-        if (act) *reinterpret_cast<float4*>(a.part + (size_t)c * d + 4 * lane) = acc;
-        const f2sum es = warp_sum_f2(f2sum{e, 0.f});
-        ew = (double)es.hi + (double)es.lo;
-        float m = fmaxf(fmaxf(fabsf(acc.x), fabsf(acc.y)), fmaxf(fabsf(acc.z), fabsf(acc.w)));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
-        am = m;
-    }
-    if (lane == 0) {
-        s_e[w] = ew;
-        s_m[w] = am;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        float m = 0.f;
-        for (int i = 0; i < 8; ++i) {
-            t += s_e[i];
-            m = fmaxf(m, s_m[i]);
-        }
-        a.pe[blockIdx.x] = t;
-        if (m > 0.f) atomicMax(a.counter + 2, __float_as_uint(m));   // non-negative: ordered as integers
-    }
-}
-
-// 5. Per chunk (one warp, lane l on dimensions 4l..4l+3, the blocks of k_dsegsum): the chunk's
-//    FP32 partial in 64-bit fixed point, added into its cluster's totals acc [K][d] with integer
-//    atomics (exact, so the totals do not depend on the order: a cluster of any size costs one
-//    atomic per chunk and dimension, and the work stays balanced over chunks); the cluster sizes
-//    into accC.  The scale 2^fxs keeps every total, at most nch * max|partial|, below 2^61.  The last
-//    block sums the energy partials of the k_dsegsum blocks and the change counts in a fixed order,
-//    publishes fxs for k_fin and runs the controller.
-__global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
+// The update's last block (every block calls it after its own work): fixed-order sums of the energy
+// partials of the k_dsegsum blocks and of the change counts, the pass's scale exponent for k_fin,
+// and the controller; a TRIAL pass whose safeguard fired clears the totals for the REVERT pass.
+__device__ __forceinline__ void dseg_finish(const DenseArgs& a, int nbk, int nseg, int fxs)
 {
     SolveState* st = a.st;
-    const int set = pass_set(st, a.mode);
-    if (set < 0) return;
     const int lane = threadIdx.x & 31, d = a.d, K = a.K;
-    const int nch = *a.nchunks;
-    const float amax = __uint_as_float(__ldcg(a.counter + 2));
-    int fxs = 0;
-    if (amax > 0.f) {
-        fxs = 60 - ilogb((double)amax * (double)nch);
-        fxs = fxs > 100 ? 100 : (fxs < -100 ? -100 : fxs);
-    }
-    if (a.mode != MODE_EPI) {                      // the epilogue pass needs only the energy
-        const float fxf = ldexpf(1.f, fxs);
-        const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
-        if (c < nch && 4 * lane < d) {
-            const int j = a.chunk_cluster[c];
-            const float4 v = *reinterpret_cast<const float4*>(a.part + (size_t)c * d + 4 * lane);
-            unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.acc) + (size_t)j * d + 4 * lane;
-            const long long q[4] = {__float2ll_rn(v.x * fxf), __float2ll_rn(v.y * fxf), __float2ll_rn(v.z * fxf),
-                                    __float2ll_rn(v.w * fxf)};
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (q[t] != 0) atomicAdd(dst + t, (unsigned long long)q[t]);
-        }
-        for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj < K; jj += gridDim.x * blockDim.x)
-            a.accC[jj] = a.counts[jj];
-    }
     __threadfence();
     __syncthreads();
     __shared__ unsigned int s_last;
@@ -1166,6 +1083,153 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
             for (int jj = threadIdx.x; jj < K; jj += blockDim.x) a.accC[jj] = 0;
         }
     }
+}
+
+// 4. Residual sums per chunk of <= SEG rows of one cluster (rows in perm order), FP32 within the
+//    chunk, the energy of the block's eight chunks (in chunk order) and the largest |partial|.  One
+//    warp per chunk: lane l holds the dimensions 4l..4l+3 (d <= 128, d % 8 == 0; 16-byte loads),
+//    the chunk's row indices sit two per lane, and rows are loaded eight at a time so that eight
+//    loads per lane are in flight; the sums still run over the rows in order.
+constexpr int SEG_UNROLL = 8;
+__global__ void __launch_bounds__(256) k_dsegsum(DenseArgs a, int nbk)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = a.d;
+    const int nch = *a.nchunks;
+    const int c = blockIdx.x * 8 + w;
+    __shared__ double s_e[8];
+    __shared__ float s_m[8];
+    double ew = 0.0;
+    float am = 0.f;
+    if (c < nch) {
+        const int j = a.chunk_cluster[c];
+        const int lc = c - a.choff[j];
+        const int p0 = a.off[j] + lc * SEG;
+        const int n = min(a.off[j + 1] - p0, SEG);
+        const bool act = 4 * lane < d;
+        const bool use64 = a.mode == MODE_EPI;   // G^t was not packed when the loop stopped at max_iter
+        float4 cj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+            const size_t o = (size_t)j * d + 4 * lane;
+            if (use64) {
+                const double* c64 = a.c64[1] + o;
+                cj = make_float4((float)c64[0], (float)c64[1], (float)c64[2], (float)c64[3]);
+            } else {
+                cj = *reinterpret_cast<const float4*>(a.c32[set] + o);
+            }
+        }
+        const int ra = lane < n ? a.perm[p0 + lane] : 0;
+        const int rb = lane + 32 < n ? a.perm[p0 + 32 + lane] : 0;
+        const float* X = a.X + 4 * lane;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float e = 0.f;
+        for (int p = 0; p < n; p += SEG_UNROLL) {
+            float4 xv[SEG_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                const int q = p + u;
+                const int r1 = __shfl_sync(FULL, ra, q & 31), r2 = __shfl_sync(FULL, rb, q & 31);
+                const int64_t row = q < 32 ? r1 : r2;
+                xv[u] = (act && q < n) ? __ldg(reinterpret_cast<const float4*>(X + row * d))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                if (p + u < n) {
+                    const float r0 = xv[u].x - cj.x, r1 = xv[u].y - cj.y, r2 = xv[u].z - cj.z, r3 = xv[u].w - cj.w;
+                    acc.x += r0;
+                    acc.y += r1;
+                    acc.z += r2;
+                    acc.w += r3;
+                    e = fmaf(r0, r0, e);
+                    e = fmaf(r1, r1, e);
+                    e = fmaf(r2, r2, e);
+                    e = fmaf(r3, r3, e);
+                }
+            }
+        }
+        if (a.prescaled) {
+            // the scale is known: the chunk's totals go straight into the cluster's fixed-point sums
+            if (act && a.mode != MODE_EPI) {
+                const float fxf = ldexpf(1.f, (int)a.counter[3]);
+                unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.acc) + (size_t)j * d + 4 * lane;
+                const long long qv[4] = {__float2ll_rn(acc.x * fxf), __float2ll_rn(acc.y * fxf),
+                                         __float2ll_rn(acc.z * fxf), __float2ll_rn(acc.w * fxf)};
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (qv[t] != 0) atomicAdd(dst + t, (unsigned long long)qv[t]);
+            }
+        } else if (act) {
+            *reinterpret_cast<float4*>(a.part + (size_t)c * d + 4 * lane) = acc;
+        }
+        const f2sum es = warp_sum_f2(f2sum{e, 0.f});
+        ew = (double)es.hi + (double)es.lo;
+        float m = fmaxf(fmaxf(fabsf(acc.x), fabsf(acc.y)), fmaxf(fabsf(acc.z), fabsf(acc.w)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+        am = m;
+    }
+    if (lane == 0) {
+        s_e[w] = ew;
+        s_m[w] = am;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        float m = 0.f;
+        for (int i = 0; i < 8; ++i) {
+            t += s_e[i];
+            m = fmaxf(m, s_m[i]);
+        }
+        a.pe[blockIdx.x] = t;
+        if (m > 0.f && !a.prescaled) atomicMax(a.counter + 2, __float_as_uint(m));   // ordered as integers
+    }
+    if (a.prescaled) {
+        if (a.mode != MODE_EPI)
+            for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj < a.K; jj += gridDim.x * blockDim.x)
+                a.accC[jj] = a.counts[jj];
+        dseg_finish(a, nbk, gridDim.x, (int)a.counter[3]);
+    }
+}
+
+// 5. Per chunk (one warp, lane l on dimensions 4l..4l+3, the blocks of k_dsegsum): the chunk's
+//    FP32 partial in 64-bit fixed point, added into its cluster's totals acc [K][d] with integer
+//    atomics (exact, so the totals do not depend on the order: a cluster of any size costs one
+//    atomic per chunk and dimension, and the work stays balanced over chunks); the cluster sizes
+//    into accC.  The scale 2^fxs keeps every total, at most nch * max|partial|, below 2^61.  The last
+//    block sums the energy partials of the k_dsegsum blocks and the change counts in a fixed order,
+//    publishes fxs for k_fin and runs the controller.
+__global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, d = a.d, K = a.K;
+    const int nch = *a.nchunks;
+    const float amax = __uint_as_float(__ldcg(a.counter + 2));
+    int fxs = 0;
+    if (amax > 0.f) {
+        fxs = 60 - ilogb((double)amax * (double)nch);
+        fxs = fxs > 100 ? 100 : (fxs < -100 ? -100 : fxs);
+    }
+    if (a.mode != MODE_EPI) {                      // the epilogue pass needs only the energy
+        const float fxf = ldexpf(1.f, fxs);
+        const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+        if (c < nch && 4 * lane < d) {
+            const int j = a.chunk_cluster[c];
+            const float4 v = *reinterpret_cast<const float4*>(a.part + (size_t)c * d + 4 * lane);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.acc) + (size_t)j * d + 4 * lane;
+            const long long q[4] = {__float2ll_rn(v.x * fxf), __float2ll_rn(v.y * fxf), __float2ll_rn(v.z * fxf),
+                                    __float2ll_rn(v.w * fxf)};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (q[t] != 0) atomicAdd(dst + t, (unsigned long long)q[t]);
+        }
+        for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj < K; jj += gridDim.x * blockDim.x)
+            a.accC[jj] = a.counts[jj];
+    }
+    dseg_finish(a, nbk, nseg, fxs);
 }
 
 // Standalone calls: per-row direct-form FP32 squared distance to the assigned centroid (optional
@@ -1332,8 +1396,9 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
     k_dscatter<<<nbk, 32, sm_sc, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nseg = (max_chunks + 7) / 8;
-    k_dsegsum<<<nseg, 256, 0, s>>>(a);
+    k_dsegsum<<<nseg, 256, 0, s>>>(a, nbk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.prescaled) return cudaSuccess;       // k_dsegsum added the totals and finished the pass
     // the last-block counters counter[0..1] and the slots counter[2..3] are zero at the start of
     // every call and reset by the kernels that use them
     k_dsegfin<<<nseg, 256, 0, s>>>(a, nbk, nseg);
@@ -1355,9 +1420,9 @@ cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st, int nsm, cudaStream_t s)
+cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st, int nsm, cudaStream_t s)
 {
-    k_xnorm<<<nsm * 8, 256, 0, s>>>(X, N, d, xnorm, st);
+    k_xcheck<<<nsm * 8, 256, 0, s>>>(X, N, d, xmax, st);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,6 @@ struct DenseArgs {
     int mode;                 // PassMode
     const float* X;           // [N][d] FP32
     const __nv_bfloat16* Xb;  // [N][d] BF16 copy x_hi (an MMA operand; its row norms feed the bound)
-    const float* xnorm;       // [N] ||x||
     const float* cn[2];       // [Kpad] ||c||^2, +inf for pad rows; set 0 = C^t, set 1 = C_AU
     const float* c32[2];      // [K][d] FP32 centroids
     const double* c64[2];     // [K][d] FP64 centroids (C^t, C_AU)
@@ -54,8 +53,10 @@ struct DenseArgs {
     long long* pnch;          // [nbk]
     long long* acc;           // [K][d] int64 fixed-point residual sums (scale 2^counter[3]), read and
     int32_t* accC;            // [K]    cleared by k_fin; cluster sizes
-    unsigned int* counter;    // [0]: k_dsegfin's last block, [1]: k_dscan's, [2]: max |chunk partial|
-                              // (FP32 bits), [3]: the pass's fixed-point scale exponent
+    unsigned int* counter;    // [0]: the update's last block, [1]: k_dscan's, [2]: max |chunk partial|
+                              // (FP32 bits), [3]: the pass's fixed-point scale exponent, [4]: max ||x||
+                              // (FP32 bits, from k_xcheck)
+    int prescaled;            // solver: the scale comes from max ||x|| and max ||c|| before the sums
     double* out_E;
     long long* out_nch;
     // controller
@@ -92,6 +93,6 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
 cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s);
 cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,
                         cudaStream_t s);
-cudaError_t launch_xnorm(const float* X, int64_t N, int d, float* xnorm, SolveState* st, int nsm, cudaStream_t s);
+cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st, int nsm, cudaStream_t s);
 
 }  // namespace km

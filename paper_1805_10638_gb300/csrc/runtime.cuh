@@ -40,7 +40,7 @@ struct Plan {
     size_t pS, pCnt, pE, pNch, pResc, pScan, pBad, pDots, counter, info, acc, qrw;
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
-    size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, xnorm, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
+    size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
         part, pe, pnch, rowe, rown;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
@@ -181,7 +181,6 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.xlo = take((size_t)N * d * 2);     // x_lo = bf16(x - x_hi), when the caller does not supply it
     P.cn0 = take((size_t)P.Kpad * 4);
     P.cn1 = take((size_t)P.Kpad * 4);
-    P.xnorm = take((size_t)N * 4);
     P.queue = take((size_t)N * 4);       // near-tie rows
     P.rkey = take((size_t)N * 8);        // their (distance, index) keys
     P.qcount = take(256);
@@ -496,7 +495,6 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.K = K;
     a.Kpad = P.Kpad;
     a.X = X32;
-    a.xnorm = at<float>(base, P.xnorm);
     a.cn[0] = at<float>(base, P.cn0);
     a.cn[1] = at<float>(base, P.cn1);
     a.c32[0] = at<float>(base, P.c32_0);
@@ -694,6 +692,7 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
         DenseArgs& da = L.da;
         da = dense_args(base, P, L.X32, X->N, d, K);
         da.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
+        da.prescaled = 1;                // max ||x|| from the prologue's check fixes the update's scale
         da.thr = thr;
         da.lloyd_only = p.lloyd_only;
         da.fixed_m = p.fixed_m ? 1 : 0;
@@ -782,7 +781,7 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
         if (e == cudaSuccess)
             e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
                             nullptr, L.st, L.p.m_init, L.m_max, s, 0);
-        if (e == cudaSuccess) e = launch_xnorm(L.X32, L.N, L.d, const_cast<float*>(L.da.xnorm), L.st, L.nsm, s);
+        if (e == cudaSuccess) e = launch_xcheck(L.X32, L.N, L.d, L.da.counter + 4, L.st, L.nsm, s);
         if (e == cudaSuccess && L.xsplit)
             e = launch_xsplit(L.X32, L.da.Xb, const_cast<void*>(L.xlo), L.N * (int64_t)L.d, L.nsm, s);
         PackArgs pk = L.pk;

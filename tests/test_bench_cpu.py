@@ -96,7 +96,7 @@ def test_solve_launch_count():
     # lowd_2m: Hamerly bounds, separate mix -> 5 kernels in the prologue and per loop pass, 2 after
     assert bench.solve_launches(152, dense=False, ham=True, fused_mix=False) == 5 * 153 + 2
     assert bench.solve_launches(10, dense=False, ham=False, fused_mix=True) == 3 * 11 + 2
-    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False) == 18 + 19 * 160
+    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23) == 18 + 10 * 160 + 7 * 23
 
 
 def test_same_energy_speed():
@@ -110,8 +110,9 @@ def test_batched_launch_count():
     # 3 groups, bounds and a separate mix: 2 + 1 + 3 + 1 in the prologue, 1 + 6 + 2 + 1 per step, 3 + 1 after
     assert bench.batched_launches(10, 3, True, True, []) == 7 + 10 * 10 + 4
     assert bench.batched_launches(10, 3, False, False, []) == 5 + 10 * 8 + 4
-    assert bench.batched_launches(5, 2, True, True, [7, 9]) == (6 + 5 * 8 + 3) + (18 + 19 * 7) + (18 + 19 * 9)
-    assert bench.batched_launches(0, 0, False, False, [4]) == 18 + 19 * 4
+    assert bench.batched_launches(5, 2, True, True, [(7, 1), (9, 0)]) == \
+        (6 + 5 * 8 + 3) + (18 + 10 * 7 + 7) + (18 + 10 * 9)
+    assert bench.batched_launches(0, 0, False, False, [(4, 2)]) == 18 + 10 * 4 + 7 * 2
 
 
 def test_oracle_thread_count_is_restored():

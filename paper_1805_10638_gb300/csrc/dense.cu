@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     const CUtensorMap* tmCl = &tm.cl[set];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nct = a.Kpad / TN;
-    const int ntiles = (int)((a.N + TM - 1) / TM);
+    const int64_t nrows = a.nrows ? (int64_t)*a.nrows : a.N;   // rows of the tiles (compacted or all)
+    const int ntiles = (int)((nrows + TM - 1) / TM);
     constexpr uint32_t XCHUNK = TM * 128, CCHUNK = TN * 128;
 
     if (tid == 0) {
@@ -495,13 +496,22 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     }
                 }
                 const int64_t row = (int64_t)tile * TM + r;
-                if (row < a.N) {
+                if (row < nrows) {
+                    const int64_t orow = a.map ? (int64_t)a.map[row] : row;    // the row of X
                     // ||x|| <= ||x_hi|| / (1 - u_b) is folded into bcoef_a
                     const float bnd = a.bcoef_a * sqrtf(xs) * cmax + a.bcoef_b * cmax2;
-                    rho[row] = i1;
-                    if (!(v2 - v1 > 2.02f * bnd)) {          // near tie: rescore the row over all K in FP32
+                    rho[orow] = i1;
+                    const bool tie = !(v2 - v1 > 2.02f * bnd);
+                    if (a.hub) {
+                        // Hamerly bounds from the scores: d_j^2 = s_j + ||x||^2, each score within bnd, and
+                        // ||x||^2 in FP32 within 1e-5 of itself; a near tie (the rescan decides) gets l = 0
+                        const float xn = a.xn2[orow], e = bnd + 1e-5f * xn;
+                        a.hub[orow] = sqrtf(fmaxf(0.f, v1 + xn + e)) * (1.f + 1e-6f);
+                        a.hlb[orow] = tie ? 0.f : sqrtf(fmaxf(0.f, v2 + xn - e)) * (1.f - 1e-6f);
+                    }
+                    if (tie) {                              // near tie: rescore the row over all K in FP32
                         const unsigned pos = atomicAdd(a.qcount, 1u);
-                        a.queue[pos] = (int)row;
+                        a.queue[pos] = (int)orow;
                         reinterpret_cast<unsigned long long*>(a.rkey)[pos] = ~0ull;
                     }
                 }
@@ -739,6 +749,133 @@ __global__ void __launch_bounds__(256) k_rescore_full(DenseArgs a)
     }
 }
 
+// ------------------------------------------------------------------ Hamerly bounds (solver passes)
+// Per pass, before the assignment: each centroid's drift since the last pass (one warp per
+// centroid; the last-pass copy is replaced by the current centroids in the same sweep), then per
+// row Hamerly's test: the assigned centroid stays the nearest when u + drift_a is below
+// l - (largest drift of the other centroids) by a relative margin of 1e-5 (far beyond FP32
+// rounding, so the rescan of a near tie would pick the same centroid); such rows keep their label
+// and their decayed bounds, the others are listed (map) and their BF16 parts copied into compact
+// buffers for the tensor-core pass.
+__global__ void __launch_bounds__(256) k_ddrift(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.nrows) *a.nrows = 0u;
+    const int lane = threadIdx.x & 31, d = a.d;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= a.K) return;
+    const float* c = a.c32[set] + (size_t)j * d;
+    float* h = a.hlast + (size_t)j * d;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const float ck = c[k];
+        const float t = ck - h[k];
+        s = fmaf(t, t, s);
+        h[k] = ck;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) a.drift[j] = a.mode == MODE_INIT ? 0.f : sqrtf(s) * (1.f + 1e-5f) + 1e-30f;
+}
+
+__global__ void __launch_bounds__(256) k_dbound(DenseArgs a)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, K = a.K;
+    // the two largest drifts and the index of the largest
+    __shared__ float s_v1[8], s_v2[8];
+    __shared__ int s_i1[8];
+    float m1 = 0.f, m2 = 0.f;
+    int i1 = 0;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const float v = a.drift[j];
+        if (v > m1) {
+            m2 = m1;
+            m1 = v;
+            i1 = j;
+        } else {
+            m2 = fmaxf(m2, v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float o1 = __shfl_xor_sync(FULL, m1, o), o2 = __shfl_xor_sync(FULL, m2, o);
+        const int oi = __shfl_xor_sync(FULL, i1, o);
+        if (o1 > m1 || (o1 == m1 && oi < i1)) {
+            m2 = fmaxf(m1, o2);
+            m1 = o1;
+            i1 = oi;
+        } else {
+            m2 = fmaxf(m2, o1);
+        }
+    }
+    if (lane == 0) {
+        s_v1[w] = m1;
+        s_v2[w] = m2;
+        s_i1[w] = i1;
+    }
+    __syncthreads();
+    m1 = s_v1[0];
+    m2 = s_v2[0];
+    i1 = s_i1[0];
+    for (int ww = 1; ww < 8; ++ww) {
+        if (s_v1[ww] > m1 || (s_v1[ww] == m1 && s_i1[ww] < i1)) {
+            m2 = fmaxf(m1, s_v2[ww]);
+            m1 = s_v1[ww];
+            i1 = s_i1[ww];
+        } else {
+            m2 = fmaxf(m2, s_v1[ww]);
+        }
+    }
+    // REVERT: the labels and bounds the TRIAL pass left (relative to its centroids)
+    const int32_t* rho_last = a.mode == MODE_TRIAL ? a.rho_pair[st->cur ^ 1] : a.rho_pair[st->cur];
+    int32_t* rho_out = a.rho_pair[st->cur];
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.N; i0 += T) {
+        const int64_t i = i0 + threadIdx.x;
+        bool scan = false;
+        if (i < a.N) {
+            const int al = rho_last[i];
+            const float u = (a.hub[i] + a.drift[al]) * (1.f + 2e-7f);
+            const float l = (a.hlb[i] - (al == i1 ? m2 : m1)) * (1.f - 2e-7f);
+            if (u * (1.f + 1e-5f) < l) {
+                rho_out[i] = al;
+                a.hub[i] = u;
+                a.hlb[i] = l;
+            } else {
+                scan = true;
+            }
+        }
+        const unsigned bal = __ballot_sync(FULL, scan);
+        if (bal) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(a.nrows, (unsigned)__popc(bal));
+            base = __shfl_sync(FULL, base, 0);
+            if (scan) a.map[base + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+        }
+    }
+}
+
+// The BF16 hi and lo parts of the listed rows into the compact buffers (row p <- row map[p]); one
+// warp per row, 16-byte copies (d * 2 bytes per part, d % 8 == 0).
+__global__ void __launch_bounds__(256) k_dgather(DenseArgs a, const uint4* Xh, const uint4* Xl, uint4* Ch, uint4* Cl)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, q = a.d / 8;      // uint4 per row per part
+    const int64_t n = (int64_t)*a.nrows;
+    for (int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); p < n; p += (int64_t)gridDim.x * 8) {
+        const int64_t r = a.map[p];
+        for (int t = lane; t < 2 * q; t += 32) {
+            if (t < q) Ch[p * q + t] = __ldg(Xh + r * q + t);
+            else Cl[p * q + (t - q)] = __ldg(Xl + r * q + (t - q));
+        }
+    }
+}
+
 // Labels of the rescored rows from their (distance, index) keys.
 __global__ void __launch_bounds__(256) k_rescore_write(DenseArgs a)
 {
@@ -807,10 +944,11 @@ __global__ void __launch_bounds__(256) k_xsplit(const float* X, const __nv_bfloa
     }
 }
 
-// Once per solve: the non-finite check of X and the largest ||x|| (FP32 bits into *xmax: the norms
+// Once per solve: the non-finite check of X, the largest ||x|| (FP32 bits into *xmax: the norms
 // are non-negative, so their bits order like the values), which bounds the update's fixed-point
-// sums.  One warp per row, lane l on dimensions 4l..4l+3 (d <= 128, d % 8 == 0), four rows in flight.
-__global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st)
+// sums, and every ||x||^2 (for the Hamerly bounds).  One warp per row, lane l on dimensions 4l..4l+3 (d <= 128, d % 8 == 0), four rows in flight.
+__global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2,
+                                                SolveState* st)
 {
     const int lane = threadIdx.x & 31;
     const bool act = 4 * lane < d;
@@ -833,6 +971,7 @@ __global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
             mx = fmaxf(mx, sq);
+            if (xn2 && lane == 0 && i0 + u * W < N) xn2[i0 + u * W] = sq;
         }
     }
     if (__any_sync(FULL, bad) && lane == 0 && st) st->status = KM_ENONFINITE;
@@ -1057,7 +1196,10 @@ __device__ __forceinline__ void dseg_finish(const DenseArgs& a, int nbk, int nse
             if (a.out_E) *a.out_E = E;
             if (a.out_nch) *a.out_nch = ch;
         } else {
-            if (a.mode != MODE_EPI) st->rescored += a.qcount[0];
+            if (a.mode != MODE_EPI) {
+                st->rescored += a.qcount[0];
+                st->scanned += a.nrows ? (long long)*a.nrows : a.N;   // rows the tensor-core pass scored
+            }
             if (a.mode == MODE_EPI) {
                 st->E_final = E;
             } else if (a.mode == MODE_INIT) {
@@ -1351,6 +1493,19 @@ bool make_tmap_bf16(void* map, const void* base, int64_t rows, int cols, int box
     return r == CUDA_SUCCESS;
 }
 
+cudaError_t launch_dense_bounds(const DenseArgs& a, const void* Xh, const void* Xl, void* Ch, void* Cl, int nsm,
+                                cudaStream_t s)
+{
+    k_ddrift<<<(a.K + 7) / 8, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.mode == MODE_INIT) return e;
+    k_dbound<<<nsm * 8, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_dgather<<<nsm * 8, 256, 0, s>>>(a, reinterpret_cast<const uint4*>(Xh), reinterpret_cast<const uint4*>(Xl),
+                                       reinterpret_cast<uint4*>(Ch), reinterpret_cast<uint4*>(Cl));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm, cudaStream_t s)
 {
     // assignment
@@ -1359,7 +1514,7 @@ cudaError_t launch_dense_pass(const DenseArgs& a, const DenseMaps& maps, int nsm
     const size_t smem = dense_assign_smem(a.dpad, a.Kpad);
     e = cudaFuncSetAttribute(k_dense_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int ntiles = (int)((a.N + TM - 1) / TM);
+    const int ntiles = (int)((a.N + TM - 1) / TM);         // at most (a compacted pass has fewer)
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_dense_assign<<<grid, DTHREADS, smem, s>>>(maps, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1420,9 +1575,10 @@ cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st, int nsm, cudaStream_t s)
+cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2, SolveState* st, int nsm,
+                          cudaStream_t s)
 {
-    k_xcheck<<<nsm * 8, 256, 0, s>>>(X, N, d, xmax, st);
+    k_xcheck<<<nsm * 8, 256, 0, s>>>(X, N, d, xmax, xn2, st);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,14 @@ struct DenseArgs {
                               // (FP32 bits), [3]: the pass's fixed-point scale exponent, [4]: max ||x||
                               // (FP32 bits, from k_xcheck)
     int prescaled;            // solver: the scale comes from max ||x|| and max ||c|| before the sums
+    // Hamerly bounds (solver passes; NULL hub: none)
+    float* hub;               // [N] upper bound on the distance to the assigned centroid
+    float* hlb;               // [N] lower bound on the distance to every other centroid
+    const float* xn2;         // [N] ||x||^2 (FP32)
+    float* hlast;             // [K][d] the centroids the bounds refer to (the last pass's)
+    float* drift;             // [K] drift of each centroid since the last pass
+    int* map;                 // [N] rows to scan, compacted (NULL: every row, in order)
+    unsigned int* nrows;      // number of rows in map (NULL: N)
     double* out_E;
     long long* out_nch;
     // controller
@@ -93,6 +101,11 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
 cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s);
 cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,
                         cudaStream_t s);
-cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, SolveState* st, int nsm, cudaStream_t s);
+cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2, SolveState* st, int nsm,
+                          cudaStream_t s);
+// Hamerly bounds of a solver pass: drifts; then (TRIAL, REVERT) the test per row, the list of rows to
+// scan and their BF16 parts copied into the compact buffers Ch, Cl ([N][d] each)
+cudaError_t launch_dense_bounds(const DenseArgs& a, const void* Xh, const void* Xl, void* Ch, void* Cl, int nsm,
+                                cudaStream_t s);
 
 }  // namespace km

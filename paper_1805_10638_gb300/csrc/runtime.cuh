@@ -41,7 +41,7 @@ struct Plan {
     size_t hX, hXb, hC0, hCout, hRho;   // device copies for kmeans_solve_host
     // dense path (tensor-core assignment, sort-based update)
     size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
-        part, pe, pnch, rowe, rown;
+        part, pe, pnch, rowe, rown, xn2, drift, map, nrows, xch, xcl;
     size_t total;
     int nb, nfin, KB, Kpad, DP;
     bool dense;
@@ -196,6 +196,17 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.pe = take((size_t)P.max_chunks * 8);
     P.pnch = take((size_t)P.nbk * 8);
     P.acc = take(n * 8 + (size_t)K * 4);     // fixed-point residual sums + counts of a pass
+    // Hamerly bounds of the solver passes: per-row bounds and norms, the last pass's centroids and
+    // their drifts, the rows to scan and their BF16 parts in compact buffers
+    P.hub = take((size_t)N * 4);
+    P.hlb = take((size_t)N * 4);
+    P.xn2 = take((size_t)N * 4);
+    P.hlast = take(n * 4);
+    P.drift = take((size_t)K * 4);
+    P.map = take((size_t)N * 4);
+    P.nrows = take(256);
+    P.xch = take((size_t)N * d * 2);
+    P.xcl = take((size_t)N * d * 2);
     P.rowe = take(4096 * 8);
     P.rown = take(4096 * 8);
     P.pS = 0;
@@ -479,6 +490,12 @@ struct Launch {
     const float* X32;
     int nsm;
     DenseMaps maps;
+    DenseMaps maps_c;            // the same over the compact buffers of the rows a bounded pass scans
+    bool dbounds = false;        // Hamerly bounds on the dense solver passes
+    int* dmap = nullptr;         // their list of rows to scan, its length and the compact BF16 buffers
+    unsigned int* dnrows = nullptr;
+    void* dxch = nullptr;
+    void* dxcl = nullptr;
     const void* xlo = nullptr;   // the low BF16 part of X the passes read
     bool xsplit = false;         // the prologue computes it into the workspace
     bool maps_ok = true;
@@ -704,7 +721,20 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
         L.pk.check_done = 1;
         L.xlo = dense_xlo(base, P, X);
         L.xsplit = X->X_bf16_lo == nullptr;
-        L.maps_ok = dense_maps(base, P, X->X_bf16, L.xlo, X->N, d, &L.maps);
+        L.maps_ok = dense_maps(base, P, X->X_bf16, L.xlo, X->N, d, &L.maps) &&
+                    dense_maps(base, P, at<void>(base, P.xch), at<void>(base, P.xcl), X->N, d, &L.maps_c);
+        L.dbounds = hamerly_mode();
+        if (L.dbounds) {
+            L.dmap = at<int>(base, P.map);
+            L.dnrows = at<unsigned int>(base, P.nrows);
+            L.dxch = at<void>(base, P.xch);
+            L.dxcl = at<void>(base, P.xcl);
+            da.hub = at<float>(base, P.hub);
+            da.hlb = at<float>(base, P.hlb);
+            da.xn2 = at<float>(base, P.xn2);
+            da.hlast = at<float>(base, P.hlast);
+            da.drift = at<float>(base, P.drift);
+        }
     }
     return L;
 }
@@ -766,7 +796,20 @@ cudaError_t dense_pass(const Launch& L, int mode, int use_cond, cudaGraphConditi
     a.use_cond_rev = use_rev;
     a.cond_rev = hr;
     cudaError_t e = cudaSuccess;
-    if (assign) e = launch_dense_pass(a, L.maps, L.nsm, s);
+    const bool bounded = assign && L.dbounds && (mode == MODE_INIT || mode == MODE_TRIAL || mode == MODE_REVERT);
+    if (!bounded) {
+        a.hub = a.hlb = nullptr;
+        if (assign) e = launch_dense_pass(a, L.maps, L.nsm, s);
+    } else if (mode == MODE_INIT) {     // every row scanned; the bounds and the last centroids set
+        e = launch_dense_bounds(a, nullptr, nullptr, nullptr, nullptr, L.nsm, s);
+        if (e == cudaSuccess) e = launch_dense_pass(a, L.maps, L.nsm, s);
+    } else {                            // the rows the bounds cannot keep, compacted
+        a.map = L.dmap;
+        a.nrows = L.dnrows;
+        e = launch_dense_bounds(a, a.Xb, L.xlo, L.dxch, L.dxcl, L.nsm, s);
+        if (e == cudaSuccess) e = launch_dense_pass(a, L.maps_c, L.nsm, s);
+        a.map = nullptr;                // the update reads only the count (rows scanned, for the info)
+    }
     if (e == cudaSuccess) e = launch_dense_update(a, L.P.nbk, L.P.max_chunks, s);
     return e;
 }
@@ -781,7 +824,8 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
         if (e == cudaSuccess)
             e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
                             nullptr, L.st, L.p.m_init, L.m_max, s, 0);
-        if (e == cudaSuccess) e = launch_xcheck(L.X32, L.N, L.d, L.da.counter + 4, L.st, L.nsm, s);
+        if (e == cudaSuccess)
+            e = launch_xcheck(L.X32, L.N, L.d, L.da.counter + 4, const_cast<float*>(L.da.xn2), L.st, L.nsm, s);
         if (e == cudaSuccess && L.xsplit)
             e = launch_xsplit(L.X32, L.da.Xb, const_cast<void*>(L.xlo), L.N * (int64_t)L.d, L.nsm, s);
         PackArgs pk = L.pk;

@@ -147,3 +147,31 @@ def test_dense_full_size_against_the_oracles_solves(ctx):
     _, _, ia = km.kmeans_solve(ctx, Xd, Cd, X_bf16=Xbd, m_max=10)
     assert ia["converged"] == 1
     assert abs(ia["E"] - g["aa"]["E"]) <= 1e-6 * g["aa"]["E"], (ia, g["aa"])
+
+
+@pytest.mark.parametrize("shape", [(20_000, 64, 64, 7), (30_000, 128, 300, 8), (12_000, 96, 1024, 9)])
+@pytest.mark.parametrize("lloyd", [False, True])
+def test_dense_bounds_change_nothing(shape, lloyd, monkeypatch):
+    """Hamerly bounds on the tensor-core solver passes: a row keeps its label without the scan only
+    when its bounds prove it by a relative margin far beyond FP32 rounding, so the solve is bitwise
+    the one that scans every row (KM_HAMERLY=0), for Lloyd and for Algorithm 1."""
+    need_gpu()
+    N, d, K, seed = shape
+    X, Xb, C0 = dense_data(N, d, K, seed)
+    kw = dict(lloyd_only=1) if lloyd else dict(m_max=10)
+
+    def run():
+        c = km.Context(0)
+        C, rho, info = km.kmeans_solve(c, dev(X), dev(C0), X_bf16=dev_bf16(Xb), **kw)
+        torch.cuda.synchronize()
+        out = (C.cpu().numpy(), rho.cpu().numpy(), info)
+        c.close()
+        return out
+
+    with_b = run()
+    monkeypatch.setenv("KM_HAMERLY", "0")
+    without = run()
+    assert with_b[0].tobytes() == without[0].tobytes()
+    assert np.array_equal(with_b[1], without[1])
+    for f in ("iters", "accepted", "rejected", "assign_passes", "converged", "E", "status"):
+        assert with_b[2][f] == without[2][f], (f, with_b[2], without[2])

@@ -76,12 +76,13 @@ def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool, rejected
     """Kernels one solve launches.  Low-d: the prologue (k_prep, [k_hprep], INIT pass, k_fin,
     [k_mix]), per loop pass the same with the TRIAL and REVERT passes in place of the INIT pass,
     and the epilogue (EPI pass, k_epi); k_hprep with Hamerly bounds, k_mix unless the mix is fused
-    into k_fin.  Dense: 13 in the prologue (k_prep, k_xcheck, two packings, the INIT chain of 7:
-    assignment, rescan, rescan labels, count, scan, scatter, segment sums; k_fin, k_mix), per loop
-    pass 10 (the TRIAL chain, k_fin, k_mix, the packing) plus the REVERT chain's 7 when the
-    safeguard fired (it sits in a conditional node otherwise), 5 in the epilogue."""
+    into k_fin.  Dense (with its Hamerly bounds): 14 in the prologue (k_prep, k_xcheck, two
+    packings, the INIT chain of 8: drifts, assignment, rescan, rescan labels, count, scan, scatter,
+    segment sums; k_fin, k_mix), per loop pass 13 (the TRIAL chain of 10: drifts, bounds test, row
+    gather and the 7 of the INIT chain; k_fin, k_mix, the packing) plus the REVERT chain's 10 when
+    the safeguard fired (it sits in a conditional node otherwise), 5 in the epilogue."""
     if dense:
-        return 18 + 10 * iters + 7 * rejected
+        return 19 + 13 * iters + 10 * rejected
     per = 3 + int(ham) + int(not fused_mix)
     return per * (iters + 1) + 2
 

@@ -96,7 +96,7 @@ def test_solve_launch_count():
     # lowd_2m: Hamerly bounds, separate mix -> 5 kernels in the prologue and per loop pass, 2 after
     assert bench.solve_launches(152, dense=False, ham=True, fused_mix=False) == 5 * 153 + 2
     assert bench.solve_launches(10, dense=False, ham=False, fused_mix=True) == 3 * 11 + 2
-    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23) == 18 + 10 * 160 + 7 * 23
+    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23) == 19 + 13 * 160 + 10 * 23
 
 
 def test_same_energy_speed():
@@ -111,8 +111,8 @@ def test_batched_launch_count():
     assert bench.batched_launches(10, 3, True, True, []) == 7 + 10 * 10 + 4
     assert bench.batched_launches(10, 3, False, False, []) == 5 + 10 * 8 + 4
     assert bench.batched_launches(5, 2, True, True, [(7, 1), (9, 0)]) == \
-        (6 + 5 * 8 + 3) + (18 + 10 * 7 + 7) + (18 + 10 * 9)
-    assert bench.batched_launches(0, 0, False, False, [(4, 2)]) == 18 + 10 * 4 + 7 * 2
+        (6 + 5 * 8 + 3) + (19 + 13 * 7 + 10) + (19 + 13 * 9)
+    assert bench.batched_launches(0, 0, False, False, [(4, 2)]) == 19 + 13 * 4 + 10 * 2
 
 
 def test_oracle_thread_count_is_restored():

@@ -112,8 +112,8 @@ typedef struct {
  *   ls_qr_solves   least-squares solves (Eq. 7) that took the Householder QR route because the
  *                  Cholesky factor of the Gram matrix could not be certified (see kmeans_params)
  *   scanned_rows   rows whose assignment took a scan over all K centroids, summed over the passes
- *                  (the rest were settled by Hamerly bounds: FP32 low-d and tensor-core solver
- *                  passes; the FP64 path reports 0) */
+ *                  (the rest were settled by the Hamerly bounds of the FP32 low-d and the
+ *                  tensor-core solver passes) */
 typedef struct {
     int32_t iters;
     int32_t accepted;

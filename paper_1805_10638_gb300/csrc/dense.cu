@@ -45,7 +45,6 @@ constexpr int CSLOT = 4;           // centroid ring slots (one K-block of the hi
 constexpr int DTHREADS = 576;      // 18 warps: TMA, MMA, 16 epilogue
 constexpr int SEG = 64;            // rows per segment-sum chunk
 constexpr int MREC = 3;            // floats per row and column quarter in the merge buffer (v1, v2, i1)
-constexpr int MAXKB = 2;           // K-blocks of 64 (d <= 128)
 constexpr unsigned SPIN_LIMIT = 1u << 28;
 
 // ------------------------------------------------------------------ PTX wrappers

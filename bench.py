@@ -72,7 +72,13 @@ def profiled_traffic(name: str):
     return None
 
 
-def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool, rejected: int = 0) -> int:
+def dense_inc() -> bool:
+    """The dense solver passes' incremental update (KM_DINC=0 switches it off)."""
+    return not os.environ.get("KM_DINC", "1").startswith("0")
+
+
+def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool, rejected: int = 0,
+                   inc: bool = True) -> int:
     """Kernels one solve launches.  Low-d: the prologue (k_prep, [k_hprep], INIT pass, k_fin,
     [k_mix]), per loop pass the same with the TRIAL and REVERT passes in place of the INIT pass,
     and the epilogue (EPI pass, k_epi); k_hprep with Hamerly bounds, k_mix unless the mix is fused
@@ -80,9 +86,12 @@ def solve_launches(iters: int, dense: bool, ham: bool, fused_mix: bool, rejected
     packings, the INIT chain of 8: drifts, assignment, rescan, rescan labels, count, scan, scatter,
     segment sums; k_fin, k_mix), per loop pass 13 (the TRIAL chain of 10: drifts, bounds test, row
     gather and the 7 of the INIT chain; k_fin, k_mix, the packing) plus the REVERT chain's 10 when
-    the safeguard fired (it sits in a conditional node otherwise), 5 in the epilogue."""
+    the safeguard fired (it sits in a conditional node otherwise), 5 in the epilogue.  The
+    incremental update adds three kernels to every INIT, TRIAL and REVERT chain (the changed-row
+    list, their sums, the new sums with the energy)."""
     if dense:
-        return 19 + 13 * iters + 10 * rejected
+        k = 3 if inc else 0
+        return 19 + k + (13 + k) * iters + (10 + k) * rejected
     per = 3 + int(ham) + int(not fused_mix)
     return per * (iters + 1) + 2
 
@@ -95,7 +104,7 @@ def batched_launches(loops: int, ngrp: int, ham: bool, mix: bool, dense_iters) -
     group, k_epi_batch); plus one tensor-core chain per dense instance."""
     h, m = int(ham), int(mix)
     lowd = (2 + h + ngrp + m) + loops * (h + 2 * ngrp + 2 + m) + ngrp + 1 if ngrp else 0
-    return lowd + sum(solve_launches(it, True, False, False, rj) for it, rj in dense_iters)
+    return lowd + sum(solve_launches(it, True, False, False, rj, dense_inc()) for it, rj in dense_iters)
 
 
 def same_energy_speed(ms_aa, ms_ll, E_aa, E_ll, rtol: float = 1e-6):
@@ -828,7 +837,7 @@ def run_ours(args, rank, world, local_rank):
 
     # our kernels in the timed Algorithm 1 solves (Hamerly bounds are on when a pass skipped rows)
     ham = (not dense) and any(i["scanned_rows"] < i["assign_passes"] * N for i in inf_aa)
-    launches = sum(solve_launches(i["iters"], dense, ham, K * d <= 64, i["rejected"]) for i in inf_aa)
+    launches = sum(solve_launches(i["iters"], dense, ham, K * d <= 64, i["rejected"], dense_inc()) for i in inf_aa)
     if rank == 0:
         E_aa = np.array([i["E"] for i in inf_aa])
         E_ll = np.array([i["E"] for i in inf_ll])

@@ -356,7 +356,12 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
     // FP32 solver passes after the first (d <= FX_MAX_D), and every dense update, sum in 64-bit
     // fixed point (scale 2^fx_s) straight into the totals acc / accC: read once, converted to FP64 once, and
     // cleared for the next pass.  Counts of the other passes are summed as integers.
-    const bool fxp = a.acc && (a.part_fx == 2 || (a.part_fx == 1 && solver && a.mode != MODE_INIT));
+    // the incremental update (dense solver passes) keeps raw sums of x per cluster instead of the
+    // residuals' sums: F = S / N_j - c there
+    const bool raw = solver && a.inc && a.part_fx == 2;
+    const long long* accp = raw ? a.Spair[st->cur] : a.acc;
+    const int32_t* accCp = raw ? a.Npair[st->cur] : a.accC;
+    const bool fxp = accp && (a.part_fx == 2 || (a.part_fx == 1 && solver && a.mode != MODE_INIT));
     const int fxs = fxp ? (a.fxs_ptr ? *a.fxs_ptr : st->fx_s) : 0;
     long long* s_ipart = reinterpret_cast<long long*>(s_part);
     const size_t Kd = (size_t)K * d;
@@ -369,12 +374,12 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
         double acc = 0.0;
         if (e < kb * d) {
             const size_t off = (size_t)j0 * d + e;
-            if (fxp) is = sp == 0 ? a.acc[off] : 0;       // the pass's exact total
+            if (fxp) is = sp == 0 ? accp[off] : 0;        // the pass's exact total
             else if (a.part_f64) acc = strided_sum<double, double>(reinterpret_cast<const double*>(a.pS) + off, Kd, sp, nb, split);
             else acc = strided_sum<float, double>(reinterpret_cast<const float*>(a.pS) + off, Kd, sp, nb, split);
         } else {
             const int j = j0 + (e - kb * d);
-            is = fxp ? (sp == 0 ? (long long)a.accC[j] : 0) : strided_sum<int32_t, long long>(a.pCnt + j, (size_t)K, sp, nb, split);
+            is = fxp ? (sp == 0 ? (long long)accCp[j] : 0) : strided_sum<int32_t, long long>(a.pCnt + j, (size_t)K, sp, nb, split);
         }
         if (split == 1)
             s_tot[e] = !isum ? acc : (e >= kb * d ? (double)is : ldexp((double)is, -fxs));
@@ -384,7 +389,7 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
             s_part[e * split + sp] = acc;
     }
     __syncthreads();
-    if (fxp) {                                   // read by this block only: clear for the next pass
+    if (fxp && !raw) {                           // read by this block only: clear for the next pass
         for (int e = tid; e < kb * d; e += blockDim.x) a.acc[(size_t)j0 * d + e] = 0;
         for (int e = tid; e < kb; e += blockDim.x) a.accC[j0 + e] = 0;
     }
@@ -435,8 +440,9 @@ __device__ __forceinline__ void fin_body(const FinArgs& a, const int bid, const 
     const size_t n = (size_t)K * d;
     for (int e = tid; e < kb * d; e += blockDim.x) {
         const size_t i = (size_t)j0 * d + e;
-        const double F = s_tot[e] * s_part[e / d];
         const double c = Ct[i];
+        const double inv = s_part[e / d];
+        const double F = !raw ? s_tot[e] * inv : (inv > 0.0 ? s_tot[e] * inv - c : 0.0);
         const double G = c + F;
         if (ring) {
             const double dfn = F - a.Fprev[i];

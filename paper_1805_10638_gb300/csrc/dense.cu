@@ -26,6 +26,8 @@
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
 // fixed-order segment sums of the residuals x_i - c_j per cluster (FP32 within chunks of 64 rows,
 // FP64 across chunks).  The energy (Eq. 1) comes out of the same segment sums.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -946,8 +948,12 @@ __global__ void __launch_bounds__(256) k_xsplit(const float* X, const __nv_bfloa
 // Once per solve: the non-finite check of X, the largest ||x|| (FP32 bits into *xmax: the norms
 // are non-negative, so their bits order like the values), which bounds the update's fixed-point
 // sums, and every ||x||^2 (for the Hamerly bounds).  One warp per row, lane l on dimensions 4l..4l+3 (d <= 128, d % 8 == 0), four rows in flight.
+// With qx: also sum_i ||x_i||^2 for the energy of the incremental update.  Each lane keeps a
+// double-float sum (hi + lo, FP32) of the exact squares x^2 = p + e (p = fl(x^2), e = fma(x, x, -p));
+// the lanes, warps and blocks are added in a fixed order (block partials in qx[1..], the last block
+// to finish sums them into qx[0]), so the result does not depend on scheduling.
 __global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2,
-                                                SolveState* st)
+                                                SolveState* st, double* qx, unsigned int* qctr)
 {
     const int lane = threadIdx.x & 31;
     const bool act = 4 * lane < d;
@@ -956,6 +962,7 @@ __global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d
     const float* Xl = X + 4 * lane;
     int bad = 0;
     float mx = 0.f;
+    f2sum q2{0.f, 0.f};
     for (int64_t i0 = w0; i0 < N; i0 += 4 * W) {
         float4 xv[4];
 #pragma unroll
@@ -966,6 +973,15 @@ __global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             bad |= !isfinite(xv[u].x) | !isfinite(xv[u].y) | !isfinite(xv[u].z) | !isfinite(xv[u].w);
+            if (qx) {
+                const float v[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float p = v[t] * v[t];
+                    two_sum_add(q2, p);
+                    q2.lo += fmaf(v[t], v[t], -p);
+                }
+            }
             float sq = fmaf(xv[u].x, xv[u].x, fmaf(xv[u].y, xv[u].y, fmaf(xv[u].z, xv[u].z, xv[u].w * xv[u].w)));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(FULL, sq, o);
@@ -975,14 +991,58 @@ __global__ void __launch_bounds__(256) k_xcheck(const float* X, int64_t N, int d
     }
     if (__any_sync(FULL, bad) && lane == 0 && st) st->status = KM_ENONFINITE;
     if (lane == 0 && mx > 0.f) atomicMax(xmax, __float_as_uint(sqrtf(mx) * (1.f + 1e-5f)));
+    if (!qx) return;
+    const f2sum wq = warp_sum_f2(q2);
+    __shared__ double s_q[8];
+    if (lane == 0) s_q[threadIdx.x >> 5] = (double)wq.hi + (double)wq.lo;
+    __syncthreads();
+    __shared__ unsigned int s_last;
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_q[w];
+        qx[1 + blockIdx.x] = b;
+        __threadfence();
+        s_last = (atomicAdd(qctr, 1u) == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(qx + 1 + b);
+    qx[0] = t;
+    *qctr = 0u;
 }
 
 // ------------------------------------------------------------------ update chain
+// A solver pass with the incremental update (INIT, TRIAL, REVERT; the final energy pass and the
+// standalone calls keep the sorted chain).
+__device__ __forceinline__ bool inc_pass(const DenseArgs& a)
+{
+    return a.inc && (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
+}
+// Scale exponent F of the incremental sums, fixed for the solve: every |x| <= max ||x||, so a
+// cluster's sum of round(x * 2^F), and a pass's change of it, stay below 2^62 in magnitude.
+__device__ __forceinline__ int inc_scale(const DenseArgs& a)
+{
+    const double rb = (double)a.N * (double)__uint_as_float(__ldcg(a.counter + 4));
+    int F = rb > 0.0 ? 60 - ilogb(rb) : 0;
+    return F > 100 ? 100 : (F < -100 ? -100 : F);
+}
+// One component in the incremental sums' fixed point (x * 2^F is exact in FP32; the conversion
+// rounds only components below 2^-F).  The incremental and the full paths both use it, so they give
+// the same integers.
+__device__ __forceinline__ long long inc_q(float v, float fxf) { return __float2ll_rn(v * fxf); }
+// The sorted chain runs in an incremental pass only when that pass rebuilds the sums in full.
+__device__ __forceinline__ bool sorted_chain_idle(const DenseArgs& a)
+{
+    return inc_pass(a) && __ldcg(a.counter + 7) == 0u;
+}
+
 // 1. Per-block label histograms (integer atomics, order-independent) and the change count.
 __global__ void __launch_bounds__(256) k_dcount(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
-    if (set < 0) return;
+    if (set < 0 || sorted_chain_idle(a)) return;
     extern __shared__ int s_hist[];
     const int K = a.K;
     for (int j = threadIdx.x; j < K; j += blockDim.x) s_hist[j] = 0;
@@ -1017,7 +1077,7 @@ __global__ void __launch_bounds__(256) k_dcount(DenseArgs a)
 __global__ void __launch_bounds__(256) k_dscan(DenseArgs a, int nbk)
 {
     const int set = pass_set(a.st, a.mode);
-    if (set < 0) return;
+    if (set < 0 || sorted_chain_idle(a)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, K = a.K;
     const int j = blockIdx.x * 8 + w;
     if (j < K) {
@@ -1120,7 +1180,7 @@ __global__ void __launch_bounds__(256) k_dscan(DenseArgs a, int nbk)
 __global__ void __launch_bounds__(32) k_dscatter(DenseArgs a)
 {
     const int set = pass_set(a.st, a.mode);
-    if (set < 0) return;
+    if (set < 0 || sorted_chain_idle(a)) return;
     extern __shared__ int s_run[];   // [K] running positions, then [rows_per_block] labels
     int* s_lab = s_run + a.K;
     const int lane = threadIdx.x, K = a.K;
@@ -1191,6 +1251,8 @@ __device__ __forceinline__ void dseg_finish(const DenseArgs& a, int nbk, int nse
         *a.counter = 0u;
         a.counter[2] = 0u;                         // max |partial| of the next pass
         a.counter[3] = (unsigned int)fxs;          // read by k_fin
+        a.counter[6] = 0u;                         // the incremental update's list and mode
+        a.counter[7] = 0u;
         if (a.mode == MODE_STANDALONE) {
             if (a.out_E) *a.out_E = E;
             if (a.out_nch) *a.out_nch = ch;
@@ -1215,8 +1277,9 @@ __device__ __forceinline__ void dseg_finish(const DenseArgs& a, int nbk, int nse
             }
         }
     }
-    // the safeguard fired: the REVERT pass adds into cleared totals
-    if (a.mode == MODE_TRIAL) {
+    // the safeguard fired: the REVERT pass adds into cleared totals (the incremental update instead
+    // starts again from the sums of the last pass's partition)
+    if (a.mode == MODE_TRIAL && !a.inc) {
         __syncthreads();
         if (st->revert && !st->done) {
             const size_t n = (size_t)K * d;
@@ -1371,6 +1434,212 @@ __global__ void __launch_bounds__(256) k_dsegfin(DenseArgs a, int nbk, int nseg)
             a.accC[jj] = a.counts[jj];
     }
     dseg_finish(a, nbk, nseg, fxs);
+}
+
+// ------------------------------------------------------------------ incremental update (solver)
+// The integer sums of a partition change only where labels change: a pass starts from the sums of
+// the last pass's partition (Spair[cur ^ 1], the labels in rho_pair[cur ^ 1]) and adds the rows
+// whose label moved.  Every term is round(x * 2^F) in 64-bit integers, so the sums are exact and
+// equal to a full recomputation whatever the order of the additions.
+
+// 1. (grid: the nbk row blocks of k_dcount) Clears the pass's deltas, lists the rows whose label
+//    differs from the last pass's in perm (warp-aggregated appends; their order is irrelevant) and
+//    writes the per-block change counts that dseg_finish adds up.  The last block picks the path:
+//    a full rebuild through the sorted chain in the INIT pass and when more than inc_cap rows
+//    changed, else the list.
+__global__ void __launch_bounds__(256) k_dinc_list(DenseArgs a)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t nS = (size_t)a.K * a.d;
+    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = gt; i < nS; i += gs) a.dS[i] = 0;
+    for (size_t j = gt; j < (size_t)a.K; j += gs) a.dN[j] = 0;
+    const bool init = a.mode == MODE_INIT;
+    long long nch = 0;
+    if (!init) {
+        const int32_t* rho = a.rho_pair[st->cur];
+        const int32_t* prev = a.rho_pair[st->cur ^ 1];
+        const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_block;
+        const int64_t r1 = min(a.N, r0 + a.rows_per_block);
+        for (int64_t i0 = r0; i0 < r1; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            const bool ch = i < r1 && rho[i] != prev[i];
+            const unsigned m = __ballot_sync(FULL, ch);
+            if (m) {
+                unsigned base = 0u;
+                if (lane == 0) base = atomicAdd(a.counter + 6, (unsigned)__popc(m));
+                base = __shfl_sync(FULL, base, 0);
+                if (ch) a.perm[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+            }
+            nch += ch ? 1 : 0;
+        }
+    }
+    nch = warp_sum_ll(nch);
+    __shared__ long long s_n[8];
+    __shared__ unsigned int s_last;
+    if (lane == 0) s_n[w] = nch;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += s_n[ww];
+        a.pnch[blockIdx.x] = t;
+        __threadfence();
+        s_last = (atomicAdd(a.counter + 5, 1u) == gridDim.x - 1) ? 1u : 0u;
+        if (s_last) {
+            __threadfence();
+            const unsigned n = atomicAdd(a.counter + 6, 0u);
+            a.counter[7] = (init || (long long)n > a.inc_cap) ? 1u : 0u;
+            a.counter[5] = 0u;
+        }
+    }
+}
+
+// 2. (list passes only) Per listed row, one warp (lane l on dimensions 4l..4l+3, four rows in flight
+//    per warp): round(x * 2^F) leaves the old cluster's sums and joins the new cluster's (64-bit
+//    integer atomics, exact in any order); the sizes follow.
+__global__ void __launch_bounds__(256) k_dinc_apply(DenseArgs a)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0 || !inc_pass(a) || __ldcg(a.counter + 7) != 0u) return;
+    const int lane = threadIdx.x & 31, d = a.d, K = a.K;
+    const bool act = 4 * lane < d;
+    const int64_t n = (int64_t)__ldcg(a.counter + 6);
+    const int32_t* rho = a.rho_pair[st->cur];
+    const int32_t* prev = a.rho_pair[st->cur ^ 1];
+    const float fxf = ldexpf(1.f, inc_scale(a));
+    const float* X = a.X + 4 * lane;
+    unsigned long long* dS = reinterpret_cast<unsigned long long*>(a.dS);
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p0 < n; p0 += 4 * W) {
+        int64_t r[4];
+        float4 xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t p = p0 + u * W;
+            r[u] = p < n ? (int64_t)__ldcg(a.perm + p) : -1;
+            xv[u] = (act && r[u] >= 0) ? __ldg(reinterpret_cast<const float4*>(X + r[u] * d))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (r[u] < 0) continue;
+            const int jn = rho[r[u]], jo = prev[r[u]];
+            if ((unsigned)jn >= (unsigned)K || (unsigned)jo >= (unsigned)K) continue;
+            if (act) {
+                const long long q[4] = {inc_q(xv[u].x, fxf), inc_q(xv[u].y, fxf), inc_q(xv[u].z, fxf),
+                                        inc_q(xv[u].w, fxf)};
+                unsigned long long* to = dS + (size_t)jn * d + 4 * lane;
+                unsigned long long* from = dS + (size_t)jo * d + 4 * lane;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (q[t] != 0) {
+                        atomicAdd(to + t, (unsigned long long)q[t]);
+                        atomicAdd(from + t, (unsigned long long)(-q[t]));
+                    }
+            }
+            if (lane == 0) {
+                atomicAdd(a.dN + jn, 1);
+                atomicAdd(a.dN + jo, -1);
+            }
+        }
+    }
+}
+
+// 3. (full rebuilds only; the blocks and chunks of k_dsegsum) Per chunk, one warp: the sum of
+//    round(x * 2^F) over the chunk's rows in 64-bit integers, lane l on dimensions 4l..4l+3, added
+//    into its cluster's dS with one atomic per dimension; the cluster sizes into dN.
+__global__ void __launch_bounds__(256) k_dsegsum_raw(DenseArgs a)
+{
+    const int set = pass_set(a.st, a.mode);
+    if (set < 0 || sorted_chain_idle(a)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = a.d;
+    const int nch = *a.nchunks;
+    const int c = blockIdx.x * 8 + w;
+    const float fxf = ldexpf(1.f, inc_scale(a));
+    if (c < nch) {
+        const int j = a.chunk_cluster[c];
+        const int lc = c - a.choff[j];
+        const int p0 = a.off[j] + lc * SEG;
+        const int n = min(a.off[j + 1] - p0, SEG);
+        const bool act = 4 * lane < d;
+        const int ra = lane < n ? a.perm[p0 + lane] : 0;
+        const int rb = lane + 32 < n ? a.perm[p0 + 32 + lane] : 0;
+        const float* X = a.X + 4 * lane;
+        long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int p = 0; p < n; p += SEG_UNROLL) {
+            float4 xv[SEG_UNROLL];
+#pragma unroll
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                const int q = p + u;
+                const int r1 = __shfl_sync(FULL, ra, q & 31), r2 = __shfl_sync(FULL, rb, q & 31);
+                const int64_t row = q < 32 ? r1 : r2;
+                xv[u] = (act && q < n) ? __ldg(reinterpret_cast<const float4*>(X + row * d))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < SEG_UNROLL; ++u) {
+                s0 += inc_q(xv[u].x, fxf);
+                s1 += inc_q(xv[u].y, fxf);
+                s2 += inc_q(xv[u].z, fxf);
+                s3 += inc_q(xv[u].w, fxf);
+            }
+        }
+        if (act) {
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.dS) + (size_t)j * d + 4 * lane;
+            const long long sv[4] = {s0, s1, s2, s3};
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (sv[t] != 0) atomicAdd(dst + t, (unsigned long long)sv[t]);
+        }
+    }
+    for (int jj = blockIdx.x * blockDim.x + threadIdx.x; jj < a.K; jj += gridDim.x * blockDim.x) a.dN[jj] = a.counts[jj];
+}
+
+// 4. (grid-stride over the K*d sums) Spair[cur] = (full rebuild ? 0 : Spair[cur ^ 1]) + dS, likewise
+//    the sizes, and the pass's energy from the sums (Eq. 1 expanded per cluster):
+//      E = sum_i ||x_i||^2 + sum_j (N_j ||c_j||^2 - 2 c_j . S_j),   S_j = 2^-F Spair[cur][j],
+//    in FP64 with the pass's FP64 centroids (each thread's elements in order, the block partials in
+//    block order); then dseg_finish (change counts, controller).
+__global__ void __launch_bounds__(256) k_denergy(DenseArgs a, int nbk)
+{
+    SolveState* st = a.st;
+    const int set = pass_set(st, a.mode);
+    if (set < 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = a.d, K = a.K;
+    const int cur = st->cur;
+    const bool full = __ldcg(a.counter + 7) != 0u;
+    const long long* Sp = a.Spair[cur ^ 1];
+    long long* Sc = a.Spair[cur];
+    const int32_t* Np = a.Npair[cur ^ 1];
+    int32_t* Nc = a.Npair[cur];
+    const double* C = a.c64[set];
+    const int F = inc_scale(a);
+    const size_t nS = (size_t)K * d;
+    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (size_t)gridDim.x * blockDim.x;
+    double e = 0.0;
+    for (size_t i = gt; i < nS; i += gs) {
+        const long long sv = (full ? 0ll : Sp[i]) + __ldcg(a.dS + i);
+        Sc[i] = sv;
+        const int j = (int)(i / (size_t)d);
+        const int nj = (full ? 0 : Np[j]) + __ldcg(a.dN + j);
+        const double c = C[i];
+        e = fma(c, (double)nj * c - 2.0 * ldexp((double)sv, -F), e);
+    }
+    for (size_t j = gt; j < (size_t)K; j += gs) Nc[j] = (full ? 0 : Np[j]) + __ldcg(a.dN + j);
+    e = warp_sum(e);
+    __shared__ double s_e[8];
+    if (lane == 0) s_e[w] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = blockIdx.x == 0 ? __ldcg(a.qx) : 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += s_e[ww];
+        a.pe[blockIdx.x] = t;
+    }
+    dseg_finish(a, nbk, gridDim.x, F);
 }
 
 // Standalone calls: per-row direct-form FP32 squared distance to the assigned centroid (optional
@@ -1538,6 +1807,13 @@ cudaError_t launch_xsplit(const float* X, const void* Xh, void* Xl, int64_t n, i
 cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cudaStream_t s)
 {
     cudaError_t e;
+    const bool inc = a.inc && (a.mode == MODE_INIT || a.mode == MODE_TRIAL || a.mode == MODE_REVERT);
+    if (inc) {       // the changed rows; the sorted chain below runs only when the sums are rebuilt
+        k_dinc_list<<<nbk, 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_dinc_apply<<<std::min(std::max(nbk, 64), 2048), 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_dcount<<<nbk, 256, (size_t)a.K * 4, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_dscan<<<(a.K + 7) / 8, 256, 0, s>>>(a, nbk);
@@ -1550,6 +1826,13 @@ cudaError_t launch_dense_update(const DenseArgs& a, int nbk, int max_chunks, cud
     k_dscatter<<<nbk, 32, sm_sc, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nseg = (max_chunks + 7) / 8;
+    if (inc) {
+        k_dsegsum_raw<<<nseg, 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const size_t ne = std::min<size_t>(1024, std::max<size_t>(1, ((size_t)a.K * a.d + 1023) / 1024));
+        k_denergy<<<(int)ne, 256, 0, s>>>(a, nbk);
+        return cudaGetLastError();
+    }
     k_dsegsum<<<nseg, 256, 0, s>>>(a, nbk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.prescaled) return cudaSuccess;       // k_dsegsum added the totals and finished the pass
@@ -1574,10 +1857,12 @@ cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
+int xcheck_blocks(int nsm) { return nsm * 8; }
+
 cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2, SolveState* st, int nsm,
-                          cudaStream_t s)
+                          cudaStream_t s, double* qx, unsigned int* qctr)
 {
-    k_xcheck<<<nsm * 8, 256, 0, s>>>(X, N, d, xmax, xn2, st);
+    k_xcheck<<<xcheck_blocks(nsm), 256, 0, s>>>(X, N, d, xmax, xn2, st, qx, qctr);
     return cudaGetLastError();
 }
 

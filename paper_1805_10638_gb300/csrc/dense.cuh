@@ -55,8 +55,23 @@ struct DenseArgs {
     int32_t* accC;            // [K]    cleared by k_fin; cluster sizes
     unsigned int* counter;    // [0]: the update's last block, [1]: k_dscan's, [2]: max |chunk partial|
                               // (FP32 bits), [3]: the pass's fixed-point scale exponent, [4]: max ||x||
-                              // (FP32 bits, from k_xcheck)
+                              // (FP32 bits, from k_xcheck), [5]: k_dinc_list's last block, [6]: rows
+                              // listed by k_dinc_list, [7]: 1 = this pass rebuilds the sums in full,
+                              // [8]: k_xcheck's last block
     int prescaled;            // solver: the scale comes from max ||x|| and max ||c|| before the sums
+    // Incremental update of the solver passes (inc != 0).  Spair[i] / Npair[i] hold the exact
+    // integer sums of the partition in rho_pair[i]: per cluster the sum of round(x * 2^F) over its
+    // rows (F fixed for the solve by max ||x||) and its size.  A pass adds only the rows whose label
+    // changed since the last pass (or, past inc_cap such rows and in the INIT pass, rebuilds the sums
+    // through the sorted chain); the energy follows from the sums.
+    int inc;
+    long long inc_cap;
+    long long* Spair[2];      // [K][d]
+    int32_t* Npair[2];        // [K]
+    long long* dS;            // [K][d] this pass's change of the sums (cleared by k_dinc_list)
+    int32_t* dN;              // [K]
+    double* qx;               // [0]: sum of ||x||^2 over all rows (once per solve); [1..]: k_xcheck's
+                              // block partials
     // Hamerly bounds (solver passes; NULL hub: none)
     float* hub;               // [N] upper bound on the distance to the assigned centroid
     float* hlb;               // [N] lower bound on the distance to every other centroid
@@ -102,7 +117,9 @@ cudaError_t launch_pack_dense(const PackArgs& p, cudaStream_t s);
 cudaError_t launch_drow(const DenseArgs& a, const int32_t* rho_in, float* dmin, double* pe, long long* pn, int blocks,
                         cudaStream_t s);
 cudaError_t launch_xcheck(const float* X, int64_t N, int d, unsigned int* xmax, float* xn2, SolveState* st, int nsm,
-                          cudaStream_t s);
+                          cudaStream_t s, double* qx = nullptr, unsigned int* qctr = nullptr);
+// Blocks of k_xcheck (its block partials of sum ||x||^2 need 1 + this many doubles)
+int xcheck_blocks(int nsm);
 // Hamerly bounds of a solver pass: drifts; then (TRIAL, REVERT) the test per row, the list of rows to
 // scan and their BF16 parts copied into the compact buffers Ch, Cl ([N][d] each)
 cudaError_t launch_dense_bounds(const DenseArgs& a, const void* Xh, const void* Xl, void* Ch, void* Cl, int nsm,

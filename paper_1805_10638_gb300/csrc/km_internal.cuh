@@ -192,6 +192,9 @@ struct FinArgs {
     long long* acc;       //   ... accumulated by the pass in acc [K][d] and accC [K] (read, then zeroed)
     int32_t* accC;
     const int* fxs_ptr;   // part_fx == 2: the scale exponent written by the pass
+    int inc;              // with part_fx == 2: the sums are the incremental update's raw sums
+    const long long* Spair[2];   //   sum of x over each cluster in Spair[st->cur] (scale *fxs_ptr),
+    const int32_t* Npair[2];     //   sizes in Npair[st->cur]; kept for the next pass (not zeroed)
     // standalone update
     const void* C_ref;    // reference centroids of the residuals (C_prev), element type T
     void* C_out;          // [K][d] element type T

@@ -42,6 +42,7 @@ struct Plan {
     // dense path (tensor-core assignment, sort-based update)
     size_t cb0, cb1, cl0, cl1, xlo, cn0, cn1, queue, rkey, qcount, err, hist, counts, off, choff, chunk_cluster, nchunks, perm,
         part, pe, pnch, rowe, rown, xn2, drift, map, nrows, xch, xcl;
+    size_t spair0, spair1, npair0, npair1, dsum, dcnt, qx;   // incremental update of the solver passes
     size_t total;
     int nb, nfin, KB, Kpad, DP;
     bool dense;
@@ -55,6 +56,7 @@ struct Plan {
 };
 
 constexpr int DENSE_RPB = 1024;   // rows per block of the dense update's histogram and scatter (at least K)
+constexpr int QX_BLOCKS = 4096;   // room for k_xcheck's block partials of sum ||x||^2
 constexpr int DENSE_SEG = 64;     // rows per segment-sum chunk
 
 }  // namespace
@@ -209,6 +211,15 @@ kmeans_status make_plan_dense(kmeans_ctx* ctx, int64_t N, int d, int K, int m_ma
     P.xcl = take((size_t)N * d * 2);
     P.rowe = take(4096 * 8);
     P.rown = take(4096 * 8);
+    // incremental update: the integer sums and sizes of the partitions in rhoA / rhoB, a pass's
+    // change of them, and sum ||x||^2 with k_xcheck's block partials
+    P.spair0 = take(n * 8);
+    P.spair1 = take(n * 8);
+    P.npair0 = take((size_t)K * 4);
+    P.npair1 = take((size_t)K * 4);
+    P.dsum = take(n * 8);
+    P.dcnt = take((size_t)K * 4);
+    P.qx = take((size_t)(1 + QX_BLOCKS) * 8);
     P.pS = 0;
     P.pCnt = P.counts;
     P.pE = P.pNch = P.pResc = P.pScan = P.pBad = 0;
@@ -243,6 +254,18 @@ bool hamerly_mode()
 {
     const char* v = getenv("KM_HAMERLY");
     return !(v && v[0] == '0');
+}
+
+// KM_DINC in the environment picks the update of the dense solver passes: 0 = the sorted update
+// over every row (the residual sums); unset or 1 = the incremental update, which rebuilds its sums
+// in full when more than a tenth of the rows changed; 2 = the incremental update rebuilding in full
+// every pass; 3 = incremental after the first pass whatever the changes.  1, 2 and 3 give the same
+// integer sums, hence bitwise the same solves.
+int dense_inc_mode()
+{
+    const char* v = getenv("KM_DINC");
+    if (!v || !v[0]) return 1;
+    return (v[0] >= '0' && v[0] <= '3') ? v[0] - '0' : 1;
 }
 
 // KM_BOUNDS in the environment picks the bounds of standalone FP32 solves: "group" = group bounds at
@@ -555,6 +578,15 @@ DenseArgs dense_args(char* base, const Plan& P, const float* X32, int64_t N, int
     a.accC = reinterpret_cast<int32_t*>(a.acc + (size_t)K * d);
     a.counter = at<unsigned int>(base, P.counter);
     a.st = at<SolveState>(base, P.st);
+    a.inc = 0;                                  // set for the solver passes by make_launch
+    a.inc_cap = N / 10;
+    a.Spair[0] = at<long long>(base, P.spair0);
+    a.Spair[1] = at<long long>(base, P.spair1);
+    a.Npair[0] = at<int32_t>(base, P.npair0);
+    a.Npair[1] = at<int32_t>(base, P.npair1);
+    a.dS = at<long long>(base, P.dsum);
+    a.dN = at<int32_t>(base, P.dcnt);
+    a.qx = at<double>(base, P.qx);
     return a;
 }
 
@@ -710,6 +742,15 @@ Launch make_launch(char* base, int nsm, const Plan& P, const kmeans_data* X, int
         da = dense_args(base, P, L.X32, X->N, d, K);
         da.Xb = reinterpret_cast<const __nv_bfloat16*>(X->X_bf16);
         da.prescaled = 1;                // max ||x|| from the prologue's check fixes the update's scale
+        const int im = dense_inc_mode();
+        da.inc = im != 0;                // solver passes add only the rows whose label changed
+        if (im == 2) da.inc_cap = -1;
+        if (im == 3) da.inc_cap = X->N;
+        fa.inc = da.inc;
+        for (int i = 0; i < 2; ++i) {
+            fa.Spair[i] = da.Spair[i];
+            fa.Npair[i] = da.Npair[i];
+        }
         da.thr = thr;
         da.lloyd_only = p.lloyd_only;
         da.fixed_m = p.fixed_m ? 1 : 0;
@@ -825,7 +866,10 @@ cudaError_t launch_prologue(const Launch& L, cudaStream_t s, cudaGraphConditiona
             e = launch_prep(L.C0, false, L.K, L.d, 0, 0, L.ma.C64, const_cast<float*>(L.ma.origin), nullptr, nullptr,
                             nullptr, L.st, L.p.m_init, L.m_max, s, 0);
         if (e == cudaSuccess)
-            e = launch_xcheck(L.X32, L.N, L.d, L.da.counter + 4, const_cast<float*>(L.da.xn2), L.st, L.nsm, s);
+            e = (L.da.inc && xcheck_blocks(L.nsm) > QX_BLOCKS)
+                    ? cudaErrorInvalidConfiguration
+                    : launch_xcheck(L.X32, L.N, L.d, L.da.counter + 4, const_cast<float*>(L.da.xn2), L.st, L.nsm, s,
+                                    L.da.inc ? L.da.qx : nullptr, L.da.counter + 8);
         if (e == cudaSuccess && L.xsplit)
             e = launch_xsplit(L.X32, L.da.Xb, const_cast<void*>(L.xlo), L.N * (int64_t)L.d, L.nsm, s);
         PackArgs pk = L.pk;

@@ -96,7 +96,10 @@ def test_solve_launch_count():
     # lowd_2m: Hamerly bounds, separate mix -> 5 kernels in the prologue and per loop pass, 2 after
     assert bench.solve_launches(152, dense=False, ham=True, fused_mix=False) == 5 * 153 + 2
     assert bench.solve_launches(10, dense=False, ham=False, fused_mix=True) == 3 * 11 + 2
-    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23) == 19 + 13 * 160 + 10 * 23
+    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23,
+                                inc=False) == 19 + 13 * 160 + 10 * 23
+    # the incremental update: three more kernels in every INIT, TRIAL and REVERT chain
+    assert bench.solve_launches(160, dense=True, ham=False, fused_mix=False, rejected=23) == 22 + 16 * 160 + 13 * 23
 
 
 def test_same_energy_speed():
@@ -106,12 +109,16 @@ def test_same_energy_speed():
     assert bench.same_energy_speed([1.0], [2.0], [1.0], [2.0]) == (None, 0)
 
 
-def test_batched_launch_count():
+def test_batched_launch_count(monkeypatch):
     # 3 groups, bounds and a separate mix: 2 + 1 + 3 + 1 in the prologue, 1 + 6 + 2 + 1 per step, 3 + 1 after
     assert bench.batched_launches(10, 3, True, True, []) == 7 + 10 * 10 + 4
     assert bench.batched_launches(10, 3, False, False, []) == 5 + 10 * 8 + 4
+    # the dense instances with the incremental update (the default; KM_DINC=0 removes the 3s)
+    monkeypatch.delenv("KM_DINC", raising=False)
     assert bench.batched_launches(5, 2, True, True, [(7, 1), (9, 0)]) == \
-        (6 + 5 * 8 + 3) + (19 + 13 * 7 + 10) + (19 + 13 * 9)
+        (6 + 5 * 8 + 3) + (22 + 16 * 7 + 13) + (22 + 16 * 9)
+    assert bench.batched_launches(0, 0, False, False, [(4, 2)]) == 22 + 16 * 4 + 13 * 2
+    monkeypatch.setenv("KM_DINC", "0")
     assert bench.batched_launches(0, 0, False, False, [(4, 2)]) == 19 + 13 * 4 + 10 * 2
 
 

@@ -175,3 +175,58 @@ def test_dense_bounds_change_nothing(shape, lloyd, monkeypatch):
     assert np.array_equal(with_b[1], without[1])
     for f in ("iters", "accepted", "rejected", "assign_passes", "converged", "E", "status"):
         assert with_b[2][f] == without[2][f], (f, with_b[2], without[2])
+
+
+def _solve_fresh(X, Xb, C0, **kw):
+    c = km.Context(0)
+    C, rho, info = km.kmeans_solve(c, dev(X), dev(C0), X_bf16=dev_bf16(Xb), **kw)
+    torch.cuda.synchronize()
+    out = (C.cpu().numpy(), rho.cpu().numpy(), info)
+    c.close()
+    return out
+
+
+@pytest.mark.parametrize("shape", [(20_000, 64, 64, 7), (30_000, 128, 300, 8), (12_000, 96, 1024, 9)])
+def test_dense_incremental_update_paths_agree(shape, monkeypatch):
+    """The incremental update of the tensor-core solver passes keeps the exact integer sums of the
+    last partition and adds the rows whose label changed, or rebuilds them through the sorted chain.
+    Both give the same integers, so the default (rebuild past a tenth of the rows changed), a
+    rebuild every pass (KM_DINC=2) and the list after the first pass (KM_DINC=3) are bitwise the
+    same solve, Algorithm 1's energy-driven decisions included."""
+    need_gpu()
+    N, d, K, seed = shape
+    X, Xb, C0 = dense_data(N, d, K, seed)
+    base = _solve_fresh(X, Xb, C0, m_max=10)
+    for mode in ("2", "3"):
+        monkeypatch.setenv("KM_DINC", mode)
+        other = _solve_fresh(X, Xb, C0, m_max=10)
+        assert base[0].tobytes() == other[0].tobytes(), mode
+        assert np.array_equal(base[1], other[1]), mode
+        for f in ("iters", "accepted", "rejected", "assign_passes", "converged", "E", "status"):
+            assert base[2][f] == other[2][f], (mode, f, base[2], other[2])
+
+
+@pytest.mark.parametrize("shape", [(20_000, 64, 64, 7), (30_000, 128, 300, 8)])
+def test_dense_incremental_update_against_sorted_and_oracle(shape, monkeypatch):
+    """The incremental update against the sorted update over every row (KM_DINC=0).  Lloyd takes
+    no decision on the energy, so both visit the same partitions: equal labels and iterations,
+    means and energies to rounding.  The incremental solves' energies (Eq. 1 from the integer sums,
+    FP64) and means (Eq. 4) are those of their partitions in the FP64 oracle's arithmetic."""
+    need_gpu()
+    N, d, K, seed = shape
+    X, Xb, C0 = dense_data(N, d, K, seed)
+    inc_l = _solve_fresh(X, Xb, C0, lloyd_only=1)
+    inc_a = _solve_fresh(X, Xb, C0, m_max=10)
+    monkeypatch.setenv("KM_DINC", "0")
+    srt_l = _solve_fresh(X, Xb, C0, lloyd_only=1)
+    assert np.array_equal(inc_l[1], srt_l[1])
+    for f in ("iters", "assign_passes", "converged", "status"):
+        assert inc_l[2][f] == srt_l[2][f], (f, inc_l[2], srt_l[2])
+    assert rel_err(inc_l[0], srt_l[0]) < 1e-6
+    assert abs(inc_l[2]["E"] - srt_l[2]["E"]) <= 1e-7 * srt_l[2]["E"]
+    for C, rho, info in (inc_l, inc_a):
+        assert info["converged"] == 1, info
+        Eo = oracle.energy(X, C, rho)
+        assert abs(info["E"] - Eo) <= 1e-9 * Eo, (info["E"], Eo)
+        Cm, _ = oracle.update(X, rho, K, C)
+        assert rel_err(C, Cm) < 1e-6

@@ -51,8 +51,11 @@ def test_update_static_allocates_nothing_and_matches(dtype):
         outs = (torch.empty_like(dev[2]), torch.empty(K, dtype=torch.int64, device="cuda"))
         ref = km.kmeans_update(ctx, *dev[:2], K, dev[2])
         inputs.append((X, rho, Cp, K, dev, outs, ref))
-    # a first call per shape (kernel modules load lazily), then the measured calls
+    # a first call per shape, then the measured calls: kernels load lazily (into a code pool that
+    # grows in 2 MiB steps), torch's fill kernels used below included
     for X, rho, Cp, K, dev, outs, ref in inputs:
+        outs[0].fill_(-1)
+        outs[1].fill_(-1)
         km.kmeans_update_static(dev[0], dev[1], K, dev[2], C_out=outs[0], counts=outs[1])
     before = _memory()
     for X, rho, Cp, K, dev, outs, ref in inputs:                     # two calls in a row

@@ -50,6 +50,9 @@ typedef enum {
  *               product; rows whose best two scores lie within that bound are rescored in FP32
  *               from X.  Centroids are float.  Needs 17 <= d <= 128 with d % 8 == 0, K <= 4096,
  *               and X, X_bf16 (and X_bf16_lo if given) 16-byte aligned (else KM_EINVAL).
+ *               In the solvers the cluster sums are exact 64-bit integer sums of x * 2^F (F
+ *               fixed per solve by max ||x||) carried from pass to pass, so a pass adds only
+ *               the rows whose label changed; E follows from them and sum ||x||^2 in FP64.
  * In every mode centroid-space arithmetic (update, residuals, Anderson least squares, energy
  * comparison) is FP64. */
 typedef enum { KM_F64 = 0, KM_F32 = 1, KM_BF16_F32 = 2 } kmeans_prec;

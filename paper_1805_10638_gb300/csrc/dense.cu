@@ -24,8 +24,11 @@
 //
 // Update (Eq. 4), deterministic and without floating-point atomics: integer per-block histograms,
 // an exclusive scan, a stable scatter of row indices by label (row order within a cluster), and
-// fixed-order segment sums of the residuals x_i - c_j per cluster (FP32 within chunks of 64 rows,
-// FP64 across chunks).  The energy (Eq. 1) comes out of the same segment sums.
+// segment sums of the residuals x_i - c_j per cluster (FP32 within chunks of 64 rows, then 64-bit
+// fixed point with integer atomics).  The energy (Eq. 1) comes out of the same segment sums.
+// The solver passes instead carry the exact integer sums of x per cluster from pass to pass and
+// add only the rows whose label changed (or rebuild the sums with the same chunks when many did);
+// their energy follows from those sums and sum ||x||^2 (the incremental update below).
 #include <algorithm>
 
 #include <cuda.h>
